@@ -1,0 +1,345 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(not against itself).  CPU only."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import apply as oapply
+from oracle import baca as ob
+from oracle import generators as og
+from oracle import hbaca as oh
+from oracle import linalg as ol
+from oracle import sampler as osamp
+from paper_1901_06101_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- sampler
+def test_splitmix64_published_vectors():
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            seed, vals = line.split(":")
+            want = [int(v) for v in vals.split()]
+            assert osamp.splitmix64_outputs(int(seed), len(want)) == want
+
+
+def test_initial_columns_distinct_and_uniform():
+    for n, d in [(1, 8), (5, 8), (500, 8), (1563, 32)]:
+        J = osamp.initial_columns(7, 3, n, d)
+        assert len(J) == min(n, d) and len(set(J)) == len(J)
+        assert all(0 <= j < n for j in J)
+    # first element uniform over [0, 10): chi-square over many streams
+    counts = np.zeros(10)
+    for b in range(5000):
+        counts[osamp.initial_columns(11, b, 10, 3)[0]] += 1
+    chi2 = ((counts - 500.0) ** 2 / 500.0).sum()
+    assert chi2 < 30.0  # 9 dof, p ~ 4e-4
+
+
+# ---------------------------------------------------------------- generators
+def test_generator_closed_forms():
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    y = np.array([[0.0, 2.0, 0.0]])
+    g = og.Gaussian(x, y, 2.0)
+    np.testing.assert_allclose(g([0, 1], [0])[:, 0], [np.exp(-4.0 / 8.0), np.exp(-5.0 / 8.0)], rtol=1e-15)
+    hz = og.Helmholtz(x, y, np.pi)
+    np.testing.assert_allclose(hz([0], [0])[0, 0], np.exp(2j * np.pi) / 2.0, rtol=1e-14)
+    np.testing.assert_allclose(hz([1], [0])[0, 0], np.exp(1j * np.pi * np.sqrt(5.0)) / np.sqrt(5.0), rtol=1e-14)
+
+
+def test_sparse_product_entries_by_intersection():
+    sp = inputs.sparse_product(seed=5, m=300, n=280, K=7, density=0.05)
+    g = og.SparseProduct(sp.dense_P(), sp.dense_Q(), sp.P2, sp.Q2)
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        i, j = int(rng.integers(300)), int(rng.integers(280))
+        # brute force: walk row i of P (CSR) and column j of Q (CSC)
+        acc = 0.0
+        ps, pe = sp.p_rowptr[i], sp.p_rowptr[i + 1]
+        qs, qe = sp.q_colptr[j], sp.q_colptr[j + 1]
+        for a in range(ps, pe):
+            for b in range(qs, qe):
+                if sp.p_colidx[a] == sp.q_rowidx[b]:
+                    acc += sp.p_val[a] * sp.q_val[b]
+        acc += sum(sp.P2[i, t] * sp.Q2[t, j] for t in range(sp.P2.shape[1]))
+        assert abs(g([i], [j])[0, 0] - acc) <= 1e-14 * (1 + abs(acc))
+    # exact density: each column of P / row of Q has exactly 5% nonzeros
+    assert np.all((sp.dense_P() != 0).sum(axis=0) == 15)
+    assert np.all((sp.dense_Q() != 0).sum(axis=1) == 14)
+
+
+# ---------------------------------------------------------------- QRCP
+def _separated(rng, p, N, cplx=False):
+    M = rng.standard_normal((p, N)) * np.geomspace(1, 1e-3, N)[rng.permutation(N)]
+    if cplx:
+        M = M + 1j * rng.standard_normal((p, N)) * 0.5
+    return M
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_greedy_qrcp_matches_lapack_geqp3(cplx):
+    rng = np.random.default_rng(1)
+    for trial in range(5):
+        M = _separated(rng, 12, 40, cplx)
+        piv, diag, marg, Q = ol.greedy_qrcp(M, 12)
+        _, R, P = scipy.linalg.qr(M, pivoting=True, mode="economic")
+        k = 0
+        while k < len(piv) and marg[k] > 1e-6:
+            k += 1
+        assert k >= 3
+        assert piv[:k] == list(P[:k])
+        np.testing.assert_allclose(diag[:k], np.abs(np.diag(R))[:k], rtol=1e-10)
+        np.testing.assert_allclose(Q.conj().T @ Q, np.eye(len(piv)), atol=1e-13)
+        T = Q.conj().T @ M[:, piv]
+        assert np.abs(np.tril(T, -1)).max() < 1e-12 * np.abs(M).max()
+
+
+def test_greedy_qrcp_second_pivot_maximises_area():
+    rng = np.random.default_rng(2)
+    M = rng.standard_normal((5, 30))
+    piv, _, _, _ = ol.greedy_qrcp(M, 2)
+    assert piv[0] == int(np.argmax(np.linalg.norm(M, axis=0)))
+    areas = [abs(np.linalg.det(M[:, [piv[0], j]].T @ M[:, [piv[0], j]])) if j != piv[0] else -1
+             for j in range(30)]
+    assert piv[1] == int(np.argmax(areas))
+
+
+def test_greedy_qrcp_candidates_and_rank_tol():
+    rng = np.random.default_rng(3)
+    U, V = inputs.lowrank(4, 10, 25, 3)
+    M = U @ V
+    cand = np.ones(25, bool)
+    cand[:5] = False
+    piv, diag, _, _ = ol.greedy_qrcp(M, 10, candidates=cand)
+    assert all(p >= 5 for p in piv) and len(piv) == 10
+    piv, diag, _, _ = ol.greedy_qrcp(M, 10, rank_tol=1e-8)
+    assert len(piv) == 3
+    piv, _, _, _ = ol.greedy_qrcp(np.zeros((4, 6)), 4, rank_tol=1e-8)
+    assert piv == []
+
+
+def test_eps_rank_definition():
+    assert ol.eps_rank([1.0, 0.5, 1e-7], 1e-6) == 2
+    assert ol.eps_rank([2.0, 2e-6, 1e-7], 1e-6) == 2  # Sigma_{k+1} < eps Sigma_1 is strict
+    assert ol.eps_rank([100.0, 1e-3, 1e-5], 1e-6) == 2  # relative to Sigma_1
+    assert ol.eps_rank([0.0, 0.0], 1e-6) == 0
+    assert ol.eps_rank([], 1e-6) == 0
+
+
+# ---------------------------------------------------------------- LRID / norms
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lrid_is_interpolative_decomposition(cplx):
+    rng = np.random.default_rng(4)
+    m, n, d = 40, 35, 6
+    A = rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if cplx else 0)
+    I = list(rng.choice(m, d, replace=False))
+    J = list(rng.choice(n, d, replace=False))
+    C, R, W = A[:, J], A[I, :], A[np.ix_(I, J)]
+    Uk, Vk, dk, jbar = ob.lrid(C, W, R, 1e-12)
+    assert dk == d and sorted(jbar) == list(range(d))
+    # full-rank W: U_k V_k = C W^{-1} R (the ID / CUR form, Sec. 3.2)
+    np.testing.assert_allclose(Uk @ Vk, C @ np.linalg.solve(W, R), rtol=1e-9, atol=1e-10)
+    # cross property: residual vanishes on the selected rows and columns
+    E = A - Uk @ Vk
+    assert np.abs(E[:, J]).max() < 1e-10 and np.abs(E[I, :]).max() < 1e-10
+
+
+def test_lrid_rank_deficient_keeps_columns_exact():
+    rng = np.random.default_rng(5)
+    U0, V0 = inputs.lowrank(6, 30, 30, 3)
+    A = U0 @ V0
+    I = list(range(8))
+    J = list(range(8))
+    Uk, Vk, dk, jbar = ob.lrid(A[:, J], A[np.ix_(I, J)], A[I, :], 1e-10)
+    assert dk == 3
+    E = A - Uk @ Vk
+    kept = [J[p] for p in jbar]
+    assert np.abs(E[:, kept]).max() < 1e-10 * np.abs(A).max()
+    # the rank-3 matrix is reproduced exactly by the rank-3 ID
+    assert np.abs(E).max() < 1e-9 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lrnorm_and_update_identities(cplx):
+    rng = np.random.default_rng(6)
+    def mat(a, b):
+        M = rng.standard_normal((a, b))
+        return M + 1j * rng.standard_normal((a, b)) if cplx else M
+    U, V, Uk, Vk = mat(30, 7), mat(7, 25), mat(30, 4), mat(4, 25)
+    nu = ob.lrnorm(Uk, Vk)
+    assert abs(nu - np.linalg.norm(Uk @ Vk)) < 1e-12 * nu
+    assert abs(nu - ob.lrnorm_cholesky(Uk, Vk)) < 1e-12 * nu  # Eqs. chol, numu
+    mu = np.linalg.norm(U @ V)
+    mu2 = ob.lrnormup(U, V, mu, Uk, Vk, nu)
+    want = np.linalg.norm(np.concatenate([U, Uk], 1) @ np.concatenate([V, Vk], 0))
+    assert abs(mu2 - want) < 1e-12 * want
+
+
+# ---------------------------------------------------------------- ACA / BACA
+def _gauss_small(m=120, n=110, seed=8, h=0.6):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (m, 3))
+    y = rng.uniform(0, 1, (n, 3)) + np.array([1.5, 0, 0])
+    return og.Gaussian(x, y, h)
+
+
+@pytest.mark.parametrize("gen", ["gauss", "lowrank"])
+def test_baca_d1_is_aca(gen):
+    """Sec. 3.2: BACA with d = 1 reduces to ACA (same pivots, same U V)."""
+    g = _gauss_small() if gen == "gauss" else og.LowRank(*inputs.lowrank(9, 80, 70, 6))
+    a = ob.aca(g, 1e-8, seed=3, bid=0)
+    b = ob.baca(g, 1, 1e-8, seed=3, bid=0)
+    # compare while the pivots are above rounding noise (nu/mu > 1e-12)
+    n_ok = sum(1 for t in b["trace"] if t["dk"] == 1 and t["nu"] > 1e-12 * t["mu"])
+    bp = [(t["I"][0], t["J"][0]) for t in b["trace"] if t["dk"] == 1]
+    assert n_ok >= 5
+    assert a["piv"][:n_ok] == bp[:n_ok]
+    A = g(np.arange(g.m), np.arange(g.n))
+    np.testing.assert_allclose(a["U"] @ a["V"], b["U"] @ b["V"], rtol=0, atol=1e-12 * np.abs(A).max())
+
+
+def test_baca_full_block_is_qrcp_id():
+    """Sec. 3.2: with d = min(m, n) BACA is the QRCP-based ID; its columns are
+    LAPACK geqp3's pivots and its rank the QRCP eps-rank."""
+    rng = np.random.default_rng(10)
+    m = n = 40
+    U0 = rng.standard_normal((m, 12)) * np.geomspace(1, 1e-9, 12)
+    A = U0 @ rng.standard_normal((12, n))
+    g = og.Dense(A)
+    eps = 1e-6
+    res = ob.baca(g, n, eps, seed=0)
+    t = res["trace"][0]
+    _, R, P = scipy.linalg.qr(A, pivoting=True, mode="economic")
+    rr = int(np.sum(np.abs(np.diag(R)) >= eps * abs(R[0, 0])))
+    assert t["dk"] == rr
+    kept = [t["J"][p] for p in t["jbar"]]
+    assert kept == list(P[:rr])
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_product_of_random_exact_rank(cplx):
+    """Product-of-random kernel (Sec. 5, kernel 6): rank exactly r after
+    re-compression, error at rounding level."""
+    U0, V0 = inputs.lowrank(11, 150, 130, 13, complex_=cplx)
+    g = og.LowRank(U0, V0)
+    res = ob.baca(g, 8, 1e-10, seed=1)
+    U, s, V = ob.recompress(res["U"], res["V"], 1e-10)
+    assert len(s) == 13
+    A = U0 @ V0
+    assert np.linalg.norm(A - (U * s) @ V) <= 1e-13 * np.linalg.norm(A)
+
+
+def test_baca_cross_property():
+    """(LRID2): after each iteration the residual vanishes on the kept
+    columns, and on the kept rows when d_k = d."""
+    g = _gauss_small()
+    A = g(np.arange(g.m), np.arange(g.n))
+    res = ob.baca(g, 6, 1e-12, seed=2)
+    U, V = res["U"], res["V"]
+    r = 0
+    for t in res["trace"]:
+        r += t["dk"]
+        E = A - U[:, :r] @ V[:r]
+        cols = [t["J"][p] for p in t["jbar"]]
+        assert np.abs(E[:, cols]).max() < 1e-11
+        if t["dk"] == len(t["I"]):
+            assert np.abs(E[t["I"], :]).max() < 1e-11
+
+
+def test_recompress_is_truncated_svd_of_product():
+    rng = np.random.default_rng(12)
+    U = rng.standard_normal((60, 9)) * np.geomspace(1, 1e-8, 9)
+    V = rng.standard_normal((9, 50))
+    Ur, s, Vr = ob.recompress(U, V, 1e-5)
+    sv = np.linalg.svd(U @ V, compute_uv=False)
+    assert len(s) == ol.eps_rank(sv, 1e-5)
+    np.testing.assert_allclose(s, sv[:len(s)], rtol=1e-9)
+    np.testing.assert_allclose(Ur.conj().T @ Ur, np.eye(len(s)), atol=1e-12)
+    np.testing.assert_allclose(Vr @ Vr.conj().T, np.eye(len(s)), atol=1e-12)
+
+
+# ---------------------------------------------------------------- merges / H-BACA
+def _random_svd(rng, m, n, r, cplx):
+    L = rng.standard_normal((m, r))
+    R = rng.standard_normal((r, n))
+    if cplx:
+        L = L + 1j * rng.standard_normal((m, r))
+        R = R + 1j * rng.standard_normal((r, n))
+    A = L @ R
+    U, s, Vh = np.linalg.svd(A, full_matrices=False)
+    return U[:, :r], s[:r], Vh[:r], A
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_merges_equal_svd_of_concatenation(cplx):
+    rng = np.random.default_rng(13)
+    U1, s1, V1, A1 = _random_svd(rng, 30, 20, 4, cplx)
+    U2, s2, V2, A2 = _random_svd(rng, 30, 25, 5, cplx)
+    U, s, V = oh.horizontal_merge(U1, s1, V1, U2, s2, V2, 1e-12)
+    sv = np.linalg.svd(np.concatenate([A1, A2], 1), compute_uv=False)
+    np.testing.assert_allclose(s, sv[:len(s)], rtol=1e-10)
+    np.testing.assert_allclose((U * s) @ V, np.concatenate([A1, A2], 1), atol=1e-10)
+    U3, s3, V3, A3 = _random_svd(rng, 22, 20, 3, cplx)
+    U, s, V = oh.vertical_merge(U1, s1, V1, U3, s3, V3, 1e-12)
+    sv = np.linalg.svd(np.concatenate([A1, A3], 0), compute_uv=False)
+    np.testing.assert_allclose(s, sv[:len(s)], rtol=1e-10)
+    np.testing.assert_allclose((U * s) @ V, np.concatenate([A1, A3], 0), atol=1e-10)
+
+
+def test_tree_split_sizes():
+    lv = oh.tree_levels(2000, 2)
+    assert lv[0] == [(0, 500), (500, 500), (1000, 500), (1500, 500)]
+    lv = oh.tree_levels(50000, 5)
+    sizes = [s for _, s in lv[0]]
+    assert len(sizes) == 32 and sum(sizes) == 50000 and set(sizes) <= {1562, 1563}
+    lv = oh.tree_levels(7, 2)
+    assert [s for _, s in lv[0]] == [2, 2, 2, 1]
+
+
+def test_hbaca_nb1_is_baca_plus_recompression():
+    """Sec. 4: with n_b = 1 H-BACA is BACA (plus its re-compression)."""
+    g = _gauss_small()
+    h = oh.hbaca(g, 0, 8, 1e-8, seed=4)
+    b = ob.baca(g, 8, 1e-8, seed=4, bid=osamp.block_id(0, 0, 0))
+    U, s, V = ob.recompress(b["U"], b["V"], 1e-8)
+    np.testing.assert_allclose(h["s"], s, rtol=1e-12)
+    np.testing.assert_allclose((h["U"] * h["s"]) @ h["V"], (U * s) @ V, atol=1e-13)
+
+
+@pytest.mark.parametrize("L", [0, 1, 2])
+@pytest.mark.parametrize("eps", [1e-2, 1e-6, 1e-10])
+def test_hbaca_accuracy_against_dense_svd(L, eps):
+    """Sec. 5.2: error ~ eps with a slight increase as n_b grows; the rank is
+    at least what Eckart-Young requires for the achieved 2-norm error."""
+    x, y = inputs.gaussian_pair(seed=0, m=256, n=240)
+    g = og.Gaussian(x, y, 1.0)
+    res = oh.hbaca(g, L, 8, eps, seed=0)
+    A = g(np.arange(g.m), np.arange(g.n))
+    E = A - (res["U"] * res["s"]) @ res["V"]
+    err = np.linalg.norm(E) / np.linalg.norm(A)
+    sv = np.linalg.svd(A, compute_uv=False)
+    # the eps-rank rule of Sec. 2 is relative to sigma_1, so even the exact
+    # truncated SVD has Frobenius error e_opt = ||sigma_{r_eps+1:}|| / ||A||_F
+    e_opt = np.linalg.norm(sv[ol.eps_rank(sv, eps):]) / np.linalg.norm(sv)
+    assert err <= (1.1 if L == 0 else 2.0) * max(eps, e_opt)
+    e2 = np.linalg.norm(E, 2)
+    need = int(np.sum(sv > e2 * (1 + 1e-9)))
+    assert res["r"] >= need
+    if e2 < eps * sv[0]:
+        assert res["r"] >= ol.eps_rank(sv, eps)
+
+
+def test_hbaca_complex_helmholtz_small():
+    x, y = inputs.sphere_pair(seed=1, m=300, n=280)
+    g = og.Helmholtz(x, y, 4 * np.pi)
+    res = oh.hbaca(g, 1, 16, 1e-4, seed=1)
+    err = oapply.rel_error_dense(g, res["U"], res["s"], res["V"])
+    assert err <= 2e-4
+    A = g(np.arange(g.m), np.arange(g.n))
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert res["r"] >= int(np.sum(sv > np.linalg.norm(A - (res["U"] * res["s"]) @ res["V"], 2)))
