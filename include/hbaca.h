@@ -1,0 +1,189 @@
+/*
+ * hbaca.h -- C ABI of the GB300 (sm_103a) H-BACA library, libhbaca.so.
+ *
+ * The method is H-BACA (Liu, Sid-Lakhdar, Rebrova, Ghysels, Li, "A Parallel
+ * Hierarchical Blocked Adaptive Cross Approximation Algorithm", arXiv
+ * 1901.06101): every leaf block of an L-level partition (n_b = 4^L leaves)
+ * is compressed by blocked adaptive cross approximation (Alg. 2) from an
+ * O(1) entry function, re-compressed by QR + truncated SVD (Sec. 3.2, last
+ * paragraph), and the leaves are merged pairwise up two binary index trees
+ * (Alg. 3, Eqs. columncomb, columnsvdmerge).  The result is an approximate
+ * truncated SVD A ~ U diag(S) V with ||A - U S V||_F <~ eps ||A||_F (the
+ * problem statement of Alg. 1-3; the bound is heuristic, Eq. aca_stop).
+ *
+ * Conventions
+ *  - All matrix and point pointers are DEVICE pointers unless stated.  The
+ *    caller allocates every device buffer (factors, workspace); the library
+ *    never calls cudaMalloc / cudaFree.
+ *  - U is column-major (element (i, p) at U[p * ldu + i]); V is row-major
+ *    (element (p, j) at V[p * ldv + j]).  Complex data is interleaved
+ *    (real, imaginary) pairs of double, 16-byte aligned.
+ *  - Every entry point is synchronous with respect to the host unless
+ *    HBACA_FLAG_ASYNC is set: it enqueues work on `stream` (a cudaStream_t;
+ *    NULL = the legacy default stream), synchronises that stream once at the
+ *    end and returns the rank on the host.
+ *  - No exception crosses the ABI.  Errors are reported as hbaca_status;
+ *    hbaca_last_error() gives a message for the calling thread.
+ *  - Device-side failures (rank capacity exceeded, NaN/Inf in a norm or a
+ *    pivot) are written to a status word in the workspace and mapped to
+ *    the return code when the call synchronises.
+ */
+#ifndef HBACA_H
+#define HBACA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hbaca_status {
+  HBACA_OK = 0,
+  HBACA_INVALID_ARG = 1,    /* a NULL pointer, a size out of range, an unknown kind */
+  HBACA_RANK_CAPACITY = 2,  /* a leaf or merged rank exceeded its capacity */
+  HBACA_CUDA = 3,           /* a CUDA runtime call failed (message has the detail) */
+  HBACA_TIMEOUT = 4,        /* a bounded device-side wait expired */
+  HBACA_NO_TAPE = 5,        /* backward called on a result without a recorded tape */
+  HBACA_NUMERICAL = 6,      /* NaN or Inf in a norm, a pivot or a singular value */
+  HBACA_WORKSPACE = 7       /* workspace too small or misaligned (256-byte alignment) */
+} hbaca_status;
+
+/* Entry generators: A(i, j) computable in O(1) (abstract; Sec. 5 kernels). */
+typedef enum hbaca_gen_kind {
+  HBACA_GEN_DENSE = 0,          /* explicit matrix a (column-major, lda >= m)             */
+  HBACA_GEN_GAUSSIAN = 1,       /* exp(-||x_i - y_j||^2 / (2 h^2))       (Sec. 5, kernel 1) */
+  HBACA_GEN_HELMHOLTZ = 2,      /* exp(i k r) / r, r = ||x_i - y_j||     (complex128)       */
+  HBACA_GEN_SPARSE_PRODUCT = 3, /* sum_k P(i,k) Q(k,j) + sum_t P2(i,t) Q2(t,j)              */
+  HBACA_GEN_LOWRANK = 4         /* sum_t LU(i,t) LV(t,j)        (Sec. 5, kernel 6)          */
+} hbaca_gen_kind;
+
+typedef enum hbaca_dtype { HBACA_F64 = 0, HBACA_C128 = 1 } hbaca_dtype;
+
+/* Description of one matrix A (m x n).  Only the fields of `kind` are read. */
+typedef struct hbaca_gen {
+  int32_t kind;        /* hbaca_gen_kind */
+  int32_t dtype;       /* hbaca_dtype; HELMHOLTZ requires C128, GAUSSIAN and
+                          SPARSE_PRODUCT require F64 */
+  int64_t m, n;        /* rows, columns (1 <= m, n < 2^31) */
+  /* GAUSSIAN, HELMHOLTZ: points, row-major, `dim` doubles each */
+  const double* x;     /* m x dim */
+  const double* y;     /* n x dim */
+  int32_t dim;         /* 1 .. 64 */
+  int32_t pad0;
+  double h;            /* Gaussian width (> 0) */
+  double k;            /* Helmholtz wavenumber */
+  /* DENSE */
+  const void* a;       /* m x n column-major, scalar = dtype */
+  int64_t lda;
+  /* LOWRANK: LU (m x lr, column-major, ld = m), LV (lr x n, row-major, ld = n) */
+  const void* lu;
+  const void* lv;
+  int64_t lr;
+  /* SPARSE_PRODUCT: P (m x K) in CSR, Q (K x n) in CSC, indices sorted
+     ascending within a row of P / a column of Q; P2 (m x r2) and Q2 (r2 x n)
+     dense row-major. */
+  int64_t K;
+  const int32_t* p_rowptr;  /* m + 1 */
+  const int32_t* p_colidx;
+  const double* p_val;
+  const int32_t* q_colptr;  /* n + 1 */
+  const int32_t* q_rowidx;
+  const double* q_val;
+  const double* p2;
+  const double* q2;
+  int32_t r2;               /* 0 .. 16 */
+  int32_t pad1;
+} hbaca_gen;
+
+/* Flags */
+#define HBACA_FLAG_ASYNC 1u  /* do not synchronise; the rank goes to result.d_rank only */
+
+/* Options of one compression (Alg. 3 inputs n_b, d, eps). */
+typedef struct hbaca_opts {
+  double eps;             /* relative tolerance, 0 < eps < 1 */
+  int32_t d;              /* BACA block size, 1 .. 32 (d = 1 is ACA, Sec. 3.2) */
+  int32_t levels;         /* L >= 0: n_b = 4^L leaves; 2^L <= min(m, n) */
+  uint64_t seed;          /* seed of the random initial column blocks J_1 */
+  int64_t rank_cap;       /* column capacity of U / rows of V (output and every
+                             merged block); 0 = min(m, n) */
+  int64_t leaf_rank_cap;  /* capacity of a leaf's BACA factors before
+                             re-compression; 0 = min(m_leaf, n_leaf, 1024) */
+  uint32_t flags;         /* HBACA_FLAG_* */
+  int32_t cluster;        /* CTAs per leaf (1, 2, 4, 8, 16); 0 = choose automatically */
+} hbaca_opts;
+
+/* Output factors (caller-owned device memory) and the rank. */
+typedef struct hbaca_result {
+  void* U;            /* m x rank_cap, column-major, ld = ldu >= m */
+  int64_t ldu;
+  double* S;          /* rank_cap singular values, descending */
+  void* V;            /* rank_cap x n, row-major, ld = ldv >= n */
+  int64_t ldv;
+  int32_t* d_rank;    /* optional device int receiving the rank (may be NULL) */
+  int64_t rank;       /* OUT (host): the rank r; rows/columns beyond r are unspecified */
+  int32_t leaf_rank_max;   /* OUT: largest leaf BACA rank before re-compression */
+  int32_t leaf_iters_max;  /* OUT: largest number of BACA iterations of a leaf */
+} hbaca_result;
+
+typedef struct hbaca_ctx hbaca_ctx;
+
+/* Create / destroy a context bound to the current CUDA device. */
+hbaca_status hbaca_create(hbaca_ctx** ctx);
+hbaca_status hbaca_destroy(hbaca_ctx* ctx);
+
+/* Bytes of device workspace hbaca_compress needs for (gen, opts); 0 when the
+   arguments are invalid (hbaca_last_error() says why). */
+size_t hbaca_workspace_size(const hbaca_gen* gen, const hbaca_opts* opts);
+
+/* H-BACA(A, n_b = 4^L, d, eps) (Alg. 3): leaf BACA (Alg. 2) with on-device
+   entry generation, leaf SVD re-compression (Sec. 3.2), hierarchical merge
+   (Eqs. columncomb, columnsvdmerge).  `workspace` must hold
+   hbaca_workspace_size(gen, opts) bytes, 256-byte aligned; it is overwritten
+   and, after the call, holds the per-leaf pivot tape read by
+   hbaca_read_leaf_trace.  Returns HBACA_RANK_CAPACITY when a rank exceeds
+   rank_cap / leaf_rank_cap. */
+hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts,
+                            hbaca_result* out, void* workspace, void* stream);
+
+/* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
+   by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index
+   a * 2^L + b.  Arrays I, J, jbar hold `max_iters * d` entries (row-major by
+   iteration, unused slots -1); dI, dJ, dk, nu, mu hold `max_iters` entries.
+   I: row pivots of QR(C_k^t, d) in pivot order (before the shrink of line 9);
+   J: column block J_k (before LRID); jbar: positions into J of the columns
+   LRID keeps (Eq. IkJkUp); dI = |I_k|, dJ = |J_k|, dk = d_k; nu, mu: the
+   norms of lines 10-11.  Indices are local to the leaf. */
+typedef struct hbaca_leaf_trace {
+  int32_t iters;      /* OUT: iterations run */
+  int32_t rank_baca;  /* OUT: BACA rank before re-compression */
+  int32_t rank;       /* OUT: rank after re-compression */
+  int32_t stop;       /* OUT: 0 converged, 1 iteration bound, 2 no columns left,
+                         3 no rows left, 4 rank capacity, 5 NaN/Inf */
+  int32_t max_iters;  /* IN: capacity of the arrays below, in iterations */
+  int32_t d;          /* IN: row stride of I, J, jbar (must equal opts.d) */
+  int32_t* I;
+  int32_t* J;
+  int32_t* jbar;
+  int32_t* dI;
+  int32_t* dJ;
+  int32_t* dk;
+  double* nu;
+  double* mu;
+} hbaca_leaf_trace;
+
+hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts,
+                                   const void* workspace, int64_t leaf,
+                                   hbaca_leaf_trace* trace, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hbaca_last_error(void);
+
+/* Library version string. */
+const char* hbaca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBACA_H */

@@ -1,0 +1,38 @@
+/*
+ * hbaca_debug.h -- inspection entry points of libhbaca.so for tests and
+ * debugging (not needed to use the library).
+ */
+#ifndef HBACA_DEBUG_H
+#define HBACA_DEBUG_H
+
+#include "hbaca.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Copy one intermediate low-rank block U diag(S) V of an H-BACA call out of
+   its workspace into HOST buffers, after hbaca_compress returned.
+   store 0: blocks after the vertical merge of level `level` (level 0 = the
+   re-compressed leaves; levels 0 .. L-1); store 1: blocks after the
+   horizontal merge of level `level` (1 .. L).  Block (a, b) of a store level
+   with nb column nodes has index a * nb + b (Alg. 3 node order).
+   U (m x rank, column-major, ld m), S (rank), V (rank x n, row-major, ld n)
+   must hold m * cap, cap and cap * n elements where cap = opts.rank_cap (as
+   resolved by the library; *cap_out receives it).  *m_out, *n_out, *rank_out
+   receive the block's size and rank. */
+hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace,
+                                    int32_t store, int32_t level, int64_t block, void* U, double* S, void* V,
+                                    int64_t* m_out, int64_t* n_out, int64_t* rank_out, int64_t* cap_out,
+                                    void* stream);
+
+/* Write a JSON description of the workspace layout of (gen, opts) (region
+   byte offsets, stage task tables) into buf (NUL-terminated, truncated to
+   len).  Returns the length the full text needs. */
+size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBACA_DEBUG_H */

@@ -35,16 +35,34 @@ def lrid(C, W, R, eps):
     """LRID(C, W, R, eps) of Alg. 2 (Eqs. LRID1, LRID2).
 
     Returns U_k = C(:, Jbar), V_k = T^{-1} Q^H R, d_k and Jbar (positions
-    into the columns of W, in pivot order)."""
+    into the columns of W, in pivot order).  With ``info`` the QRCP margins
+    and |T_tt| are returned as a fifth element."""
+    return _lrid(C, W, R, eps)[:4]
+
+
+def _noise(A, absUV):
+    """Absolute rounding-noise level of the norms of residual vectors
+    A - U V (d-vectors): 1e-12 * sqrt(d) * max(|A|, |U| |V|), where absUV is
+    the product of the entry-wise magnitudes (cancellation in U V leaves
+    rounding errors proportional to it, not to |U V|)."""
+    scale = max(float(np.abs(A).max(initial=0.0)), float(np.abs(absUV).max(initial=0.0)))
+    return 1e-12 * np.sqrt(max(A.shape[0] if A.ndim == 1 else min(A.shape), 1)) * scale
+
+
+def _lrid(C, W, R, eps, noise=0.0):
     dI, dJ = W.shape
-    piv, diag, _, Q = greedy_qrcp(W, min(dI, dJ), rank_tol=eps)
+    piv, diag, marg, Q = greedy_qrcp(W, min(dI, dJ), rank_tol=eps, abs_noise=noise)
+    # the first rejected candidate (for the margin of the rank decision)
+    full, fdiag, _, _ = greedy_qrcp(W, min(dI, dJ), abs_noise=noise)
+    info = dict(marg=marg, diag=diag, noise=noise,
+                next=(fdiag[len(piv)] if len(fdiag) > len(piv) else None))
     dk = len(piv)
     if dk == 0:
-        return C[:, :0], R[:0, :], 0, []
+        return C[:, :0], R[:0, :], 0, [], info
     T = np.triu(Q.conj().T @ W[:, piv])
     Uk = C[:, piv]
     Vk = scipy.linalg.solve_triangular(T, Q.conj().T @ R, lower=False)
-    return Uk, Vk, dk, piv
+    return Uk, Vk, dk, piv, info
 
 
 def lrnorm(Uk, Vk):
@@ -92,17 +110,22 @@ def baca(gen, d, eps, seed=0, bid=0):
         if len(J) == 0:
             stop = "no columns"
             break
-        C = gen(allrows, J) - U @ V[:, J]
-        I, _, imarg, _ = greedy_qrcp(C.T, d, candidates=~kept_rows)
+        AJ = gen(allrows, J)
+        UVJ = U @ V[:, J]
+        C = AJ - UVJ
+        nC = _noise(AJ, np.abs(U) @ np.abs(V[:, J]))
+        I, _, imarg, _ = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC)
         if len(I) == 0:
             stop = "no rows"
             break
-        R = gen(I, allcols) - U[I, :] @ V
+        AI = gen(I, allcols)
+        UVI = U[I, :] @ V
+        R = AI - UVI
         cand = ~kept_cols
         cand[J] = False
-        Jn, _, jmarg, _ = greedy_qrcp(R, d, candidates=cand)
+        Jn, _, jmarg, _ = greedy_qrcp(R, d, candidates=cand, abs_noise=_noise(AI, np.abs(U[I, :]) @ np.abs(V)))
         W = C[I, :]
-        Uk, Vk, dk, jbar = lrid(C, W, R, eps)
+        Uk, Vk, dk, jbar, winfo = _lrid(C, W, R, eps, nC)
         nu = lrnorm(Uk, Vk) if dk else 0.0
         mu = lrnormup(U, V, mu, Uk, Vk, nu) if dk else mu
         U = np.concatenate([U, Uk], axis=1)
@@ -110,7 +133,7 @@ def baca(gen, d, eps, seed=0, bid=0):
         kept_rows[I[:dk]] = True
         kept_cols[[J[p] for p in jbar]] = True
         trace.append(dict(J=list(J), I=list(I), Imarg=imarg, Jnext=list(Jn),
-                          Jmarg=jmarg, jbar=list(jbar), dk=dk, nu=nu, mu=mu))
+                          Jmarg=jmarg, jbar=list(jbar), dk=dk, nu=nu, mu=mu, W=winfo))
         if nu < eps * mu:
             stop = "converged"
             break
@@ -176,3 +199,111 @@ def recompress(U, V, eps):
     Qv, Tv = np.linalg.qr(V.conj().T)
     X, s, Yh = truncated_svd(Tu @ Tv.conj().T, eps)
     return Qu @ X, s, Yh @ Qv.conj().T
+
+
+def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
+    """Frozen-pivot BACA: Alg. 2 with the pivot choices I_k, J_{k+1}, Jbar,
+    d_k and the iteration count taken from ``trace`` (a record of another
+    run, e.g. the CUDA path).  Every forced choice is checked to be a valid
+    greedy choice up to rounding noise; the arithmetic (residuals, LRID,
+    norms) is the oracle's own.
+
+    ``stop`` is the recorded reason the run ended ("converged", "no columns",
+    "no rows", "iterations"); the last record's valid_stop checks it.
+
+    Returns U, V, r and per-iteration records with the validity flags
+    (valid_I, valid_J, valid_W, valid_dk, valid_stop), nu, mu and
+    noise_level (W at the rounding-noise level; records after the first such
+    one are not comparable with the recorded run)."""
+    m, n = gen.m, gen.n
+    dt = np.dtype(gen.dtype)
+    U = np.zeros((m, 0), dt)
+    V = np.zeros((0, n), dt)
+    mu = 0.0
+    kept_rows = np.zeros(m, bool)
+    kept_cols = np.zeros(n, bool)
+    J = initial_columns(seed, bid, n, d)
+    allrows, allcols = np.arange(m), np.arange(n)
+    recs = []
+    for k, t in enumerate(trace):
+        rec = dict(J_ok=list(J) == list(t["J"]))
+        J = list(t["J"])
+        AJ = gen(allrows, J)
+        UVJ = U @ V[:, J]
+        C = AJ - UVJ
+        nC = _noise(AJ, np.abs(U) @ np.abs(V[:, J]))
+        I, _, _, _, vI = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC, forced=list(t["I"]))
+        rec["valid_I"] = all(v is True for v in vI) and len(I) == len(t["I"])
+        if not rec["valid_I"]:
+            rec["why"] = [v for v in vI if v is not True]
+            recs.append(rec)
+            break
+        AI = gen(I, allcols)
+        UVI = U[I, :] @ V
+        R = AI - UVI
+        cand = ~kept_cols
+        cand[J] = False
+        if k + 1 < len(trace):
+            Jn, _, _, _, vJ = greedy_qrcp(R, d, candidates=cand, abs_noise=_noise(AI, np.abs(U[I, :]) @ np.abs(V)),
+                                          forced=list(trace[k + 1]["J"]))
+            # the forced block must also be as long as the greedy rule allows
+            rec["valid_J"] = all(v is True for v in vJ) and len(Jn) == min(d, len(I), int(cand.sum()))
+        else:
+            rec["valid_J"] = True
+        ncand_next = int(cand.sum())
+        W = C[I, :]
+        dI, dJ = W.shape
+        jbar = list(t["jbar"])
+        dk = t["dk"]
+        piv, diag, _, Q, vW = greedy_qrcp(W, min(dI, dJ), abs_noise=nC, forced=jbar, rank_tol=eps)
+        rec["valid_W"] = all(v is True for v in vW) and len(piv) == dk
+        # a cross W whose largest residual column is within 100x the rounding
+        # level carries no information, and a kept pivot |T_tt| within 1e4x of
+        # it is rounding-dominated: LRID's relative rank rule keeps it and
+        # T^-1 amplifies the noise, after which two correct implementations
+        # legitimately part ways
+        rec["noise_level"] = bool(len(diag) == 0 or diag[0] <= 100.0 * nC
+                                  or (dk > 0 and min(diag[:dk]) <= 1e4 * nC))
+        # rank rule QR(W, eps): kept pivots at or above eps |T_11|, the next one below
+        nxt = greedy_qrcp(W, min(dI, dJ), abs_noise=nC)[1]
+        ok = True
+        if dk > 0:
+            ok = all(x >= eps * diag[0] - nC for x in diag[:dk])
+            if dk < len(nxt):
+                ok = ok and nxt[dk] < eps * diag[0] + nC + 1e-9 * diag[0]
+        else:
+            ok = len(nxt) == 0 or nxt[0] <= nC
+        rec["valid_dk"] = ok
+        if dk > 0:
+            T = np.triu(Q.conj().T @ W[:, piv])
+            Uk = C[:, piv]
+            Vk = scipy.linalg.solve_triangular(T, Q.conj().T @ R, lower=False)
+            nu = lrnorm(Uk, Vk)
+            mu = lrnormup(U, V, mu, Uk, Vk, nu)
+            U = np.concatenate([U, Uk], axis=1)
+            V = np.concatenate([V, Vk], axis=0)
+        else:
+            nu = 0.0
+        kept_rows[I[:dk]] = True
+        kept_cols[[J[p] for p in jbar]] = True
+        last = k + 1 == len(trace)
+        # the stop decision, with slack for rounding in nu and mu
+        tol = 1e-9 * mu
+        converged = nu < eps * mu + tol
+        if not last:
+            rec["valid_stop"] = nu >= eps * mu - tol
+        elif stop == "converged":
+            rec["valid_stop"] = converged
+        elif stop == "no columns":
+            rec["valid_stop"] = ncand_next == 0
+        elif stop == "no rows":
+            rec["valid_stop"] = bool(kept_rows.all())
+        elif stop == "iterations":
+            rec["valid_stop"] = len(trace) == min(m, n)
+        else:
+            rec["valid_stop"] = False
+        rec.update(nu=nu, mu=mu, dk=dk)
+        recs.append(rec)
+        if k + 1 < len(trace):
+            J = list(trace[k + 1]["J"])
+    return dict(U=U, V=V, r=U.shape[1], recs=recs, mu=mu)

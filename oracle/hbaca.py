@@ -11,7 +11,7 @@ other stacked factor.
 """
 import numpy as np
 
-from .baca import baca, recompress
+from .baca import baca, baca_replay, recompress
 from .generators import Window
 from .linalg import truncated_svd
 from .sampler import block_id
@@ -55,10 +55,13 @@ def vertical_merge(U1, s1, V1, U2, s2, V2, eps):
     return Ub @ Up, s, V
 
 
-def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False):
+def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None):
     """H-BACA(A, n_b = 4^L, d, eps) of Alg. 3.  Returns a dict with U, s, V,
     rank r, the leaf BACA results (if ``keep_leaves``), the leaf ranks before
-    and after re-compression, and the merge ranks per level."""
+    and after re-compression, and the merge ranks per level.  ``forced``
+    maps a leaf index a * 2^L + b to a pivot record {"trace": [...], "stop":
+    reason}; those leaves are run by
+    the frozen-pivot replay (baca_replay) instead of the greedy choices."""
     rows = tree_levels(gen.m, L)
     cols = tree_levels(gen.n, L)
     blocks = {}
@@ -66,7 +69,15 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False):
     for a, (r0, mr) in enumerate(rows[0]):
         for b, (c0, nc) in enumerate(cols[0]):
             w = Window(gen, r0, mr, c0, nc)
-            res = baca(w, d, eps, seed=seed, bid=block_id(batch_index, a, b))
+            leaf = a * len(cols[0]) + b
+            if forced is not None and leaf in forced:
+                fr = forced[leaf]
+                res = baca_replay(w, d, eps, fr["trace"], seed=seed, bid=block_id(batch_index, a, b),
+                                  stop=fr.get("stop", "converged"))
+                res["trace"] = res["recs"]
+                res["stop"] = "replayed"
+            else:
+                res = baca(w, d, eps, seed=seed, bid=block_id(batch_index, a, b))
             U, s, V = recompress(res["U"], res["V"], eps)
             blocks[(a, b)] = (U, s, V)
             info = dict(r_baca=res["r"], r=len(s), iters=len(res["trace"]), stop=res["stop"])
@@ -74,6 +85,7 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False):
                 info["baca"] = res
             leaf_info[(a, b)] = info
     merge_ranks = []
+    stages = [("full", 0, dict(blocks))] if keep_leaves else []
     for l in range(1, L + 1):
         half = {}
         for a in range(len(rows[l - 1])):
@@ -89,6 +101,9 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False):
                 full[(a, b)] = vertical_merge(U1, s1, V1, U2, s2, V2, eps)
         merge_ranks.append(dict(half={k: len(v[1]) for k, v in half.items()},
                                 full={k: len(v[1]) for k, v in full.items()}))
+        if keep_leaves:
+            stages.append(("half", l, half))
+            stages.append(("full", l, full))
         blocks = full
     U, s, V = blocks[(0, 0)]
-    return dict(U=U, s=s, V=V, r=len(s), leaves=leaf_info, merges=merge_ranks)
+    return dict(U=U, s=s, V=V, r=len(s), leaves=leaf_info, merges=merge_ranks, stages=stages)

@@ -22,7 +22,7 @@ def _project_out(Q, X):
     return R
 
 
-def greedy_qrcp(M, kmax, candidates=None, rank_tol=None):
+def greedy_qrcp(M, kmax, candidates=None, rank_tol=None, abs_noise=0.0, forced=None):
     """Greedy column-pivoted QR of M (p x N).
 
     Parameters
@@ -34,6 +34,12 @@ def greedy_qrcp(M, kmax, candidates=None, rank_tol=None):
     rank_tol : if given, stop before step t when the chosen residual norm
         falls below ``rank_tol * (first residual norm)``, or when the first
         residual norm is 0 (the QR(A, eps) form of Sec. 2).
+    abs_noise : absolute rounding-noise level of the residual norms; a step
+        whose best-minus-second gap is below it gets margin 0.
+    forced : replay mode.  The pivots are taken from this list (its length is
+        the pivot count, rank_tol is not applied) and every step records
+        whether the forced column is a valid greedy choice, i.e. its
+        residual norm is within 1e-9 * best + abs_noise of the largest one.
 
     Returns
     -------
@@ -44,6 +50,7 @@ def greedy_qrcp(M, kmax, candidates=None, rank_tol=None):
         times the largest initial candidate norm).
     Q : (p, len(piv)) orthonormal basis of the chosen columns (a column is
         zero when its residual norm was zero).
+    In replay mode a fifth element lists the validity of every forced step.
     """
     M = np.asarray(M)
     p, N = M.shape
@@ -51,31 +58,57 @@ def greedy_qrcp(M, kmax, candidates=None, rank_tol=None):
     piv, diag, margins = [], [], []
     Q = np.zeros((p, 0), dtype=np.result_type(M.dtype, np.float64))
     all_norms = np.sqrt((np.abs(M[:, cand]) ** 2).sum(axis=0))
-    noise = 1e-12 * (all_norms.max() if all_norms.size else 0.0)
-    for _ in range(min(kmax, p)):
+    noise = max(1e-12 * (all_norms.max() if all_norms.size else 0.0), abs_noise)
+    valid = []
+    steps = min(kmax, p) if forced is None else len(forced)
+    for step in range(steps):
         idx = np.flatnonzero(cand)
         if idx.size == 0:
             break
         R = _project_out(Q, M[:, idx])
         norms = np.sqrt((np.abs(R) ** 2).sum(axis=0))
         b = int(np.argmax(norms))
+        if forced is not None:
+            top = norms[b]
+            hit = np.flatnonzero(idx == forced[step])
+            if hit.size == 0:
+                valid.append(False)
+                break
+            b = int(hit[0])
+            ok = bool(norms[b] >= top - 1e-9 * top - noise)
+            valid.append(ok if ok else (step, float(top), float(norms[b]), float(noise)))
         best = norms[b]
-        if rank_tol is not None:
+        if rank_tol is not None and forced is None:
             if len(diag) == 0 and best == 0.0:
                 break
             if len(diag) > 0 and best < rank_tol * diag[0]:
                 break
         if idx.size > 1:
             second = np.max(np.delete(norms, b))
-            margins.append((best - second) / best if best > noise else 0.0)
+            gap = best - second
+            margins.append(gap / best if (best > noise and gap > noise) else 0.0)
         else:
             margins.append(np.inf)
         j = int(idx[b])
         piv.append(j)
         diag.append(best)
         cand[j] = False
-        q = R[:, b] / best if best > 0 else np.zeros(p, dtype=Q.dtype)
+        # new basis direction: the normalised residual, orthogonalised once more
+        # against the basis.  In pivot selection (no rank_tol) a residual at the
+        # noise floor, or one that was mostly inside span(Q), adds no direction;
+        # QR(W, eps) keeps every pivot its rank rule accepts (T_tt != 0).
+        q = np.zeros(p, dtype=Q.dtype)
+        if best > (0.0 if rank_tol is not None else noise):
+            q = R[:, b] / best
+            q = q - Q @ (Q.conj().T @ q)
+            nq = np.linalg.norm(q)
+            if rank_tol is not None or nq >= 0.5:
+                q = q / nq
+            else:
+                q = np.zeros(p, dtype=Q.dtype)
         Q = np.concatenate([Q, q[:, None]], axis=1)
+    if forced is not None:
+        return piv, diag, margins, Q, valid  # invalid steps hold (step, best, forced, noise)
     return piv, diag, margins, Q
 
 

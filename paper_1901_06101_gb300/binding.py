@@ -1,0 +1,320 @@
+"""Thin Python binding of libhbaca.so (include/hbaca.h).
+
+Argument marshalling only: every step of the compression runs in the CUDA
+library.  PyTorch provides device memory and the stream.  There is no CPU
+fallback: if the library is missing, ``lib()`` raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhbaca.so")
+
+# hbaca_gen_kind
+GEN_DENSE, GEN_GAUSSIAN, GEN_HELMHOLTZ, GEN_SPARSE_PRODUCT, GEN_LOWRANK = 0, 1, 2, 3, 4
+# hbaca_dtype
+F64, C128 = 0, 1
+FLAG_ASYNC = 1
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
+          5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE"}
+STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}
+
+
+class Gen(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("dtype", ctypes.c_int32),
+        ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+        ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+        ("dim", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("h", ctypes.c_double), ("k", ctypes.c_double),
+        ("a", ctypes.c_void_p), ("lda", ctypes.c_int64),
+        ("lu", ctypes.c_void_p), ("lv", ctypes.c_void_p), ("lr", ctypes.c_int64),
+        ("K", ctypes.c_int64),
+        ("p_rowptr", ctypes.c_void_p), ("p_colidx", ctypes.c_void_p), ("p_val", ctypes.c_void_p),
+        ("q_colptr", ctypes.c_void_p), ("q_rowidx", ctypes.c_void_p), ("q_val", ctypes.c_void_p),
+        ("p2", ctypes.c_void_p), ("q2", ctypes.c_void_p),
+        ("r2", ctypes.c_int32), ("pad1", ctypes.c_int32),
+    ]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.c_double), ("d", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("rank_cap", ctypes.c_int64), ("leaf_rank_cap", ctypes.c_int64),
+        ("flags", ctypes.c_uint32), ("cluster", ctypes.c_int32),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64), ("S", ctypes.c_void_p),
+        ("V", ctypes.c_void_p), ("ldv", ctypes.c_int64), ("d_rank", ctypes.c_void_p),
+        ("rank", ctypes.c_int64), ("leaf_rank_max", ctypes.c_int32), ("leaf_iters_max", ctypes.c_int32),
+    ]
+
+
+class LeafTrace(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32), ("rank_baca", ctypes.c_int32), ("rank", ctypes.c_int32),
+        ("stop", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("d", ctypes.c_int32),
+        ("I", ctypes.c_void_p), ("J", ctypes.c_void_p), ("jbar", ctypes.c_void_p),
+        ("dI", ctypes.c_void_p), ("dJ", ctypes.c_void_p), ("dk", ctypes.c_void_p),
+        ("nu", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+    ]
+
+
+_LIB = None
+
+# (name, restype, argtypes) for every function include/hbaca.h declares
+SIGNATURES = [
+    ("hbaca_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    ("hbaca_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("hbaca_workspace_size", ctypes.c_size_t, [ctypes.POINTER(Gen), ctypes.POINTER(Opts)]),
+    ("hbaca_compress", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Opts),
+                                      ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_void_p]),
+    ("hbaca_read_leaf_trace", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
+                                             ctypes.c_int64, ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
+    ("hbaca_debug_read_block", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4
+     + [ctypes.c_void_p]),
+    ("hbaca_debug_plan_json", ctypes.c_size_t, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_char_p,
+                                                ctypes.c_size_t]),
+    ("hbaca_last_error", ctypes.c_char_p, []),
+    ("hbaca_version", ctypes.c_char_p, []),
+]
+
+
+def lib():
+    """Load libhbaca.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhbaca.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_1901_06101_gb300.build); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class HbacaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hbaca status %s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def check(code):
+    if code != 0:
+        raise HbacaError(code, lib().hbaca_last_error().decode())
+
+
+class Context:
+    """hbaca_ctx bound to the current CUDA device."""
+
+    def __init__(self):
+        self.ptr = ctypes.c_void_p()
+        check(lib().hbaca_create(ctypes.byref(self.ptr)))
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().hbaca_destroy(self.ptr)
+        except Exception:
+            pass
+
+
+def make_opts(eps, d, levels, seed=0, rank_cap=0, leaf_rank_cap=0, flags=0, cluster=0):
+    return Opts(eps=eps, d=d, levels=levels, seed=seed, rank_cap=rank_cap,
+                leaf_rank_cap=leaf_rank_cap, flags=flags, cluster=cluster)
+
+
+def workspace_size(gen, opts):
+    n = lib().hbaca_workspace_size(ctypes.byref(gen), ctypes.byref(opts))
+    if n == 0:
+        raise HbacaError(1, lib().hbaca_last_error().decode())
+    return n
+
+
+# ---------------------------------------------------------------- torch helpers
+def _dev(t, dtype=None):
+    import torch
+    if dtype is not None:
+        t = torch.as_tensor(t, dtype=dtype)
+    t = torch.as_tensor(t)
+    if not t.is_cuda:
+        t = t.to("cuda")
+    return t.contiguous()
+
+
+class GenSpec:
+    """A hbaca_gen plus the device tensors it points into (kept alive)."""
+
+    def __init__(self, gen, keep):
+        self.gen = gen
+        self.keep = keep
+
+    @property
+    def m(self):
+        return self.gen.m
+
+    @property
+    def n(self):
+        return self.gen.n
+
+    @property
+    def complex(self):
+        return self.gen.dtype == C128
+
+
+def gaussian(x, y, h):
+    import torch
+    x = _dev(x, torch.float64)
+    y = _dev(y, torch.float64)
+    g = Gen(kind=GEN_GAUSSIAN, dtype=F64, m=x.shape[0], n=y.shape[0], x=x.data_ptr(), y=y.data_ptr(),
+            dim=x.shape[1], h=float(h))
+    return GenSpec(g, (x, y))
+
+
+def helmholtz(x, y, k):
+    import torch
+    x = _dev(x, torch.float64)
+    y = _dev(y, torch.float64)
+    g = Gen(kind=GEN_HELMHOLTZ, dtype=C128, m=x.shape[0], n=y.shape[0], x=x.data_ptr(), y=y.data_ptr(),
+            dim=x.shape[1], k=float(k))
+    return GenSpec(g, (x, y))
+
+
+def dense(A):
+    """A (m x n) numpy / torch array; stored column-major on the device."""
+    import torch
+    A = torch.as_tensor(A)
+    cplx = A.is_complex()
+    At = _dev(A.T.contiguous(), torch.complex128 if cplx else torch.float64)  # (n, m) row-major = A col-major
+    g = Gen(kind=GEN_DENSE, dtype=C128 if cplx else F64, m=A.shape[0], n=A.shape[1], a=At.data_ptr(), lda=A.shape[0])
+    return GenSpec(g, (At,))
+
+
+def lowrank(LU, LV):
+    import torch
+    LU = torch.as_tensor(LU)
+    LV = torch.as_tensor(LV)
+    cplx = LU.is_complex() or LV.is_complex()
+    dt = torch.complex128 if cplx else torch.float64
+    LUt = _dev(LU.T.contiguous(), dt)  # column-major m x lr
+    LVd = _dev(LV, dt)
+    g = Gen(kind=GEN_LOWRANK, dtype=C128 if cplx else F64, m=LU.shape[0], n=LV.shape[1],
+            lu=LUt.data_ptr(), lv=LVd.data_ptr(), lr=LU.shape[1])
+    return GenSpec(g, (LUt, LVd))
+
+
+def sparse_product(sp):
+    """``sp``: paper_1901_06101_gb300.inputs.SparseProductInputs."""
+    import torch
+    t = [_dev(torch.as_tensor(a)) for a in (sp.p_rowptr, sp.p_colidx, sp.p_val, sp.q_colptr, sp.q_rowidx,
+                                             sp.q_val, sp.P2, sp.Q2)]
+    g = Gen(kind=GEN_SPARSE_PRODUCT, dtype=F64, m=sp.m, n=sp.n, K=sp.K,
+            p_rowptr=t[0].data_ptr(), p_colidx=t[1].data_ptr(), p_val=t[2].data_ptr(),
+            q_colptr=t[3].data_ptr(), q_rowidx=t[4].data_ptr(), q_val=t[5].data_ptr(),
+            p2=t[6].data_ptr(), q2=t[7].data_ptr(), r2=sp.P2.shape[1])
+    return GenSpec(g, tuple(t))
+
+
+class Compressed:
+    """Output of compress(): U (m x r), S (r), V (r x n) as torch views, plus the
+    workspace (which holds the leaf tapes)."""
+
+    def __init__(self, U, S, V, rank, ws, res):
+        self.U, self.S, self.V, self.rank, self.ws, self.res = U, S, V, rank, ws, res
+
+
+def compress(ctx, spec, opts, stream=None, ws=None, out=None):
+    """hbaca_compress on the current torch stream.  ``ws`` / ``out`` may be
+    passed to reuse device buffers across calls."""
+    import torch
+    m, n = spec.m, spec.n
+    cap = opts.rank_cap if opts.rank_cap else min(m, n, 1024)
+    dt = torch.complex128 if spec.complex else torch.float64
+    if ws is None:
+        ws = torch.empty(workspace_size(spec.gen, opts), dtype=torch.uint8, device="cuda")
+    if out is None:
+        Ut = torch.empty((cap, m), dtype=dt, device="cuda")
+        S = torch.empty(cap, dtype=torch.float64, device="cuda")
+        V = torch.empty((cap, n), dtype=dt, device="cuda")
+    else:
+        Ut, S, V = out
+    res = Result(U=Ut.data_ptr(), ldu=m, S=S.data_ptr(), V=V.data_ptr(), ldv=n)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib().hbaca_compress(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.byref(res),
+                               ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(stream)))
+    r = int(res.rank)
+    c = Compressed(Ut[:r].T, S[:r], V[:r], r, ws, res)
+    c.buffers = (Ut, S, V)
+    return c
+
+
+def read_leaf_trace(spec, opts, ws, leaf, max_iters=None):
+    """Per-leaf BACA record (numpy arrays)."""
+    import numpy as np
+    import torch
+    d = opts.d
+    if max_iters is None:
+        max_iters = 4096
+    I = np.full(max_iters * d, -1, np.int32)
+    J = np.full(max_iters * d, -1, np.int32)
+    jb = np.full(max_iters * d, -1, np.int32)
+    dI = np.zeros(max_iters, np.int32)
+    dJ = np.zeros(max_iters, np.int32)
+    dk = np.zeros(max_iters, np.int32)
+    nu = np.zeros(max_iters)
+    mu = np.zeros(max_iters)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    tr = LeafTrace(max_iters=max_iters, d=d, I=p(I), J=p(J), jbar=p(jb), dI=p(dI), dJ=p(dJ), dk=p(dk),
+                   nu=p(nu), mu=p(mu))
+    check(lib().hbaca_read_leaf_trace(ctypes.byref(spec.gen), ctypes.byref(opts),
+                                      ctypes.c_void_p(ws.data_ptr()), leaf, ctypes.byref(tr),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    it = tr.iters
+    recs = []
+    for k in range(it):
+        recs.append(dict(I=list(I[k * d:k * d + dI[k]]), J=list(J[k * d:k * d + dJ[k]]),
+                         jbar=list(jb[k * d:k * d + dk[k]]), dk=int(dk[k]), nu=float(nu[k]), mu=float(mu[k])))
+    return dict(iters=it, rank_baca=tr.rank_baca, rank=tr.rank, stop=STOP.get(tr.stop, tr.stop), trace=recs)
+
+
+def read_block(spec, opts, ws, store, level, block):
+    """Intermediate block (store 0: after the vertical merge of ``level``, level
+    0 = re-compressed leaves; store 1: after the horizontal merge of ``level``)
+    as numpy U (m x r), S (r), V (r x n)."""
+    import numpy as np
+    import torch
+    m, n = spec.m, spec.n
+    cap = opts.rank_cap if opts.rank_cap else min(m, n, 1024)
+    dt = np.complex128 if spec.complex else np.float64
+    # block sizes are at most the matrix sizes
+    Ub = np.zeros(m * cap, dt)
+    Sb = np.zeros(cap)
+    Vb = np.zeros(cap * n, dt)
+    mo, no, ro, co = (ctypes.c_int64() for _ in range(4))
+    check(lib().hbaca_debug_read_block(ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()),
+                                       store, level, block, Ub.ctypes.data_as(ctypes.c_void_p),
+                                       Sb.ctypes.data_as(ctypes.c_void_p), Vb.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(mo), ctypes.byref(no), ctypes.byref(ro), ctypes.byref(co),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    bm, bn, r = mo.value, no.value, ro.value
+    U = Ub[:bm * r].reshape(r, bm).T
+    V = Vb[:r * bn].reshape(r, bn)
+    return U, Sb[:r], V
+
+
+def plan_json(spec, opts):
+    """Workspace layout of (spec, opts) as a dict (debugging aid)."""
+    import json
+    n = lib().hbaca_debug_plan_json(ctypes.byref(spec.gen), ctypes.byref(opts), None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib().hbaca_debug_plan_json(ctypes.byref(spec.gen), ctypes.byref(opts), buf, n)
+    return json.loads(buf.value.decode())

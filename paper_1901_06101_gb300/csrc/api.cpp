@@ -1,0 +1,279 @@
+// C ABI of libhbaca (include/hbaca.h): argument checks, planning, launches,
+// device status mapping.  No exception crosses this boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hbaca.h"
+#include "hbaca_debug.h"
+#include "plan.h"
+#include "run.h"
+#include "types.h"
+
+struct hbaca_ctx {
+  int device;
+  int sms;
+};
+
+namespace {
+
+thread_local std::string tls_err;
+
+hbaca_status fail(hbaca_status s, const std::string& m) {
+  tls_err = m;
+  return s;
+}
+
+int current_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 152; }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); return 152; }
+  return sms > 0 ? sms : 152;
+}
+
+hbaca_status map_device_status(int ds) {
+  switch (ds) {
+    case 0: return HBACA_OK;
+    case 2: return HBACA_RANK_CAPACITY;
+    case 4: return HBACA_TIMEOUT;
+    case 6: return HBACA_NUMERICAL;
+    default: return HBACA_CUDA;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hbaca_version(void) { return "hbaca-gb300 0.1 (sm_103a)"; }
+
+const char* hbaca_last_error(void) { return tls_err.c_str(); }
+
+hbaca_status hbaca_create(hbaca_ctx** ctx) {
+  if (!ctx) return fail(HBACA_INVALID_ARG, "ctx is NULL");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  int major = 0, minor = 0, sms = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (major * 10 + minor != 103)
+    return fail(HBACA_CUDA, "libhbaca is built for sm_103a (GB300); device is sm_" + std::to_string(major * 10 + minor));
+  *ctx = new (std::nothrow) hbaca_ctx{dev, sms};
+  if (!*ctx) return fail(HBACA_INVALID_ARG, "out of host memory");
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_destroy(hbaca_ctx* ctx) {
+  delete ctx;
+  return HBACA_OK;
+}
+
+size_t hbaca_workspace_size(const hbaca_gen* gen, const hbaca_opts* opts) {
+  if (!gen || !opts) { tls_err = "gen or opts is NULL"; return 0; }
+  hbaca::Plan p;
+  std::string err;
+  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) { tls_err = err; return 0; }
+  return p.total;
+}
+
+hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts, hbaca_result* out,
+                            void* workspace, void* stream) {
+  if (!ctx || !gen || !opts || !out) return fail(HBACA_INVALID_ARG, "NULL ctx, gen, opts or result");
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return fail(HBACA_WORKSPACE, "workspace must be a non-NULL, 256-byte aligned device pointer");
+  if (!out->U || !out->S || !out->V) return fail(HBACA_INVALID_ARG, "result U, S and V must be set");
+  if (out->ldu < gen->m || out->ldv < gen->n) return fail(HBACA_INVALID_ARG, "result needs ldu >= m and ldv >= n");
+  hbaca::Plan p;
+  std::string err;
+  if (!hbaca::make_plan(*gen, *opts, ctx->sms, p, err)) return fail(HBACA_INVALID_ARG, err);
+  hbaca::bind_user_result(p, *out);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  hbaca::RunCtx rc{ws, st, ctx->sms, out, 0};
+  // status word and leaf work counter live in separate 256-byte regions
+  cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.desc_region.off, p.desc.data(), p.desc.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.user_lv.rank_off, 0, 4, st);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("workspace set-up: ") + cudaGetErrorString(e));
+  e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, err.empty() ? cudaGetErrorString(e) : err);
+  int32_t* d_rank_ws = reinterpret_cast<int32_t*>(ws + p.user_lv.rank_off);
+  if (out->d_rank) {
+    e = cudaMemcpyAsync(out->d_rank, d_rank_ws, 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("rank copy: ") + cudaGetErrorString(e));
+  }
+  out->rank = -1;
+  if (opts->flags & HBACA_FLAG_ASYNC) {
+    tls_err.clear();
+    return HBACA_OK;
+  }
+  int status = 0, rank = 0;
+  std::vector<hbaca::LeafOut> lo(p.nleaves);
+  e = cudaMemcpyAsync(&status, ws + p.status.off, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rank, d_rank_ws, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lo.data(), ws + p.leafout_off, lo.size() * sizeof(hbaca::LeafOut), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("kernel execution: ") + cudaGetErrorString(e));
+  int rmax = 0, imax = 0;
+  for (const auto& l : lo) {
+    rmax = std::max(rmax, l.rank);
+    imax = std::max(imax, l.iters);
+  }
+  out->rank = rank;
+  out->leaf_rank_max = rmax;
+  out->leaf_iters_max = imax;
+  hbaca_status hs = map_device_status(status);
+  if (hs != HBACA_OK) {
+    const char* what = hs == HBACA_RANK_CAPACITY ? "a rank exceeded rank_cap or leaf_rank_cap"
+                       : hs == HBACA_NUMERICAL   ? "NaN or Inf in a norm or a singular value"
+                                                 : "device-side failure";
+    return fail(hs, what);
+  }
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t leaf,
+                                   hbaca_leaf_trace* tr, void* stream) {
+  if (!gen || !opts || !workspace || !tr) return fail(HBACA_INVALID_ARG, "NULL argument");
+  hbaca::Plan p;
+  std::string err;
+  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
+  if (leaf < 0 || leaf >= p.nleaves) return fail(HBACA_INVALID_ARG, "leaf index out of range");
+  if (tr->d != p.d) return fail(HBACA_INVALID_ARG, "trace.d must equal opts.d");
+  hbaca::LeafDesc L;
+  std::memcpy(&L, p.desc.data() + p.leafdesc_off + leaf * sizeof(hbaca::LeafDesc), sizeof(L));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const char* ws = reinterpret_cast<const char*>(workspace);
+  hbaca::LeafOut lo;
+  int rank_after = 0;
+  cudaError_t e = cudaMemcpyAsync(&lo, ws + p.leafout_off + leaf * sizeof(hbaca::LeafOut), sizeof(lo),
+                                  cudaMemcpyDeviceToHost, st);
+  const size_t rank_off = p.L == 0 ? p.user_lv.rank_off : p.full_lv[0].rank_off + leaf * 4;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rank_after, ws + rank_off, 4, cudaMemcpyDeviceToHost, st);
+  const int rec = 4 + 3 * p.d;
+  const int nit = std::min(L.tape_iters, tr->max_iters);
+  std::vector<int32_t> ti((size_t)std::max(nit, 1) * rec);
+  std::vector<double> td((size_t)std::max(nit, 1) * 2);
+  if (e == cudaSuccess && nit > 0)
+    e = cudaMemcpyAsync(ti.data(), ws + p.tape_int.off + L.tape_off * 4, (size_t)nit * rec * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && nit > 0)
+    e = cudaMemcpyAsync(td.data(), ws + p.tape_dbl.off + L.taped_off * 8, (size_t)nit * 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("trace copy: ") + cudaGetErrorString(e));
+  tr->iters = lo.iters;
+  tr->rank_baca = lo.rank;
+  tr->rank = rank_after;
+  tr->stop = lo.stop;
+  const int d = p.d;
+  for (int it = 0; it < nit && it < lo.iters; ++it) {
+    const int32_t* r = ti.data() + (size_t)it * rec;
+    if (tr->dI) tr->dI[it] = r[0];
+    if (tr->dJ) tr->dJ[it] = r[1];
+    if (tr->dk) tr->dk[it] = r[2];
+    for (int s = 0; s < d; ++s) {
+      if (tr->I) tr->I[(size_t)it * d + s] = r[4 + s];
+      if (tr->J) tr->J[(size_t)it * d + s] = r[4 + d + s];
+      if (tr->jbar) tr->jbar[(size_t)it * d + s] = r[4 + 2 * d + s];
+    }
+    if (tr->nu) tr->nu[it] = td[2 * it];
+    if (tr->mu) tr->mu[it] = td[2 * it + 1];
+  }
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace,
+                                    int32_t store, int32_t level, int64_t block, void* U, double* S, void* V,
+                                    int64_t* m_out, int64_t* n_out, int64_t* rank_out, int64_t* cap_out,
+                                    void* stream) {
+  if (!gen || !opts || !workspace) return fail(HBACA_INVALID_ARG, "NULL argument");
+  hbaca::Plan p;
+  std::string err;
+  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
+  const hbaca::StoreLevel* lv = nullptr;
+  const hbaca::Region *ru, *rs, *rv;
+  if (store == 0 && level >= 0 && level < p.L) {
+    lv = &p.full_lv[level];
+    ru = &p.full_u; rs = &p.full_s; rv = &p.full_v;
+  } else if (store == 1 && level >= 1 && level <= p.L) {
+    lv = &p.half_lv[level];
+    ru = &p.half_u; rs = &p.half_s; rv = &p.half_v;
+  } else {
+    return fail(HBACA_INVALID_ARG, "no such store level");
+  }
+  if (block < 0 || block >= lv->nblocks) return fail(HBACA_INVALID_ARG, "block index out of range");
+  hbaca::BlockRef b;
+  std::memcpy(&b, p.desc.data() + lv->refs_off + block * sizeof(b), sizeof(b));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const char* ws = reinterpret_cast<const char*>(workspace);
+  int32_t rank = 0;
+  cudaError_t e = cudaMemcpyAsync(&rank, ws + lv->rank_off + b.rank_slot * 4, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && rank > 0) {
+    if (U) e = cudaMemcpyAsync(U, ws + ru->off + b.u_off * p.esz, (size_t)b.m * rank * p.esz, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && S) e = cudaMemcpyAsync(S, ws + rs->off + b.s_off * 8, (size_t)rank * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && V) e = cudaMemcpyAsync(V, ws + rv->off + b.v_off * p.esz, (size_t)rank * b.n * p.esz, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("block copy: ") + cudaGetErrorString(e));
+  if (m_out) *m_out = b.m;
+  if (n_out) *n_out = b.n;
+  if (rank_out) *rank_out = rank;
+  if (cap_out) *cap_out = p.rank_cap;
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char* buf, size_t len) {
+  if (!gen || !opts) return 0;
+  hbaca::Plan p;
+  std::string err;
+  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) { tls_err = err; return 0; }
+  std::string j = "{";
+  auto reg = [&](const char* name, const hbaca::Region& r) {
+    j += std::string("\"") + name + "\": [" + std::to_string(r.off) + ", " + std::to_string(r.bytes) + "], ";
+  };
+  reg("status", p.status); reg("queue", p.queue); reg("desc", p.desc_region);
+  reg("uar", p.uar); reg("var", p.var); reg("qr", p.qr); reg("tau", p.tau); reg("core", p.core); reg("ord", p.ord);
+  reg("full_u", p.full_u); reg("full_s", p.full_s); reg("full_v", p.full_v);
+  reg("half_u", p.half_u); reg("half_s", p.half_s); reg("half_v", p.half_v);
+  j += "\"leafout\": " + std::to_string(p.leafout_off) + ", \"leafdesc\": " + std::to_string(p.leafdesc_off) + ", ";
+  j += "\"baca_cluster\": " + std::to_string(p.baca_cluster) + ", \"rank_cap\": " + std::to_string(p.rank_cap) + ", ";
+  j += "\"stages\": [";
+  for (size_t si = 0; si < p.stages.size(); ++si) {
+    const hbaca::Stage& st = p.stages[si];
+    j += "{\"kind\": " + std::to_string(st.kind) + ", \"ntasks\": " + std::to_string(st.ntasks) +
+         ", \"kcap\": " + std::to_string(st.kcap) + ", \"dims\": " + std::to_string(st.dims_off) + ", \"tasks\": [";
+    for (size_t ti = 0; ti < st.tasks_h->size(); ++ti) {
+      const hbaca::SvdTask& t = (*st.tasks_h)[ti];
+      j += "{\"a_off\": " + std::to_string(t.a_off) + ", \"rows_a\": " + std::to_string(t.rows_a) +
+           ", \"lda\": " + std::to_string(t.lda) + ", \"a_in_baca\": " + std::to_string(t.a_in_baca) +
+           ", \"b_off\": " + std::to_string(t.b_off) + ", \"rows_b\": " + std::to_string(t.rows_b) +
+           ", \"tau_off\": " + std::to_string(t.tau_off) + ", \"m_off\": " + std::to_string(t.m_off) +
+           ", \"y_off\": " + std::to_string(t.y_off) + ", \"ord_off\": " + std::to_string(t.ord_off) +
+           ", \"kcap\": " + std::to_string(t.kcap) + ", \"in1\": " + std::to_string(t.in1) +
+           ", \"in2\": " + std::to_string(t.in2) + ", \"out\": " + std::to_string(t.out) + "}";
+      if (ti + 1 < st.tasks_h->size()) j += ", ";
+    }
+    j += "]}";
+    if (si + 1 < p.stages.size()) j += ", ";
+  }
+  j += "], \"total\": " + std::to_string(p.total) + "}";
+  if (buf && len) {
+    size_t n = std::min(len - 1, j.size());
+    std::memcpy(buf, j.data(), n);
+    buf[n] = 0;
+  }
+  return j.size() + 1;
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// Shared device-side building blocks of libhbaca: scalar arithmetic for
+// float64 and interleaved complex128, the O(1) entry generators that the
+// residual kernels evaluate in registers, and warp / block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hbaca.h"
+
+namespace hbaca {
+
+// ------------------------------------------------------------------ scalars
+struct __align__(16) cplx {
+  double re, im;
+};
+
+__host__ __device__ __forceinline__ cplx mk(double r, double i) { cplx z; z.re = r; z.im = i; return z; }
+
+template <typename T> struct Traits;
+template <> struct Traits<double> {
+  static constexpr bool is_complex = false;
+  __device__ __forceinline__ static double zero() { return 0.0; }
+};
+template <> struct Traits<cplx> {
+  static constexpr bool is_complex = true;
+  __device__ __forceinline__ static cplx zero() { return mk(0.0, 0.0); }
+};
+
+__device__ __forceinline__ double conj_(double a) { return a; }
+__device__ __forceinline__ cplx conj_(cplx a) { return mk(a.re, -a.im); }
+__device__ __forceinline__ double re_(double a) { return a; }
+__device__ __forceinline__ double re_(cplx a) { return a.re; }
+__device__ __forceinline__ double im_(double) { return 0.0; }
+__device__ __forceinline__ double im_(cplx a) { return a.im; }
+__device__ __forceinline__ double abs2(double a) { return a * a; }
+__device__ __forceinline__ double abs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ cplx add(cplx a, cplx b) { return mk(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ cplx sub(cplx a, cplx b) { return mk(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ cplx mul(cplx a, cplx b) {
+  return mk(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+__device__ __forceinline__ double scale(double a, double s) { return a * s; }
+__device__ __forceinline__ cplx scale(cplx a, double s) { return mk(a.re * s, a.im * s); }
+// acc + a * b
+__device__ __forceinline__ double mac(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ __forceinline__ cplx mac(cplx acc, cplx a, cplx b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+__device__ __forceinline__ double cmac(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ __forceinline__ cplx cmac(cplx acc, cplx a, cplx b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+// acc - a * b
+__device__ __forceinline__ double msub(double acc, double a, double b) { return fma(-a, b, acc); }
+__device__ __forceinline__ cplx msub(cplx acc, cplx a, cplx b) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+// a / b
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ cplx div_(cplx a, cplx b) {
+  double d = 1.0 / abs2(b);
+  return mk((a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d);
+}
+template <typename T> __device__ __forceinline__ T from_re(double r);
+template <> __device__ __forceinline__ double from_re<double>(double r) { return r; }
+template <> __device__ __forceinline__ cplx from_re<cplx>(double r) { return mk(r, 0.0); }
+
+__device__ __forceinline__ bool finite_(double a) { return isfinite(a); }
+
+// Loads of data written by other CTAs of the cluster earlier in the same
+// kernel go through L2 (ld.global.cg), never a possibly stale L1 line.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ cplx ldcg(const cplx* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk(v.x, v.y);
+}
+
+// |z| without squaring (no underflow for tiny z) and the exact unit phase
+// conj(z) / |z| (sign for real z).
+__device__ __forceinline__ double absval(double a) { return fabs(a); }
+__device__ __forceinline__ double absval(cplx a) { return hypot(a.re, a.im); }
+__device__ __forceinline__ double conj_phase(double a, double) { return a >= 0.0 ? 1.0 : -1.0; }
+__device__ __forceinline__ cplx conj_phase(cplx a, double mag) { return mk(a.re / mag, -a.im / mag); }
+
+// Non-negative doubles order like their bit patterns: argmax reductions on
+// norms compare 64-bit integers and keep the FP64 pipe for arithmetic.
+__device__ __forceinline__ long long nbits(double nonneg) { return __double_as_longlong(nonneg); }
+
+// Householder reflector (LAPACK larfg convention) for a vector x of length
+// len with head alpha = x[0] and tail squared norm sig2: beta, tau and the
+// scale 1/(alpha - beta) of the tail.  H = I - tau u u^H, u = [1; x(1:)*sc],
+// H^H x = beta e_1.  tau = 0 (H = I) when the tail is zero and alpha is real.
+template <typename T>
+__device__ __forceinline__ void householder(T alpha, double sig2, double& beta, T& tau, T& sc) {
+  double ar = re_(alpha), ai = im_(alpha);
+  if (sig2 == 0.0 && ai == 0.0) {
+    beta = ar;
+    tau = Traits<T>::zero();
+    sc = Traits<T>::zero();
+    return;
+  }
+  double nrm = sqrt(ar * ar + ai * ai + sig2);
+  beta = (ar >= 0.0) ? -nrm : nrm;
+  T b = from_re<T>(beta);
+  tau = div_(sub(b, alpha), b);
+  sc = div_(from_re<T>(1.0), sub(alpha, b));
+}
+
+// ------------------------------------------------------------------ generators
+// Each generator maps global (row, column) indices to one entry.  They are
+// passed by value into the kernels and inlined into the residual updates.
+struct GenDense {
+  using scalar = double;
+  const double* a;
+  int64_t lda;
+  __device__ __forceinline__ double operator()(int64_t i, int64_t j) const { return a[j * lda + i]; }
+};
+struct GenDenseC {
+  using scalar = cplx;
+  const cplx* a;
+  int64_t lda;
+  __device__ __forceinline__ cplx operator()(int64_t i, int64_t j) const { return a[j * lda + i]; }
+};
+
+struct GenGaussian {
+  using scalar = double;
+  const double* x;
+  const double* y;
+  int dim;
+  double c;  // -1 / (2 h^2)
+  __device__ __forceinline__ double operator()(int64_t i, int64_t j) const {
+    const double* xi = x + i * dim;
+    const double* yj = y + j * dim;
+    double s = 0.0;
+    if (dim == 3) {
+      double t0 = xi[0] - yj[0], t1 = xi[1] - yj[1], t2 = xi[2] - yj[2];
+      s = fma(t0, t0, fma(t1, t1, t2 * t2));
+    } else {
+      for (int t = 0; t < dim; ++t) {
+        double u = xi[t] - yj[t];
+        s = fma(u, u, s);
+      }
+    }
+    return exp(s * c);
+  }
+};
+
+struct GenHelmholtz {
+  using scalar = cplx;
+  const double* x;
+  const double* y;
+  int dim;
+  double kpi;  // k / pi: sincospi(kpi * r) = (sin, cos)(k r)
+  __device__ __forceinline__ cplx operator()(int64_t i, int64_t j) const {
+    const double* xi = x + i * dim;
+    const double* yj = y + j * dim;
+    double s = 0.0;
+    for (int t = 0; t < dim; ++t) {
+      double u = xi[t] - yj[t];
+      s = fma(u, u, s);
+    }
+    double rinv = rsqrt(s);
+    double r = s * rinv;
+    double sn, cs;
+    sincospi(kpi * r, &sn, &cs);
+    return mk(cs * rinv, sn * rinv);
+  }
+};
+
+struct GenLowRank {
+  using scalar = double;
+  const double* lu;  // m x lr, column-major, ld = m
+  const double* lv;  // lr x n, row-major, ld = n
+  int64_t m, n, lr;
+  __device__ __forceinline__ double operator()(int64_t i, int64_t j) const {
+    double s = 0.0;
+    for (int64_t t = 0; t < lr; ++t) s = fma(lu[t * m + i], lv[t * n + j], s);
+    return s;
+  }
+};
+struct GenLowRankC {
+  using scalar = cplx;
+  const cplx* lu;
+  const cplx* lv;
+  int64_t m, n, lr;
+  __device__ __forceinline__ cplx operator()(int64_t i, int64_t j) const {
+    cplx s = mk(0.0, 0.0);
+    for (int64_t t = 0; t < lr; ++t) s = mac(s, lu[t * m + i], lv[t * n + j]);
+    return s;
+  }
+};
+
+// A(i,j) = sum_k P(i,k) Q(k,j) + sum_t P2(i,t) Q2(t,j): a sorted-list
+// intersection of row i of P (CSR) with column j of Q (CSC), then the dense term.
+struct GenSparseProduct {
+  using scalar = double;
+  const int32_t* prp;
+  const int32_t* pci;
+  const double* pv;
+  const int32_t* qcp;
+  const int32_t* qri;
+  const double* qv;
+  const double* p2;
+  const double* q2;
+  int64_t n;
+  int r2;
+  __device__ __forceinline__ double operator()(int64_t i, int64_t j) const {
+    int a = prp[i], ae = prp[i + 1];
+    int b = qcp[j], be = qcp[j + 1];
+    double s = 0.0;
+    while (a < ae && b < be) {
+      int ka = pci[a], kb = qri[b];
+      if (ka == kb) {
+        s = fma(pv[a], qv[b], s);
+        ++a;
+        ++b;
+      } else if (ka < kb) {
+        ++a;
+      } else {
+        ++b;
+      }
+    }
+    double t = 0.0;
+    for (int u = 0; u < r2; ++u) t = fma(p2[i * r2 + u], q2[u * n + j], t);
+    return s + t;
+  }
+};
+
+// ------------------------------------------------------------------ reductions
+template <typename T> __device__ __forceinline__ T shfl_xor(T v, int m);
+template <> __device__ __forceinline__ double shfl_xor<double>(double v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+template <> __device__ __forceinline__ cplx shfl_xor<cplx>(cplx v, int m) {
+  return mk(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
+}
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = add(v, shfl_xor(v, o));
+  return v;
+}
+
+// (bits, index) argmax: larger bits win, ties go to the smaller index.
+__device__ __forceinline__ void argmax_merge(long long& b, int& i, long long ob, int oi) {
+  if (ob > b || (ob == b && oi < i)) {
+    b = ob;
+    i = oi;
+  }
+}
+__device__ __forceinline__ void warp_argmax(long long& b, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+    int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    argmax_merge(b, i, ob, oi);
+  }
+}
+
+// Device status word values (first error wins).
+enum DevStatus : int {
+  DS_OK = 0,
+  DS_RANK_CAPACITY = 2,
+  DS_TIMEOUT = 4,
+  DS_NUMERICAL = 6,
+};
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+}  // namespace hbaca

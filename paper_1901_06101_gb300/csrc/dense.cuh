@@ -1,0 +1,517 @@
+// Re-compression and hierarchical merge (Sec. 3.2 last paragraph; Alg. 3,
+// Eqs. columncomb, columnsvdmerge) as batched kernels.
+//
+// Every task is "truncated SVD of a product whose factors are known":
+//   LEAF   U V            : QR(U) = Q_A R_A, QR(V^H) = Q_B R_B, core M = R_A R_B^H
+//   HORIZ  [U1 S1, U2 S2] diag(V1, V2)   : QR of the stacked U side, core M = R_A
+//   VERT   diag(U1, U2) [S1 V1; S2 V2]   : QR of the stacked V^H side, core M = R_A
+// SVD(M) = X S Y^H by one-sided Jacobi; s = eps-rank (Sec. 2); the Q side is
+// Q_A [X_s; 0] and the other side is Q_B [Y_s; 0] (LEAF) or the block-diagonal
+// factor times Y_s (HORIZ: V = Y_s^H diag(V1, V2); VERT: U = diag(U1, U2) Y_s).
+// For the merges this is SVD(U_bar, eps) computed as QR followed by the SVD of
+// the triangular factor, which equals the paper's SVD of the stacked factor.
+//
+// Tasks read their ranks from device memory, so a whole level is launched
+// without a host round trip.  QR, Jacobi and Q-application kernels run one
+// thread-block cluster per task; partial sums are combined across the cluster
+// through distributed shared memory in a fixed order, so every CTA holds
+// bit-identical reflector coefficients.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <climits>
+
+#include "common.cuh"
+#include "types.h"
+
+namespace cg = cooperative_groups;
+
+namespace hbaca {
+
+constexpr int kDenseThreads = 256;
+
+
+
+
+
+template <typename T>
+struct DenseParams {
+  const SvdTask* tasks;
+  TaskDims* dims;
+  int ntasks;
+  // BACA arenas and leaf table (LEAF tasks)
+  T* Uar;
+  T* Var;
+  const int32_t* leaf_rank;  // stride leaf_rank_stride ints (LeafOut.rank)
+  int leaf_rank_stride;
+  // input / output block stores
+  const BlockRef* in_blocks;
+  const int32_t* in_rank;
+  T* inU;
+  const double* inS;
+  T* inV;
+  const BlockRef* out_blocks;
+  int32_t* out_rank;
+  T* outU;
+  double* outS;
+  T* outV;
+  int64_t out_cap;     // rank capacity of output blocks
+  // scratch
+  T* qr;               // QR arena (operand B of LEAF tasks, stacked operands of merges)
+  T* tau;
+  T* core;             // M and Y matrices
+  int32_t* ord;        // per-task column order after Jacobi
+  int* status;
+  double eps;
+};
+
+template <typename T>
+__device__ __forceinline__ T* qr_a_ptr(const DenseParams<T>& P, const SvdTask& t) {
+  return (t.a_in_baca ? P.Uar : P.qr) + t.a_off;
+}
+
+// ------------------------------------------------------------------ pack
+// Build the QR operands and the task dimensions.
+template <typename T>
+__global__ void pack_kernel(const DenseParams<T> P) {
+  const int ti = blockIdx.y;
+  if (ti >= P.ntasks) return;
+  const SvdTask t = P.tasks[ti];
+  int k = 0;
+  if (t.kind == TASK_LEAF) {
+    k = P.leaf_rank[(size_t)t.in1 * P.leaf_rank_stride];
+    if (k < 0 || k > t.kcap) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(P.status, DS_RANK_CAPACITY);
+      k = 0;
+    }
+    // B = V^H (rows_b x k): B(j, p) = conj(V(p, j)); the leaf V (k x n, ld n)
+    // and B (n x k, ld n) share the index p * n + j
+    const T* V = P.Var + t.src_v_off;
+    T* B = P.qr + t.b_off;
+    const int64_t tot = (int64_t)t.rows_b * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t j = e % t.rows_b, p = e / t.rows_b;
+      B[p * t.rows_b + j] = conj_(V[p * t.rows_b + j]);
+    }
+  } else {
+    const BlockRef b1 = P.in_blocks[t.in1], b2 = P.in_blocks[t.in2];
+    const int r1 = P.in_rank[b1.rank_slot], r2 = P.in_rank[b2.rank_slot];
+    k = r1 + r2;
+    if (k > t.kcap) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(P.status, DS_RANK_CAPACITY);
+      k = 0;
+    }
+    T* A = P.qr + t.a_off;
+    const int rows = t.rows_a;
+    const int64_t tot = (int64_t)rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e % rows, p = e / rows;
+      const BlockRef& b = p < r1 ? b1 : b2;
+      const int64_t pp = p < r1 ? p : p - r1;
+      const double sg = P.inS[b.s_off + pp];
+      T v;
+      if (t.kind == TASK_HORIZ) v = P.inU[b.u_off + pp * b.ldu + i];    // [U1 S1, U2 S2]
+      else v = conj_(P.inV[b.v_off + pp * b.ldv + i]);                  // [V1^H S1, V2^H S2]
+      A[p * t.lda + i] = scale(v, sg);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    TaskDims dm;
+    dm.k = k;
+    dm.kra = min(t.rows_a, k);
+    dm.krb = t.kind == TASK_LEAF ? min(t.rows_b, k) : 0;
+    dm.s = 0;
+    P.dims[ti] = dm;
+  }
+}
+
+// ------------------------------------------------------------------ QR
+// Householder QR (LAPACK geqr2 convention) of a rows x k column-major matrix,
+// in place: R in the upper triangle (diagonal = beta), reflector tails below,
+// tau[j].  One cluster per matrix; CTA q owns a contiguous slice of rows.
+// Per column: one pass forms the partial squared tail norm, the partial
+// inner products of the tail with every trailing column and the head row;
+// one cluster barrier; every CTA combines the partials in rank order.
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> P, const QrJob* jobs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
+  const int job = blockIdx.x / c;
+  const QrJob jb = jobs[job];
+  const SvdTask t = P.tasks[jb.task];
+  const TaskDims dm = P.dims[jb.task];
+  const int k = dm.k;
+  const int rows = jb.which ? t.rows_b : t.rows_a;
+  T* A = jb.which ? P.qr + t.b_off : qr_a_ptr(P, t);
+  const int64_t lda = jb.which ? (int64_t)t.rows_b : t.lda;
+  T* tau = P.tau + t.tau_off + (jb.which ? t.kcap : 0);
+  const int kk = min(rows, k);
+  if (kk <= 0) return;
+  const int chunk = (rows + c - 1) / c;
+  const int ra = min(rows, q * chunk), rb = min(rows, ra + chunk);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // partial buffer (double-buffered): [0] sig2 (re), [1] alpha, [2 + l] dot_l, [2 + kcap + l] head row value
+  const int plen = 2 + 2 * t.kcap;
+  T* part = reinterpret_cast<T*>(smem_raw);
+  T* tot = part + 2 * plen;
+  T* coef = tot + plen;  // [0] conj(tau), [1] sc, [2] beta (re), [3] tau
+  for (int j = 0; j < kk; ++j) {
+    T* pb = part + (j & 1) * plen;
+    const int i0 = max(ra, j + 1);
+    const int ncol = k - j;  // column j and trailing ones
+    for (int l = warp; l < ncol; l += nw) {
+      const T* colj = A + (int64_t)j * lda;
+      const T* coll = A + (int64_t)(j + l) * lda;
+      T acc = Traits<T>::zero();
+      for (int i = i0 + lane; i < rb; i += 32) acc = cmac(acc, colj[i], coll[i]);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        if (l == 0) pb[0] = acc;
+        else pb[2 + (l - 1)] = acc;
+        const bool own = (j >= ra && j < rb);
+        if (l == 0) pb[1] = own ? A[(int64_t)j * lda + j] : Traits<T>::zero();
+        else pb[2 + t.kcap + (l - 1)] = own ? A[(int64_t)(j + l) * lda + j] : Traits<T>::zero();
+      }
+    }
+    __syncthreads();
+    cl.sync();
+    for (int e = tid; e < 2 * ncol; e += blockDim.x) {
+      const int idx = e < ncol ? (e == 0 ? 0 : 2 + (e - 1)) : (e == ncol ? 1 : 2 + t.kcap + (e - ncol - 1));
+      T s = Traits<T>::zero();
+      for (int r = 0; r < c; ++r) {
+        const T* rp = cl.map_shared_rank(part + (j & 1) * plen, r);
+        s = add(s, rp[idx]);
+      }
+      tot[idx] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double beta;
+      T tu, sc;
+      householder(tot[1], re_(tot[0]), beta, tu, sc);
+      coef[0] = conj_(tu);
+      coef[1] = sc;
+      coef[2] = from_re<T>(beta);
+      coef[3] = tu;
+      if (q == 0) tau[j] = tu;
+    }
+    __syncthreads();
+    const T ctau = coef[0], sc = coef[1];
+    const T csc = conj_(sc);
+    // w_l = a_jl + conj(sc) dot_l ; A(i, l) -= conj(tau) * (x_i sc) * w_l ; head row: A(j, l) -= conj(tau) w_l
+    for (int l = 1; l < ncol; ++l) {
+      const T w = mac(tot[2 + t.kcap + (l - 1)], csc, tot[2 + (l - 1)]);
+      const T f = mul(ctau, w);
+      T* coll = A + (int64_t)(j + l) * lda;
+      const T* colj = A + (int64_t)j * lda;
+      for (int i = i0 + tid; i < rb; i += blockDim.x) coll[i] = msub(coll[i], mul(colj[i], sc), f);
+      if (tid == 0 && j >= ra && j < rb) coll[j] = sub(coll[j], f);
+    }
+    __syncthreads();
+    {
+      T* colj = A + (int64_t)j * lda;
+      for (int i = i0 + tid; i < rb; i += blockDim.x) colj[i] = mul(colj[i], sc);
+      if (tid == 0 && j >= ra && j < rb) colj[j] = coef[2];
+    }
+    __syncthreads();
+  }
+  cl.sync();
+}
+
+// ------------------------------------------------------------------ core
+// M = R_A R_B^H (LEAF, kra x krb) or M = R_A (merges, kra x k), column-major ld kcap.
+template <typename T>
+__global__ void core_kernel(const DenseParams<T> P) {
+  const int ti = blockIdx.y;
+  const SvdTask t = P.tasks[ti];
+  const TaskDims dm = P.dims[ti];
+  T* M = P.core + t.m_off;
+  const T* A = qr_a_ptr(P, t);
+  const int kra = dm.kra;
+  if (t.kind == TASK_LEAF) {
+    const T* B = P.qr + t.b_off;
+    const int krb = dm.krb, k = dm.k;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kra * krb; e += gridDim.x * blockDim.x) {
+      const int i = e % kra, j = e / kra;
+      T s = Traits<T>::zero();
+      for (int p = max(i, j); p < k; ++p) s = mac(s, A[(int64_t)p * t.lda + i], conj_(B[(int64_t)p * t.rows_b + j]));
+      M[(int64_t)j * t.kcap + i] = s;
+    }
+  } else {
+    const int k = dm.k;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kra * k; e += gridDim.x * blockDim.x) {
+      const int i = e % kra, j = e / kra;
+      M[(int64_t)j * t.kcap + i] = (i <= j) ? A[(int64_t)j * t.lda + i] : Traits<T>::zero();
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi SVD
+// One-sided Jacobi (Hestenes) on M (mr x nc): M Y = X S.  Round-robin pairs;
+// per pair the warp forms alpha = |a|^2, beta = |b|^2, gamma = a^H b and
+// rotates [a, e^{-i phi} b] by the real angle that zeroes their inner product,
+// accumulating the same rotation in Y.  The pairs of one round are spread over
+// all warps of all CTAs in the cluster; a cluster barrier separates rounds.
+// At the end singular values are column norms, sorted descending; s = eps-rank.
+template <typename T>
+__device__ __forceinline__ void rotate_pair(T* a, T* b, int len, double cs, double sn, T ph, int lane) {
+  // a' = c a - s ph b ; b' = s a + c ph b     (ph = e^{-i phi})
+  for (int i = lane; i < len; i += 32) {
+    const T ai = ldcg(a + i);
+    const T bi = mul(ph, ldcg(b + i));
+    a[i] = sub(scale(ai, cs), scale(bi, sn));
+    b[i] = add(scale(ai, sn), scale(bi, cs));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams<T> P, int max_sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
+  const int ti = blockIdx.x / c;
+  const SvdTask t = P.tasks[ti];
+  const TaskDims dm = P.dims[ti];
+  const int mr = dm.kra;
+  const int nc = t.kind == TASK_LEAF ? dm.krb : dm.k;
+  T* M = P.core + t.m_off;
+  T* Y = P.core + t.y_off;
+  const int ld = t.kcap;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int* flag = reinterpret_cast<int*>(smem_raw);  // [0..1] rotation-applied flags (double-buffered)
+  double* sv = reinterpret_cast<double*>(smem_raw + 16);  // nc singular values (CTA 0, sorting)
+  if (mr <= 0 || nc <= 0) {
+    if (q == 0 && tid == 0) {
+      P.dims[ti].s = 0;
+      P.out_rank[P.out_blocks[t.out].rank_slot] = 0;
+    }
+    return;
+  }
+  // Y = I
+  {
+    const int per = (nc + c - 1) / c;
+    const int j0 = q * per, j1 = min(nc, j0 + per);
+    for (int j = j0; j < j1; ++j)
+      for (int i = tid; i < nc; i += blockDim.x) Y[(int64_t)j * ld + i] = from_re<T>(i == j ? 1.0 : 0.0);
+  }
+  const int K = nc + (nc & 1);
+  const double tol = 4.0e-16 * (double)max(mr, 8);
+  int sweep = 0;
+  unsigned fb = 0;
+  if (tid == 0) { flag[0] = 0; flag[1] = 0; }
+  cl.sync();
+  for (; sweep < max_sweeps && K > 1; ++sweep) {
+    if (tid == 0) flag[fb & 1] = 0;
+    __syncthreads();
+    for (int rd = 0; rd < K - 1; ++rd) {
+      // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
+      for (int pi = q * nw + warp; pi < K / 2; pi += c * nw) {
+        int a, b;
+        if (pi == 0) { a = rd; b = K - 1; }
+        else { a = (rd + pi) % (K - 1); b = (rd - pi + K - 1) % (K - 1); }
+        if (a > b) { int tmp = a; a = b; b = tmp; }
+        if (b >= nc) continue;  // padding column
+        T* ca = M + (int64_t)a * ld;
+        T* cb = M + (int64_t)b * ld;
+        double al = 0.0, be = 0.0;
+        T ga = Traits<T>::zero();
+        for (int i = lane; i < mr; i += 32) {
+          const T xa = ldcg(ca + i), xb = ldcg(cb + i);
+          al += abs2(xa);
+          be += abs2(xb);
+          ga = cmac(ga, xa, xb);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        // columns whose squared norm is in the denormal range count as zero
+        const double g = absval(ga);
+        if (g == 0.0 || al < 1e-290 || be < 1e-290 || g <= tol * sqrt(al) * sqrt(be)) continue;
+        const double zeta = (be - al) / (2.0 * g);
+        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        const T ph = conj_phase(ga, g);  // e^{-i phi} exactly unit, gamma = |gamma| e^{i phi}
+        rotate_pair(ca, cb, mr, cs, sn, ph, lane);
+        rotate_pair(Y + (int64_t)a * ld, Y + (int64_t)b * ld, nc, cs, sn, ph, lane);
+        if (lane == 0) flag[fb & 1] = 1;
+      }
+      __syncthreads();
+      cl.sync();
+    }
+    // any rotation anywhere in the cluster this sweep?
+    int any = 0;
+    for (int r = 0; r < c; ++r) any |= *cl.map_shared_rank(&flag[fb & 1], r);
+    ++fb;
+    cl.sync();
+    if (!any) break;
+  }
+  // singular values and their order (CTA 0); then every CTA normalises a
+  // share of the kept columns of M in place (X = M / sigma) and writes S
+  int* ord = reinterpret_cast<int*>(sv + nc);
+  int* sshare = ord + nc;
+  if (q == 0) {
+    for (int j = warp; j < nc; j += nw) {
+      double s = 0.0;
+      for (int i = lane; i < mr; i += 32) s += abs2(ldcg(M + (int64_t)j * ld + i));
+      s = warp_sum(s);
+      if (lane == 0) sv[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = tid; j < nc; j += blockDim.x) {  // rank by (value desc, index asc)
+      int rk = 0;
+      const double vj = sv[j];
+      for (int i = 0; i < nc; ++i) rk += (sv[i] > vj) || (sv[i] == vj && i < j);
+      ord[rk] = j;
+    }
+    __syncthreads();
+    for (int j = tid; j < nc; j += blockDim.x) P.ord[t.ord_off + j] = ord[j];
+    if (tid == 0) {
+      const double s1 = sv[ord[0]];
+      int s = 0;
+      if (s1 > 0.0 && isfinite(s1))
+        while (s < nc && s < mr && sv[ord[s]] >= P.eps * s1) ++s;
+      if (!isfinite(s1)) set_status(P.status, DS_NUMERICAL);
+      if (s > P.out_cap) { set_status(P.status, DS_RANK_CAPACITY); s = (int)P.out_cap; }
+      sshare[0] = s;
+      P.dims[ti].s = s;
+      const BlockRef ob = P.out_blocks[t.out];
+      P.out_rank[ob.rank_slot] = s;
+    }
+  }
+  cl.sync();
+  {
+    const double* sv0 = cl.map_shared_rank(sv, 0);
+    const int* ord0 = cl.map_shared_rank(ord, 0);
+    const int s = *cl.map_shared_rank(sshare, 0);
+    const BlockRef ob = P.out_blocks[t.out];
+    for (int tc = q * nw + warp; tc < s; tc += c * nw) {
+      const int j = ord0[tc];
+      const double sg = sv0[j];
+      const double inv = 1.0 / sg;
+      for (int i = lane; i < mr; i += 32) M[(int64_t)j * ld + i] = scale(ldcg(M + (int64_t)j * ld + i), inv);
+      if (lane == 0) P.outS[ob.s_off + tc] = sg;
+    }
+  }
+  cl.sync();
+}
+
+// ------------------------------------------------------------------ Q application
+// D = Q [Z; 0] with Q = H_0 H_1 ... H_{kk-1} from qr_kernel (Z = X_s for the A
+// side, Y_s for the B side), written to an output block: U side stored
+// column-major, V side stored as V = D^H (row-major).  Reflectors are applied
+// from the last to the first; each needs w = u^H D (cluster-wide partial sums
+// combined through DSMEM) and a rank-1 update of this CTA's rows.
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams<T> P, const QJob* jobs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
+  const QJob jb = jobs[blockIdx.x / c];
+  const SvdTask t = P.tasks[jb.task];
+  const TaskDims dm = P.dims[jb.task];
+  const int s = dm.s;
+  const int rows = jb.which ? t.rows_b : t.rows_a;
+  const int kk = jb.which ? dm.krb : dm.kra;
+  const T* A = jb.which ? P.qr + t.b_off : qr_a_ptr(P, t);
+  const int64_t lda = jb.which ? (int64_t)t.rows_b : t.lda;
+  const T* tau = P.tau + t.tau_off + (jb.which ? t.kcap : 0);
+  const T* Z = P.core + (jb.which ? t.y_off : t.m_off);  // column ord[tc] holds Z(:, tc)
+  const int32_t* ord = P.ord + t.ord_off;
+  const BlockRef ob = P.out_blocks[t.out];
+  T* D = jb.to_v ? P.outV + ob.v_off : P.outU + ob.u_off;
+  const int64_t ldd = jb.to_v ? ob.ldv : ob.ldu;
+  if (s <= 0) return;
+  const int chunk = (rows + c - 1) / c;
+  const int ra = min(rows, q * chunk), rb = min(rows, ra + chunk);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  T* part = reinterpret_cast<T*>(smem_raw);  // 2 x s partials
+  T* wv = part + 2 * s;                       // s combined
+  for (int tc = 0; tc < s; ++tc)
+    for (int i = ra + tid; i < rb; i += blockDim.x)
+      D[(int64_t)tc * ldd + i] = i < kk ? Z[(int64_t)ord[tc] * t.kcap + i] : Traits<T>::zero();
+  __syncthreads();
+  for (int j = kk - 1; j >= 0; --j) {
+    T* pb = part + (j & 1) * s;
+    const T tj = tau[j];
+    const int i0 = max(ra, j);
+    for (int tc = warp; tc < s; tc += nw) {
+      T acc = Traits<T>::zero();
+      for (int i = i0 + lane; i < rb; i += 32) {
+        const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];
+        acc = cmac(acc, u, D[(int64_t)tc * ldd + i]);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) pb[tc] = acc;
+    }
+    __syncthreads();
+    cl.sync();
+    for (int tc = tid; tc < s; tc += blockDim.x) {
+      T sum = Traits<T>::zero();
+      for (int r = 0; r < c; ++r) sum = add(sum, cl.map_shared_rank(part + (j & 1) * s, r)[tc]);
+      wv[tc] = mul(tj, sum);
+    }
+    __syncthreads();
+    for (int tc = 0; tc < s; ++tc) {
+      const T f = wv[tc];
+      for (int i = i0 + tid; i < rb; i += blockDim.x) {
+        const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];
+        D[(int64_t)tc * ldd + i] = msub(D[(int64_t)tc * ldd + i], u, f);
+      }
+    }
+    __syncthreads();
+  }
+  if (jb.to_v)
+    for (int tc = 0; tc < s; ++tc)
+      for (int i = ra + tid; i < rb; i += blockDim.x) D[(int64_t)tc * ldd + i] = conj_(D[(int64_t)tc * ldd + i]);
+  cl.sync();
+}
+
+// ------------------------------------------------------------------ block-diagonal side
+// HORIZ: V_out = Y_s^H diag(V1, V2); VERT: U_out = diag(U1, U2) Y_s.
+template <typename T>
+__global__ void blockprod_kernel(const DenseParams<T> P) {
+  const int ti = blockIdx.y;
+  const SvdTask t = P.tasks[ti];
+  if (t.kind == TASK_LEAF) return;
+  const TaskDims dm = P.dims[ti];
+  const int s = dm.s;
+  const BlockRef b1 = P.in_blocks[t.in1], b2 = P.in_blocks[t.in2];
+  const int r1 = P.in_rank[b1.rank_slot], r2 = P.in_rank[b2.rank_slot];
+  const BlockRef ob = P.out_blocks[t.out];
+  const T* Y = P.core + t.y_off;
+  const int32_t* ord = P.ord + t.ord_off;
+  if (t.kind == TASK_HORIZ) {
+    const int n1 = b1.n, ntot = b1.n + b2.n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)ntot * s; e += (int64_t)gridDim.x * blockDim.x) {
+      const int j = (int)(e % ntot), tc = (int)(e / ntot);
+      T acc = Traits<T>::zero();
+      if (j < n1) {
+        const T* ys = Y + (int64_t)ord[tc] * t.kcap;
+        for (int p = 0; p < r1; ++p) acc = cmac(acc, ys[p], P.inV[b1.v_off + (int64_t)p * b1.ldv + j]);
+      } else {
+        const T* ys = Y + (int64_t)ord[tc] * t.kcap + r1;
+        for (int p = 0; p < r2; ++p) acc = cmac(acc, ys[p], P.inV[b2.v_off + (int64_t)p * b2.ldv + (j - n1)]);
+      }
+      P.outV[ob.v_off + (int64_t)tc * ob.ldv + j] = acc;
+    }
+  } else {
+    const int m1 = b1.m, mtot = b1.m + b2.m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)mtot * s; e += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(e % mtot), tc = (int)(e / mtot);
+      T acc = Traits<T>::zero();
+      if (i < m1) {
+        const T* ys = Y + (int64_t)ord[tc] * t.kcap;
+        for (int p = 0; p < r1; ++p) acc = mac(acc, P.inU[b1.u_off + (int64_t)p * b1.ldu + i], ys[p]);
+      } else {
+        const T* ys = Y + (int64_t)ord[tc] * t.kcap + r1;
+        for (int p = 0; p < r2; ++p) acc = mac(acc, P.inU[b2.u_off + (int64_t)p * b2.ldu + (i - m1)], ys[p]);
+      }
+      P.outU[ob.u_off + (int64_t)tc * ob.ldu + i] = acc;
+    }
+  }
+}
+
+}  // namespace hbaca

@@ -1,0 +1,203 @@
+// Launch sequence of one H-BACA call for scalar type T: the persistent leaf
+// BACA kernel, the leaf re-compression stage, then for every level l = 1..L
+// the horizontal stage (step l - 1/2) and the vertical stage (step l) of
+// Alg. 3.  All launches go to one stream; task sizes live on the device.
+#pragma once
+
+#include <string>
+
+#include "baca.cuh"
+#include "dense.cuh"
+#include "plan.h"
+#include "run.h"
+
+namespace hbaca {
+
+#define HB_TRY(call)                                                              \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+      return e_;                                                                  \
+    }                                                                             \
+  } while (0)
+
+template <typename K, typename... Args>
+cudaError_t launch_cluster(K kern, int grid, int cluster, size_t smem, cudaStream_t st, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (cluster > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kDenseThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+inline int pick_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
+  int c = 1;
+  while (c < 16 && (int64_t)jobs * c < 2 * sms && rows / (2 * c) >= min_rows_per_cta) c *= 2;
+  return c;
+}
+
+template <typename Gen>
+cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
+  using T = typename Gen::scalar;
+  char* ws = rc.ws;
+  BacaParams<Gen> P;
+  P.gen = gen;
+  P.leaves = reinterpret_cast<const LeafDesc*>(ws + p.desc_region.off + p.leafdesc_off);
+  P.out = reinterpret_cast<LeafOut*>(ws + p.leafout_off);
+  P.nleaves = p.nleaves;
+  P.queue = reinterpret_cast<int*>(ws + p.queue.off);
+  P.status = reinterpret_cast<int*>(ws + p.status.off);
+  P.Uar = reinterpret_cast<T*>(ws + p.uar.off);
+  P.Var = reinterpret_cast<T*>(ws + p.var.off);
+  P.Cscr = reinterpret_cast<T*>(ws + p.cscr.off);
+  P.Rscr = reinterpret_cast<T*>(ws + p.rscr.off);
+  P.Gscr = reinterpret_cast<T*>(ws + p.gscr.off);
+  P.cscr_stride = p.cscr_stride;
+  P.rscr_stride = p.rscr_stride;
+  P.gscr_stride = p.gscr_stride;
+  P.tape_int = reinterpret_cast<int32_t*>(ws + p.tape_int.off);
+  P.tape_dbl = reinterpret_cast<double*>(ws + p.tape_dbl.off);
+  P.eps = p.opts.eps;
+  P.d = p.d;
+  P.seed = p.opts.seed;
+  P.mr_max = p.mr_max;
+  P.nc_max = p.nc_max;
+  P.rcap_max = p.rcap_max;
+  auto kern = baca_leaf_kernel<Gen>;
+  const int c = p.baca_cluster;
+  HB_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.baca_smem));
+  if (c > 8) HB_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c, 1, 1);
+  cfg.blockDim = dim3(kBacaThreads, 1, 1);
+  cfg.dynamicSmemBytes = p.baca_smem;
+  cfg.stream = rc.st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  HB_TRY(cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg));
+  if (ncl < 1) {
+    err = "BACA kernel cannot be made resident (cluster " + std::to_string(c) + ", smem " + std::to_string(p.baca_smem) + ")";
+    return cudaErrorInvalidConfiguration;
+  }
+  int nclusters = std::min(std::min(p.nleaves, ncl), p.max_clusters_scratch);
+  p.baca_clusters = nclusters;
+  cfg.gridDim = dim3(nclusters * c, 1, 1);
+  HB_TRY(cudaLaunchKernelEx(&cfg, kern, P));
+  ++rc.launches;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
+  char* ws = rc.ws;
+  char* desc = ws + p.desc_region.off;
+  DenseParams<T> D;
+  D.tasks = reinterpret_cast<const SvdTask*>(desc + sg.tasks_off);
+  D.dims = reinterpret_cast<TaskDims*>(ws + sg.dims_off);
+  D.ntasks = sg.ntasks;
+  D.Uar = reinterpret_cast<T*>(ws + p.uar.off);
+  D.Var = reinterpret_cast<T*>(ws + p.var.off);
+  D.leaf_rank = reinterpret_cast<const int32_t*>(ws + p.leafout_off);
+  D.leaf_rank_stride = (int)(sizeof(LeafOut) / sizeof(int32_t));
+  auto store = [&](int id, int level, const BlockRef*& refs, int32_t*& rank, T*& U, double*& S, T*& V) {
+    if (id == 0) {
+      refs = reinterpret_cast<const BlockRef*>(desc + p.full_lv[level].refs_off);
+      rank = reinterpret_cast<int32_t*>(ws + p.full_lv[level].rank_off);
+      U = reinterpret_cast<T*>(ws + p.full_u.off);
+      S = reinterpret_cast<double*>(ws + p.full_s.off);
+      V = reinterpret_cast<T*>(ws + p.full_v.off);
+    } else if (id == 1) {
+      refs = reinterpret_cast<const BlockRef*>(desc + p.half_lv[level].refs_off);
+      rank = reinterpret_cast<int32_t*>(ws + p.half_lv[level].rank_off);
+      U = reinterpret_cast<T*>(ws + p.half_u.off);
+      S = reinterpret_cast<double*>(ws + p.half_s.off);
+      V = reinterpret_cast<T*>(ws + p.half_v.off);
+    } else {
+      refs = reinterpret_cast<const BlockRef*>(desc + p.user_ref_off);
+      rank = reinterpret_cast<int32_t*>(ws + p.user_lv.rank_off);
+      U = reinterpret_cast<T*>(rc.res->U);
+      S = rc.res->S;
+      V = reinterpret_cast<T*>(rc.res->V);
+    }
+  };
+  {
+    const BlockRef* r = nullptr;
+    int32_t* rk = nullptr;
+    T *U = nullptr, *V = nullptr;
+    double* S = nullptr;
+    if (sg.in_store >= 0) store(sg.in_store, sg.in_level, r, rk, U, S, V);
+    D.in_blocks = r;
+    D.in_rank = rk;
+    D.inU = U;
+    D.inS = S;
+    D.inV = V;
+    store(sg.out_store, sg.out_level, r, rk, U, S, V);
+    D.out_blocks = r;
+    D.out_rank = rk;
+    D.outU = U;
+    D.outS = S;
+    D.outV = V;
+  }
+  D.out_cap = p.rank_cap;
+  D.qr = reinterpret_cast<T*>(ws + p.qr.off);
+  D.tau = reinterpret_cast<T*>(ws + p.tau.off);
+  D.core = reinterpret_cast<T*>(ws + p.core.off);
+  D.ord = reinterpret_cast<int32_t*>(ws + p.ord.off);
+  D.status = reinterpret_cast<int*>(ws + p.status.off);
+  D.eps = p.opts.eps;
+  const int nt = sg.ntasks;
+  const QrJob* qj = reinterpret_cast<const QrJob*>(desc + sg.qrjobs_off);
+  const QJob* aj = reinterpret_cast<const QJob*>(desc + sg.qjobs_off);
+
+  pack_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D);
+  HB_TRY(cudaGetLastError());
+  const int cq = pick_cluster(sg.nqr, sg.rows_max, rc.sms, 64);
+  const size_t qr_smem = (size_t)(3 * (2 + 2 * sg.kcap) + 4) * sizeof(T);
+  HB_TRY(launch_cluster(qr_kernel<T>, sg.nqr * cq, cq, qr_smem, rc.st, D, qj));
+  core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D);
+  HB_TRY(cudaGetLastError());
+  const int cj = pick_cluster(nt, sg.kcap, rc.sms, 16);
+  const size_t j_smem = 16 + (size_t)sg.kcap * 12 + 64;
+  HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_smem, rc.st, D, 40));
+  const size_t qa_smem = (size_t)3 * p.rank_cap * sizeof(T) + 64;
+  HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj));
+  rc.launches += 5;
+  if (sg.kind != TASK_LEAF) {
+    blockprod_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D);
+    HB_TRY(cudaGetLastError());
+    ++rc.launches;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t run_stages(Plan& p, RunCtx& rc, std::string& err) {
+  for (const Stage& sg : p.stages) {
+    cudaError_t e = run_stage<T>(p, sg, rc, err);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace hbaca

@@ -1,0 +1,20 @@
+// Entry points of the two scalar-type translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "plan.h"
+
+namespace hbaca {
+struct RunCtx {
+  char* ws;
+  cudaStream_t st;
+  int sms;
+  const hbaca_result* res;
+  int launches = 0;  // kernels launched by the call
+};
+cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
+cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);
+}  // namespace hbaca

@@ -1,0 +1,86 @@
+// Plain descriptor structs shared by the host planner and the kernels.
+#pragma once
+
+#include <stdint.h>
+
+namespace hbaca {
+
+struct LeafDesc {
+  int64_t row0, col0;     // global offsets of the leaf
+  int32_t m, n;           // leaf size
+  int32_t rcap;           // BACA rank capacity of this leaf
+  int32_t tape_iters;     // iteration capacity of the tape
+  int64_t stream_id;      // counter-based stream of J_1
+  int64_t u_off, v_off;   // element offsets of U (m x rcap, ld m) and V (rcap x n, ld n)
+  int64_t tape_off;       // int offset into tape_int (records of 4 + 3d ints)
+  int64_t taped_off;      // double offset into tape_dbl (records of 2 doubles)
+};
+
+struct LeafOut {
+  int32_t rank, iters, stop, status;
+  double mu;
+};
+
+enum StopReason : int {
+  STOP_CONVERGED = 0,
+  STOP_ITERS = 1,
+  STOP_NO_COLS = 2,
+  STOP_NO_ROWS = 3,
+  STOP_CAPACITY = 4,
+  STOP_NUMERICAL = 5,
+};
+
+enum TaskKind : int { TASK_LEAF = 0, TASK_HORIZ = 1, TASK_VERT = 2 };
+
+// A stored low-rank block U diag(S) V (U column-major ld m, V row-major ld n).
+struct BlockRef {
+  int64_t u_off, s_off, v_off;  // element offsets (U, V: scalars; S: doubles)
+  int64_t ldu, ldv;             // U column-major (ld >= m), V row-major (ld >= n)
+  int32_t m, n;
+  int32_t rank_slot;            // index into the rank array of its store
+  int32_t pad;
+};
+
+struct SvdTask {
+  int32_t kind;
+  int32_t kcap;        // capacity of k (columns of the QR operand)
+  // inputs (LEAF: leaf index into the BACA arenas; merges: blocks of the input store)
+  int32_t in1, in2;
+  // QR operand A: rows_a x k, column-major, ld = lda (LEAF: the BACA U arena in place)
+  int64_t a_off;       // offset in the arena selected by a_in_baca
+  int32_t rows_a, a_in_baca;
+  int64_t lda;
+  // QR operand B (LEAF only): rows_b x k, column-major (V^H), in the QR arena
+  int64_t b_off;
+  int32_t rows_b, pad0;
+  int64_t src_v_off;   // LEAF: offset of the leaf's V (k x rows_b, row-major) in the BACA V arena
+  int64_t tau_off;     // 2 * kcap scalars
+  int64_t m_off;       // core M: kcap x kcap, column-major ld kcap; after Jacobi its
+                       // columns hold X (normalised), in unsorted order
+  int64_t y_off;       // Y: kcap x kcap, column-major ld kcap
+  int64_t ord_off;     // kcap ints: column order by descending singular value
+  int32_t out;         // block index in the output store
+  int32_t m1;          // HORIZ / VERT: rows (VERT) or columns (HORIZ) of the first child
+};
+
+// Device-side per-task sizes written by the kernels.
+struct TaskDims {
+  int32_t k;    // columns of the QR operand(s) (LEAF: BACA rank; merges: r1 + r2)
+  int32_t kra;  // rows of R_A = min(rows_a, k)
+  int32_t krb;  // rows of R_B (LEAF) = min(rows_b, k)
+  int32_t s;    // truncated rank
+};
+
+struct QrJob {
+  int32_t task;
+  int32_t which;  // 0: operand A, 1: operand B
+};
+
+struct QJob {
+  int32_t task;
+  int32_t which;   // 0: operand A with X_s, 1: operand B with Y_s
+  int32_t to_v;    // 1: the result is stored as V = D^H in the output block
+  int32_t pad;
+};
+
+}  // namespace hbaca

@@ -1,0 +1,91 @@
+"""Comparison of GPU leaf records with the oracle's, following the parity
+rule: pivot sequences and ranks must be identical while every decision is
+unique by a relative margin of 1e-9; after the first sub-margin decision a
+leaf is only compared through ranks (+-2) and errors."""
+import numpy as np
+
+MARGIN = 1e-9
+
+
+def _prefix_ok(margins):
+    """Number of leading decisions with a unique margin."""
+    n = 0
+    for m in margins:
+        if not (m > MARGIN):
+            break
+        n += 1
+    return n
+
+
+def compare_leaf(o, g, eps):
+    """o: oracle baca() dict, g: binding.read_leaf_trace() dict.
+    Returns (iterations compared, diverged flag)."""
+    ot, gt = o["trace"], g["trace"]
+    for k in range(min(len(ot), len(gt))):
+        a, b = ot[k], gt[k]
+        assert a["J"] == b["J"], ("J", k, a["J"], b["J"])
+        nI = _prefix_ok(a["Imarg"])
+        assert a["I"][:nI] == b["I"][:nI], ("I", k, a["I"], b["I"])
+        if nI < len(a["I"]):
+            return k, True
+        w = a["W"]
+        nW = _prefix_ok(w["marg"])
+        assert a["jbar"][:nW] == b["jbar"][:nW], ("jbar", k, a["jbar"], b["jbar"])
+        if nW < len(a["jbar"]):
+            return k, True
+        # the eps-rank decision of QR(W, eps) is unique unless a |T_tt| sits at eps |T_11|
+        d0 = w["diag"][0] if w["diag"] else 0.0
+        tol = max(1e-6 * eps * d0, w.get("noise", 0.0))
+        near = [abs(t - eps * d0) <= tol for t in w["diag"][1:]] if d0 else []
+        if w["next"] is not None and d0:
+            near.append(abs(w["next"] - eps * d0) <= tol)
+        if any(near):
+            return k, True
+        assert a["dk"] == b["dk"], ("dk", k, a["dk"], b["dk"])
+        # nu, mu are norms of the same low-rank blocks
+        assert abs(a["mu"] - b["mu"]) <= 1e-9 * max(a["mu"], 1e-300), ("mu", k, a["mu"], b["mu"])
+        assert abs(a["nu"] - b["nu"]) <= 1e-9 * max(a["mu"], 1e-300), ("nu", k, a["nu"], b["nu"])
+        nJ = _prefix_ok(a["Jmarg"])
+        if k + 1 < len(ot) and k + 1 < len(gt):
+            assert ot[k + 1]["J"][:nJ] == gt[k + 1]["J"][:nJ], ("Jnext", k)
+        if nJ < len(a["Jnext"]):
+            return k + 1, True
+    assert len(ot) == len(gt), ("iterations", len(ot), len(gt))
+    assert o["r"] == g["rank_baca"], ("rank", o["r"], g["rank_baca"])
+    return len(ot), False
+
+
+def dense_rel_error(A, U, s, V):
+    E = A - (U * s[None, :]) @ V
+    return float(np.linalg.norm(E) / np.linalg.norm(A))
+
+
+def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid):
+    """Replay the GPU's pivot record through the oracle (frozen pivots): every
+    GPU choice must be a valid greedy choice up to rounding, and the norms and
+    ranks must agree.  Returns the replay result."""
+    from oracle import baca as ob
+    rep = ob.baca_replay(ogen_leaf, d, eps, g["trace"], seed=seed, bid=bid, stop=g["stop"])
+    noisy = [k for k, r in enumerate(rep["recs"]) if r.get("noise_level")]
+    limit = noisy[0] + 1 if noisy else len(g["trace"])
+    assert len(rep["recs"]) >= limit, ("replay stopped", len(rep["recs"]), len(g["trace"]), rep["recs"][-1])
+    rep["comparable"] = True
+    for k, (r, t) in enumerate(zip(rep["recs"], g["trace"])):
+        for key in ("J_ok", "valid_I", "valid_J", "valid_W", "valid_dk", "valid_stop"):
+            assert r[key], (key, k, g["stop"], r)
+        assert abs(r["mu"] - t["mu"]) <= 1e-9 * max(r["mu"], 1e-300), ("mu", k, r["mu"], t["mu"])
+        assert abs(r["nu"] - t["nu"]) <= 1e-9 * max(r["mu"], 1e-300), ("nu", k, r["nu"], t["nu"])
+        if r.get("noise_level"):
+            rep["comparable"] = k + 1 == len(g["trace"])
+            rep["compared_iters"] = k + 1
+            break
+    assert rep["r"] == g["rank_baca"] or not rep["comparable"]
+    return rep
+
+
+def near_threshold(s, eps, rel=1e-6):
+    """True when an eps-rank decision on singular values s is ambiguous."""
+    s = np.asarray(s)
+    if s.size == 0 or s[0] == 0:
+        return False
+    return bool(np.any(np.abs(s / s[0] - eps) <= rel * eps))

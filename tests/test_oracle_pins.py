@@ -343,3 +343,41 @@ def test_hbaca_complex_helmholtz_small():
     A = g(np.arange(g.m), np.arange(g.n))
     sv = np.linalg.svd(A, compute_uv=False)
     assert res["r"] >= int(np.sum(sv > np.linalg.norm(A - (res["U"] * res["s"]) @ res["V"], 2)))
+
+
+# ---------------------------------------------------------------- frozen-pivot replay
+@pytest.mark.parametrize("cplx", [False, True])
+def test_replay_of_own_trace_is_valid_and_identical(cplx):
+    if cplx:
+        x, y = inputs.sphere_pair(seed=4, m=160, n=150)
+        g = og.Helmholtz(x, y, 4 * np.pi)
+    else:
+        g = _gauss_small()
+    res = ob.baca(g, 6, 1e-9, seed=5)
+    rep = ob.baca_replay(g, 6, 1e-9, res["trace"], seed=5)
+    for r in rep["recs"]:
+        assert r["J_ok"] and r["valid_I"] and r["valid_J"] and r["valid_W"] and r["valid_dk"] and r["valid_stop"], r
+    assert rep["r"] == res["r"]
+    np.testing.assert_allclose(rep["U"] @ rep["V"], res["U"] @ res["V"], rtol=0, atol=1e-13)
+    for a, b in zip(rep["recs"], res["trace"]):
+        assert abs(a["nu"] - b["nu"]) <= 1e-12 * b["mu"] and abs(a["mu"] - b["mu"]) <= 1e-12 * b["mu"]
+
+
+def test_replay_flags_a_non_greedy_pivot():
+    g = _gauss_small()
+    res = ob.baca(g, 6, 1e-9, seed=5)
+    bad = [dict(t) for t in res["trace"]]
+    # swap the first two row pivots of the first iteration: the second is not the max at step 0
+    bad[0] = dict(bad[0], I=[bad[0]["I"][1], bad[0]["I"][0]] + bad[0]["I"][2:])
+    rep = ob.baca_replay(g, 6, 1e-9, bad, seed=5)
+    assert not rep["recs"][0]["valid_I"]
+    # a kept row reused later is not a candidate
+    bad = [dict(t) for t in res["trace"]]
+    bad[1] = dict(bad[1], I=[res["trace"][0]["I"][0]] + bad[1]["I"][1:])
+    rep = ob.baca_replay(g, 6, 1e-9, bad, seed=5)
+    assert not rep["recs"][1]["valid_I"]
+    # a wrong rank decision d_k is flagged
+    bad = [dict(t) for t in res["trace"]]
+    bad[0] = dict(bad[0], dk=bad[0]["dk"] - 1, jbar=bad[0]["jbar"][:-1])
+    rep = ob.baca_replay(g, 6, 1e-9, bad, seed=5)
+    assert not rep["recs"][0]["valid_dk"]
