@@ -1,0 +1,349 @@
+"""Benchmark of the H-BACA hot path on GB300.
+
+Workload (one "step"): H-BACA compression of the Helmholtz kernel matrix
+A(i, j) = exp(i k r) / r, complex128, m = n = 20000, points uniform on two unit
+spheres centred 3 apart, k = 4 pi, seed 1; block size d = 16, 16 x 16 leaves
+(L = 4), eps = 1e-4.  Inputs are synthetic (the paper's data sets are not
+available) and resident in HBM when the timed region starts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  value = matrix entries generated per second
+by the leaf BACA over the whole job; ms_per_step = device time of one
+compression (CUDA events on the launching stream).  Between timed steps L2 is
+flushed by writing a 512 MiB buffer.  With N > 1 (torchrun) every rank
+compresses its own copy of the workload (the path has no exchange between
+independent problems): weak scaling, replicas.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H-BACA compress ms & entries/s at stated ε; batched vs per-block; bwd/fwd"
+WORKLOAD = dict(workload="helmholtz_c128_20000_d16_L4_eps1e-4", kernel="helmholtz exp(ikr)/r",
+                m=20000, n=20000, k=4 * np.pi, d=16, levels=4, eps=1e-4, seed=1,
+                rank_cap=256, leaf_rank_cap=256)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ work accounting
+def leaf_spans(n, L):
+    """Leaves of the L-level index tree on [0, n) (first child ceil(s/2))."""
+    spans = [(0, n)]
+    for _ in range(L):
+        nxt = []
+        for s0, sz in spans:
+            a = (sz + 1) // 2
+            nxt += [(s0, a), (s0 + a, sz - a)]
+        spans = nxt
+    return spans
+
+
+def leaf_accounting(traces, leaf_sizes, d, complex_):
+    """Entries generated and algorithmic FP64 flops of the leaf BACA (Alg. 2)
+    from the per-leaf pivot records: per iteration with running rank r,
+    C panel m r dJ MACs, R panel dI n r, QRCP of C^t / R (3 MACs per
+    candidate component per step), V_k = T^-1 Q^H R n dk dI, Gram norms
+    (m + n)(r + dk) dk.  A complex MAC is 8 real flops, a real one 2."""
+    entries = 0
+    macs = 0
+    for tr, (m, n) in zip(traces, leaf_sizes):
+        r = 0
+        kept_r = 0
+        kept_c = 0
+        for rec in tr["trace"]:
+            dI, dJ, dk = len(rec["I"]), len(rec["J"]), rec["dk"]
+            entries += m * dJ + dI * n
+            macs += m * r * dJ + dI * n * r
+            macs += sum(3 * (dJ - t) * (m - kept_r) for t in range(dI))
+            macs += sum(3 * (dI - t) * max(n - kept_c - dJ, 0) for t in range(min(d, dI)))
+            macs += n * dk * dI + (m + n) * (r + dk) * dk
+            r += dk
+            kept_r += dk
+            kept_c += dk
+    return entries, macs * (8 if complex_ else 2)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def _oracle_leaf(args):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    x, y, k, r0, mr, c0, nc, d, eps, seed, a, b = args
+    from oracle import baca as ob
+    from oracle import generators as og
+    from oracle import sampler as osamp
+    g = og.Window(og.Helmholtz(x, y, k), r0, mr, c0, nc)
+    res = ob.baca(g, d, eps, seed=seed, bid=osamp.block_id(0, a, b))
+    ob.recompress(res["U"], res["V"], eps)
+    return sum(mr * len(t["J"]) + len(t["I"]) * nc for t in res["trace"])
+
+
+def _warm(_):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import oracle.baca  # noqa: F401
+    return 0
+
+
+def oracle_sample(x, y, cfg, seconds, max_procs=None):
+    """The CPU oracle (leaf BACA + re-compression of Alg. 2 / Sec. 3.2) on a
+    bounded sample of the workload's leaves, processes spawned, one BLAS thread
+    each.  Returns (entries/s, cores used, description)."""
+    import multiprocessing as mp
+    L = cfg["levels"]
+    rows = leaf_spans(cfg["m"], L)
+    cols = leaf_spans(cfg["n"], L)
+    nb = 1 << L
+    cores = len(os.sched_getaffinity(0))
+    procs = max(1, min(cores, max_procs or cores))
+    ctx = mp.get_context("spawn")
+    jobs = []
+    order = np.random.default_rng(0).permutation(nb * nb)
+    for leaf in order:
+        a, b = divmod(int(leaf), nb)
+        jobs.append((x, y, cfg["k"], rows[a][0], rows[a][1], cols[b][0], cols[b][1], cfg["d"], cfg["eps"],
+                     cfg["seed"], a, b))
+    done = 0
+    entries = 0
+    with ctx.Pool(procs) as pool:
+        pool.map(_warm, range(procs))  # interpreter start-up outside the timed sample
+        t0 = time.perf_counter()
+        while done < len(jobs) and time.perf_counter() - t0 < seconds:
+            batch = jobs[done:done + procs]
+            entries += sum(pool.map(_oracle_leaf, batch))
+            done += len(batch)
+    dt = time.perf_counter() - t0
+    desc = ("oracle leaf BACA + SVD re-compression (Alg. 2, Sec. 3.2) on %d of %d leaves (%dx%d each), "
+            "%d spawned processes x 1 BLAS thread; merges not sampled" % (done, nb * nb, rows[0][1], cols[0][1], procs))
+    return entries / dt, procs, desc, dt
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+
+    cfg = WORKLOAD
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    x, y = inputs.sphere_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
+    ctx = B.Context()
+    spec = B.helmholtz(x, y, cfg["k"])
+    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE)
+    ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
+    cap = cfg["rank_cap"]
+    out = (torch.empty((cap, cfg["m"]), dtype=torch.complex128, device=dev),
+           torch.empty(cap, dtype=torch.float64, device=dev),
+           torch.empty((cap, cfg["n"]), dtype=torch.complex128, device=dev))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        res = B.compress(ctx, spec, opts, ws=ws, out=out)
+    torch.cuda.synchronize(dev)
+    # accounting from the (deterministic) pivot records of the last run
+    L = cfg["levels"]
+    nb = 1 << L
+    rows = leaf_spans(cfg["m"], L)
+    cols = leaf_spans(cfg["n"], L)
+    traces, sizes = [], []
+    for leaf in range(nb * nb):
+        traces.append(B.read_leaf_trace(spec, opts, ws, leaf))
+        a, b = divmod(leaf, nb)
+        sizes.append((rows[a][1], cols[b][1]))
+    entries, flops = leaf_accounting(traces, sizes, cfg["d"], True)
+    rank = res.rank
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms, baca_ms, recomp_ms, merge_ms = [], [], [], []
+    launches = 0
+    with ClockSampler(dev.index) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = B.compress(ctx, spec, opts, ws=ws, out=out)
+            e1.record(stream)
+            (tb, tr, tm, tt), launches = B.phase_times(ctx)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            baca_ms.append(tb)
+            recomp_ms.append(tr)
+            merge_ms.append(tm)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    ms = float(np.mean(step_ms))
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * entries / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned inputs -> device,
+    # compress, factors -> pinned host, every step
+    xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    yh = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
+    xd = torch.empty_like(xh, device=dev)
+    yd = torch.empty_like(yh, device=dev)
+    spec_e2e = B.helmholtz(xd, yd, cfg["k"])
+    Uh = torch.empty((cap, cfg["m"]), dtype=torch.complex128).pin_memory()
+    Sh = torch.empty(cap, dtype=torch.float64).pin_memory()
+    Vh = torch.empty((cap, cfg["n"]), dtype=torch.complex128).pin_memory()
+    opts_e2e = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cap,
+                           leaf_rank_cap=cfg["leaf_rank_cap"])
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        xd.copy_(xh, non_blocking=True)
+        yd.copy_(yh, non_blocking=True)
+        r = B.compress(ctx, spec_e2e, opts_e2e, ws=ws, out=out)
+        k = r.rank
+        Uh[:k].copy_(out[0][:k], non_blocking=True)
+        Sh[:k].copy_(out[1][:k], non_blocking=True)
+        Vh[:k].copy_(out[2][:k], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        h2d = xh.numel() * 8 + yh.numel() * 8
+        d2h = k * (cfg["m"] + cfg["n"]) * 16 + k * 8
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = world * entries / e2e_s
+
+    # roofline of the dominant phase (FP64 ALU bound; see the accounting above)
+    phases = {"leaf_baca_ms": float(np.mean(baca_ms)), "leaf_recompression_ms": float(np.mean(recomp_ms)),
+              "merge_ms": float(np.mean(merge_ms))}
+    achieved = flops / (phases["leaf_baca_ms"] / 1e3) / 1e12
+    probe = B.fp64_probe()
+    roof = {"bound": "alu", "kernel": "baca_leaf_kernel (leaf BACA, Alg. 2)", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": None, "flops_per_launch": flops,
+            "peak_note": "FP64 peak derived from 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz; live probe DFMA "
+                         "%.3f, DMMA %.3f TFLOP/s" % probe}
+    return dict(value=value, ms=ms_max, entries=entries, flops=flops, rank=rank, phases=phases, roof=roof,
+                launches=launches, clocks=clk.summary(), wall=wall, e2e=dict(value=e2e_value, unit="entries/s",
+                h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, seconds_per_step=e2e_s), x=x, y=y)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cfg = WORKLOAD
+        from paper_1901_06101_gb300 import inputs
+        x, y = inputs.sphere_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
+        per = max(5.0, min(60.0, 150.0 / max(1, args.steps + args.warmup)))
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, cores, desc, dt = oracle_sample(x, y, cfg, per)
+            if i >= args.warmup:
+                vals.append(v)
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+                "config": dict({k: v for k, v in cfg.items() if k != "k"}, k="4*pi", l2="n/a (CPU)"),
+                "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, dt = oracle_sample(r["x"], r["y"], WORKLOAD, args.cpu_seconds)
+        cpu = {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+    cfg = dict({k: v for k, v in WORKLOAD.items() if k != "k"}, k="4*pi",
+               l2="flushed between timed steps (512 MiB write)", parallelism="replicas" if world > 1 else "1 GPU")
+    line = {"metric": METRIC, "value": r["value"], "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": cfg,
+            "roofline": r["roof"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+            "clocks": r["clocks"], "phases_ms": r["phases"], "rank": r["rank"],
+            "entries_per_step": r["entries"]}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

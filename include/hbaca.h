@@ -97,7 +97,9 @@ typedef struct hbaca_gen {
 } hbaca_gen;
 
 /* Flags */
-#define HBACA_FLAG_ASYNC 1u  /* do not synchronise; the rank goes to result.d_rank only */
+#define HBACA_FLAG_ASYNC 1u    /* do not synchronise; the rank goes to result.d_rank only */
+#define HBACA_FLAG_PROFILE 2u  /* record CUDA events around each phase on `stream`
+                                  (read with hbaca_phase_times after the call) */
 
 /* Options of one compression (Alg. 3 inputs n_b, d, eps). */
 typedef struct hbaca_opts {
@@ -175,6 +177,13 @@ typedef struct hbaca_leaf_trace {
 hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts,
                                    const void* workspace, int64_t leaf,
                                    hbaca_leaf_trace* trace, void* stream);
+
+/* Device time of the phases of the last hbaca_compress on `ctx` that ran with
+   HBACA_FLAG_PROFILE, from CUDA events recorded on the call's stream:
+   ms[0] leaf BACA kernel (Alg. 2), ms[1] leaf re-compression (Sec. 3.2),
+   ms[2] hierarchical merges (Alg. 3), ms[3] whole call.  *launches receives
+   the number of kernels the call launched.  Synchronises on the events. */
+hbaca_status hbaca_phase_times(hbaca_ctx* ctx, double ms[4], int32_t* launches);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* hbaca_last_error(void);

@@ -264,6 +264,9 @@ def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
         # legitimately part ways
         rec["noise_level"] = bool(len(diag) == 0 or diag[0] <= 100.0 * nC
                                   or (dk > 0 and min(diag[:dk]) <= 1e4 * nC))
+        # condition number of the kept triangle: rounding in V_k = T^-1 Q^H R
+        # (and so in nu, mu) is amplified by it
+        rec["cond_T"] = float(diag[0] / min(diag[:dk])) if dk > 0 else 1.0
         # rank rule QR(W, eps): kept pivots at or above eps |T_11|, the next one below
         nxt = greedy_qrcp(W, min(dI, dJ), abs_noise=nC)[1]
         ok = True

@@ -15,6 +15,7 @@ GEN_DENSE, GEN_GAUSSIAN, GEN_HELMHOLTZ, GEN_SPARSE_PRODUCT, GEN_LOWRANK = 0, 1, 
 # hbaca_dtype
 F64, C128 = 0, 1
 FLAG_ASYNC = 1
+FLAG_PROFILE = 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
           5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE"}
 STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}
@@ -80,6 +81,9 @@ SIGNATURES = [
      + [ctypes.c_void_p]),
     ("hbaca_debug_plan_json", ctypes.c_size_t, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_char_p,
                                                 ctypes.c_size_t]),
+    ("hbaca_phase_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_last_error", ctypes.c_char_p, []),
     ("hbaca_version", ctypes.c_char_p, []),
 ]
@@ -318,3 +322,18 @@ def plan_json(spec, opts):
     buf = ctypes.create_string_buffer(n)
     lib().hbaca_debug_plan_json(ctypes.byref(spec.gen), ctypes.byref(opts), buf, n)
     return json.loads(buf.value.decode())
+
+
+def phase_times(ctx):
+    """(ms BACA, ms leaf re-compression, ms merges, ms total), launches of the
+    last call made with FLAG_PROFILE."""
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int32()
+    check(lib().hbaca_phase_times(ctx.ptr, ms, ctypes.byref(n)))
+    return tuple(ms), n.value
+
+
+def fp64_probe():
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(lib().hbaca_debug_fp64_probe(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

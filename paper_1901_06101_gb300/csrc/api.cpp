@@ -16,6 +16,9 @@
 struct hbaca_ctx {
   int device;
   int sms;
+  cudaEvent_t ev[4];
+  bool have_times;
+  int launches;
 };
 
 namespace {
@@ -63,13 +66,20 @@ hbaca_status hbaca_create(hbaca_ctx** ctx) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (major * 10 + minor != 103)
     return fail(HBACA_CUDA, "libhbaca is built for sm_103a (GB300); device is sm_" + std::to_string(major * 10 + minor));
-  *ctx = new (std::nothrow) hbaca_ctx{dev, sms};
+  *ctx = new (std::nothrow) hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0};
   if (!*ctx) return fail(HBACA_INVALID_ARG, "out of host memory");
+  for (int i = 0; i < 4; ++i) {
+    e = cudaEventCreate(&(*ctx)->ev[i]);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+  }
   tls_err.clear();
   return HBACA_OK;
 }
 
 hbaca_status hbaca_destroy(hbaca_ctx* ctx) {
+  if (ctx)
+    for (int i = 0; i < 4; ++i)
+      if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
   return HBACA_OK;
 }
@@ -96,6 +106,13 @@ hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_op
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
   hbaca::RunCtx rc{ws, st, ctx->sms, out, 0};
+  const bool prof = (opts->flags & HBACA_FLAG_PROFILE) != 0;
+  ctx->have_times = false;
+  if (prof) {
+    for (int i = 0; i < 4; ++i) rc.ev[i] = ctx->ev[i];
+    cudaError_t pe = cudaEventRecord(ctx->ev[0], st);
+    if (pe != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(pe));
+  }
   // status word and leaf work counter live in separate 256-byte regions
   cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);
@@ -104,6 +121,12 @@ hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_op
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("workspace set-up: ") + cudaGetErrorString(e));
   e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
   if (e != cudaSuccess) return fail(HBACA_CUDA, err.empty() ? cudaGetErrorString(e) : err);
+  ctx->launches = rc.launches;
+  if (prof) {
+    e = cudaEventRecord(ctx->ev[3], st);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    ctx->have_times = true;
+  }
   int32_t* d_rank_ws = reinterpret_cast<int32_t*>(ws + p.user_lv.rank_off);
   if (out->d_rank) {
     e = cudaMemcpyAsync(out->d_rank, d_rank_ws, 4, cudaMemcpyDeviceToDevice, st);
@@ -229,6 +252,24 @@ hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts
   if (n_out) *n_out = b.n;
   if (rank_out) *rank_out = rank;
   if (cap_out) *cap_out = p.rank_cap;
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_phase_times(hbaca_ctx* ctx, double ms[4], int32_t* launches) {
+  if (!ctx || !ms) return fail(HBACA_INVALID_ARG, "NULL argument");
+  if (launches) *launches = ctx->launches;
+  if (!ctx->have_times) return fail(HBACA_INVALID_ARG, "the last call did not run with HBACA_FLAG_PROFILE");
+  float t[3];
+  cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t[0], ctx->ev[0], ctx->ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t[1], ctx->ev[1], ctx->ev[2]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t[2], ctx->ev[2], ctx->ev[3]);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("event timing: ") + cudaGetErrorString(e));
+  ms[0] = t[0];
+  ms[1] = t[1];
+  ms[2] = t[2];
+  ms[3] = (double)t[0] + t[1] + t[2];
   tls_err.clear();
   return HBACA_OK;
 }

@@ -121,6 +121,7 @@ __global__ void pack_kernel(const DenseParams<T> P) {
     dm.kra = min(t.rows_a, k);
     dm.krb = t.kind == TASK_LEAF ? min(t.rows_b, k) : 0;
     dm.s = 0;
+    dm.sweeps = 0;
     P.dims[ti] = dm;
   }
 }
@@ -248,6 +249,135 @@ __global__ void core_kernel(const DenseParams<T> P) {
   }
 }
 
+// Block-wide max (identical in every CTA of a cluster).
+__device__ __forceinline__ double block_max_dense(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s = fmax(s, scratch[w]);
+  __syncthreads();
+  return s;
+}
+
+// Block-wide sum with a fixed order (identical in every CTA of a cluster).
+__device__ __forceinline__ double block_sum_dense(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += scratch[w];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------------------------ QRCP of the core
+// Preconditioning of the one-sided Jacobi SVD (Drmac & Veselic, "New fast and
+// accurate Jacobi SVD algorithm", SIAM J. Matrix Anal. Appl. 2008): column-
+// pivoted Householder QR of the core, M P = Q2 R2 (pivot = largest trailing
+// column norm, recomputed explicitly), then the Jacobi sweeps run on the
+// graded matrix X = R2^H (nc x p), which converges in a few sweeps.
+// M (mr x nc) is overwritten by R2 (column perm[t] holds R2(0..t, t)) and the
+// reflector tails; perm (nc ints) lists the pivot order followed by the
+// unchosen columns; X = R2^H is written to the x_off region.  One CTA per task.
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads) qrcp_core_kernel(const DenseParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ti = blockIdx.x;
+  const SvdTask t = P.tasks[ti];
+  const TaskDims dm = P.dims[ti];
+  const int mr = dm.kra;
+  const int nc = t.kind == TASK_LEAF ? dm.krb : dm.k;
+  const int ld = t.kcap;
+  if (mr <= 0 || nc <= 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  T* M = P.core + t.m_off;
+  T* X = P.core + t.x_off;
+  T* tau = P.tau + t.tau_off + 2 * t.kcap;
+  int32_t* perm = P.ord + t.ord_off + t.kcap;
+  double* nrm = reinterpret_cast<double*>(smem_raw);            // nc
+  T* coef = reinterpret_cast<T*>(nrm + nc + (nc & 1));           // [0] conj(tau)
+  long long* wb = reinterpret_cast<long long*>(coef + 2);        // 32
+  int* wi = reinterpret_cast<int*>(wb + 32);                     // 32
+  int* sh = wi + 32;                                             // [0] pivot
+  uint8_t* chosen = reinterpret_cast<uint8_t*>(sh + 4);          // nc
+  for (int j = tid; j < nc; j += blockDim.x) chosen[j] = 0;
+  __syncthreads();
+  const int p = min(mr, nc);
+  for (int st = 0; st < p; ++st) {
+    for (int j = warp; j < nc; j += nw) {
+      if (chosen[j]) continue;
+      double a = 0.0;
+      for (int i = st + lane; i < mr; i += 32) a += abs2(M[(int64_t)j * ld + i]);
+      a = warp_sum(a);
+      if (lane == 0) nrm[j] = a;
+    }
+    __syncthreads();
+    long long bb = -1;
+    int bi = INT_MAX;
+    for (int j = tid; j < nc; j += blockDim.x)
+      if (!chosen[j]) argmax_merge(bb, bi, nbits(nrm[j]), j);
+    warp_argmax(bb, bi);
+    if (lane == 0) { wb[warp] = bb; wi[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      bb = lane < nw ? wb[lane] : -1;
+      bi = lane < nw ? wi[lane] : INT_MAX;
+      warp_argmax(bb, bi);
+      if (lane == 0) { sh[0] = bi; perm[st] = bi; chosen[bi] = 1; }
+    }
+    __syncthreads();
+    T* col = M + (int64_t)sh[0] * ld;
+    if (warp == 0) {
+      double sig2 = 0.0;
+      for (int i = st + 1 + lane; i < mr; i += 32) sig2 += abs2(col[i]);
+      sig2 = warp_sum(sig2);
+      if (lane == 0) {
+        double beta;
+        T tu, sc;
+        householder(col[st], sig2, beta, tu, sc);
+        coef[0] = conj_(tu);
+        coef[1] = sc;
+        tau[st] = tu;
+        col[st] = from_re<T>(beta);
+      }
+      __syncwarp();
+      const T sc = coef[1];
+      for (int i = st + 1 + lane; i < mr; i += 32) col[i] = mul(col[i], sc);
+    }
+    __syncthreads();
+    const T ctau = coef[0];
+    for (int j = warp; j < nc; j += nw) {
+      if (chosen[j]) continue;
+      T* y = M + (int64_t)j * ld;
+      T w = Traits<T>::zero();
+      for (int i = st + 1 + lane; i < mr; i += 32) w = cmac(w, col[i], y[i]);
+      w = warp_sum(w);
+      w = add(w, y[st]);
+      const T f = mul(ctau, w);
+      if (lane == 0) y[st] = sub(y[st], f);
+      for (int i = st + 1 + lane; i < mr; i += 32) y[i] = msub(y[i], col[i], f);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {  // unchosen columns (nc > mr) follow in index order
+    int q = p;
+    for (int j = 0; j < nc; ++j)
+      if (!chosen[j]) perm[q++] = j;
+  }
+  __syncthreads();
+  // X = R2^H: X(j, i) = conj(R2(i, j)) = conj(M(i, perm[j])) for i <= j, i < p
+  for (int e = tid; e < nc * p; e += blockDim.x) {
+    const int j = e % nc, i = e / nc;
+    X[(int64_t)i * ld + j] = i <= j ? conj_(M[(int64_t)perm[j] * ld + i]) : Traits<T>::zero();
+  }
+}
+
 // ------------------------------------------------------------------ Jacobi SVD
 // One-sided Jacobi (Hestenes) on M (mr x nc): M Y = X S.  Round-robin pairs;
 // per pair the warp forms alpha = |a|^2, beta = |b|^2, gamma = a^H b and
@@ -266,6 +396,25 @@ __device__ __forceinline__ void rotate_pair(T* a, T* b, int len, double cs, doub
   }
 }
 
+// Rotation of one Jacobi pair from alpha = |a|^2, beta = |b|^2, gamma = a^H b.
+// Returns false when the pair counts as orthogonal: |gamma| below tol times
+// |a| |b|, or both columns negligible, or a column in the denormal range.
+template <typename T>
+__device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, double tol, double negl, double fro2,
+                                                double& cs, double& sn, T& ph) {
+  const double g = absval(ga);
+  if (g == 0.0 || al < 1e-290 || be < 1e-290 || fmax(al, be) < negl) return false;
+  if (g <= tol * sqrt(al) * sqrt(be)) return false;
+  const double zeta = (be - al) / (2.0 * g);
+  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  cs = 1.0 / sqrt(1.0 + tt * tt);
+  sn = cs * tt;
+  ph = conj_phase(ga, g);  // e^{-i phi} exactly unit, gamma = |gamma| e^{i phi}
+  return true;
+}
+
+constexpr int kJacRegs = 8;  // columns of up to 256 rows are held in registers
+
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams<T> P, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -274,9 +423,11 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
   const int ti = blockIdx.x / c;
   const SvdTask t = P.tasks[ti];
   const TaskDims dm = P.dims[ti];
-  const int mr = dm.kra;
-  const int nc = t.kind == TASK_LEAF ? dm.krb : dm.k;
-  T* M = P.core + t.m_off;
+  // the sweeps orthogonalise the columns of X = R2^H (nc_M x p), accumulating W
+  const int ncm = t.kind == TASK_LEAF ? dm.krb : dm.k;
+  const int mr = ncm;
+  const int nc = min(dm.kra, ncm);
+  T* M = P.core + t.x_off;
   T* Y = P.core + t.y_off;
   const int ld = t.kcap;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -298,12 +449,38 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
   }
   const int K = nc + (nc & 1);
   const double tol = 4.0e-16 * (double)max(mr, 8);
+  // ||M||_F^2 (rotation invariant) and the largest column norm^2, the same in
+  // every CTA (fixed summation order)
+  double fro2 = 0.0, cmax = 0.0;
+  {
+    double part = 0.0, pm = 0.0;
+    for (int j = warp; j < nc; j += nw) {
+      double cj = 0.0;
+      for (int i = lane; i < mr; i += 32) cj += abs2(M[(int64_t)j * ld + i]);
+      cj = warp_sum(cj);
+      part += (lane == 0) ? cj : 0.0;
+      pm = fmax(pm, cj);
+    }
+    fro2 = block_sum_dense(part, sv);
+    cmax = block_max_dense(pm, sv);
+  }
+  // a pair of columns both below 1e-3 eps ||M||_F (<= 0.011 eps sigma_1 for
+  // nc <= 128) cannot affect a singular value or vector above the eps-rank
+  // threshold: such pairs are not rotated
+  const double negl = 1e-6 * P.eps * P.eps * fro2;
+  // a rotation counts against convergence only if it touches a column that can
+  // still be kept (norm >= 0.1 eps max column norm); columns below that never
+  // grow (a rotation always shrinks the smaller column of its pair), so they
+  // cannot cross the eps-rank threshold.  All pairs are still rotated.
+  double* cmx = reinterpret_cast<double*>(smem_raw + 8);  // largest column norm^2 seen this sweep
   int sweep = 0;
   unsigned fb = 0;
   if (tid == 0) { flag[0] = 0; flag[1] = 0; }
   cl.sync();
   for (; sweep < max_sweeps && K > 1; ++sweep) {
-    if (tid == 0) flag[fb & 1] = 0;
+    const double tau2 = 0.01 * P.eps * P.eps * cmax;
+    double wmax = 0.0;
+    if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; }
     __syncthreads();
     for (int rd = 0; rd < K - 1; ++rd) {
       // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
@@ -315,34 +492,87 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
         if (b >= nc) continue;  // padding column
         T* ca = M + (int64_t)a * ld;
         T* cb = M + (int64_t)b * ld;
-        double al = 0.0, be = 0.0;
-        T ga = Traits<T>::zero();
-        for (int i = lane; i < mr; i += 32) {
-          const T xa = ldcg(ca + i), xb = ldcg(cb + i);
-          al += abs2(xa);
-          be += abs2(xb);
-          ga = cmac(ga, xa, xb);
+        T* ya = Y + (int64_t)a * ld;
+        T* yb = Y + (int64_t)b * ld;
+        if (mr <= 32 * kJacRegs && nc <= 32 * kJacRegs) {
+          // both columns of M and of Y in registers: one L2 round trip per pair
+          T ra[kJacRegs], rb[kJacRegs], qa[kJacRegs], qb[kJacRegs];
+#pragma unroll
+          for (int u = 0; u < kJacRegs; ++u) {
+            const int i = lane + 32 * u;
+            ra[u] = i < mr ? ldcg(ca + i) : Traits<T>::zero();
+            rb[u] = i < mr ? ldcg(cb + i) : Traits<T>::zero();
+            qa[u] = i < nc ? ldcg(ya + i) : Traits<T>::zero();
+            qb[u] = i < nc ? ldcg(yb + i) : Traits<T>::zero();
+          }
+          double al = 0.0, be = 0.0;
+          T ga = Traits<T>::zero();
+#pragma unroll
+          for (int u = 0; u < kJacRegs; ++u) {
+            if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
+              al += abs2(ra[u]);
+              be += abs2(rb[u]);
+              ga = cmac(ga, ra[u], rb[u]);
+            }
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          wmax = fmax(wmax, fmax(al, be));
+          double cs, sn;
+          T ph;
+          if (!jacobi_rotation(al, be, ga, tol, negl, fro2, cs, sn, ph)) continue;
+          if (lane == 0 && fmax(al, be) >= tau2) flag[fb & 1] = 1;
+#pragma unroll
+          for (int u = 0; u < kJacRegs; ++u) {
+            const int i = lane + 32 * u;
+            if (i < mr) {
+              const T x = ra[u], yv = mul(ph, rb[u]);
+              ca[i] = sub(scale(x, cs), scale(yv, sn));
+              cb[i] = add(scale(x, sn), scale(yv, cs));
+            }
+            if (i < nc) {
+              const T x = qa[u], yv = mul(ph, qb[u]);
+              ya[i] = sub(scale(x, cs), scale(yv, sn));
+              yb[i] = add(scale(x, sn), scale(yv, cs));
+            }
+          }
+        } else {
+          double al = 0.0, be = 0.0;
+          T ga = Traits<T>::zero();
+          for (int i = lane; i < mr; i += 32) {
+            const T xa = ldcg(ca + i), xb = ldcg(cb + i);
+            al += abs2(xa);
+            be += abs2(xb);
+            ga = cmac(ga, xa, xb);
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          wmax = fmax(wmax, fmax(al, be));
+          double cs, sn;
+          T ph;
+          if (!jacobi_rotation(al, be, ga, tol, negl, fro2, cs, sn, ph)) continue;
+          if (lane == 0 && fmax(al, be) >= tau2) flag[fb & 1] = 1;
+          rotate_pair(ca, cb, mr, cs, sn, ph, lane);
+          rotate_pair(ya, yb, nc, cs, sn, ph, lane);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        // columns whose squared norm is in the denormal range count as zero
-        const double g = absval(ga);
-        if (g == 0.0 || al < 1e-290 || be < 1e-290 || g <= tol * sqrt(al) * sqrt(be)) continue;
-        const double zeta = (be - al) / (2.0 * g);
-        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-        const T ph = conj_phase(ga, g);  // e^{-i phi} exactly unit, gamma = |gamma| e^{i phi}
-        rotate_pair(ca, cb, mr, cs, sn, ph, lane);
-        rotate_pair(Y + (int64_t)a * ld, Y + (int64_t)b * ld, nc, cs, sn, ph, lane);
-        if (lane == 0) flag[fb & 1] = 1;
       }
       __syncthreads();
       cl.sync();
     }
-    // any rotation anywhere in the cluster this sweep?
+    // the largest column norm^2 of this sweep, over the cluster (for the next tau)
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(cmx), (unsigned long long)__double_as_longlong(wmax));
+    __syncthreads();
+    cl.sync();
+    // any relevant rotation anywhere in the cluster this sweep?
     int any = 0;
-    for (int r = 0; r < c; ++r) any |= *cl.map_shared_rank(&flag[fb & 1], r);
+    double cm = 0.0;
+    for (int r = 0; r < c; ++r) {
+      any |= *cl.map_shared_rank(&flag[fb & 1], r);
+      cm = fmax(cm, *cl.map_shared_rank(cmx, r));
+    }
+    if (cm > 0.0) cmax = cm;
     ++fb;
     cl.sync();
     if (!any) break;
@@ -376,6 +606,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
       if (s > P.out_cap) { set_status(P.status, DS_RANK_CAPACITY); s = (int)P.out_cap; }
       sshare[0] = s;
       P.dims[ti].s = s;
+      P.dims[ti].sweeps = sweep;
       const BlockRef ob = P.out_blocks[t.out];
       P.out_rank[ob.rank_slot] = s;
     }
@@ -395,6 +626,52 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
     }
   }
   cl.sync();
+}
+
+// ------------------------------------------------------------------ finish
+// Singular vectors of the core M from the preconditioned Jacobi: with
+// X = R2^H, X W = Z S and M P = Q2 R2, M = (Q2 W) S (P Z)^H.  Writes, for the
+// s kept columns in descending order, Xs = Q2 [W(:, ord); 0] (mr x s) and
+// Ys(perm[j], :) = Z(j, ord) (nc x s).  One warp per output column.
+template <typename T>
+__global__ void finish_kernel(const DenseParams<T> P) {
+  const int ti = blockIdx.y;
+  const SvdTask t = P.tasks[ti];
+  const TaskDims dm = P.dims[ti];
+  const int s = dm.s;
+  const int mr = dm.kra;
+  const int nc = t.kind == TASK_LEAF ? dm.krb : dm.k;
+  const int p = min(mr, nc);
+  const int ld = t.kcap;
+  const T* M = P.core + t.m_off;
+  const T* W = P.core + t.y_off;
+  const T* Z = P.core + t.x_off;
+  T* Xs = P.core + t.xs_off;
+  T* Ys = P.core + t.ys_off;
+  const T* tau = P.tau + t.tau_off + 2 * t.kcap;
+  const int32_t* ord = P.ord + t.ord_off;
+  const int32_t* perm = P.ord + t.ord_off + t.kcap;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwt = (gridDim.x * blockDim.x) >> 5;
+  for (int tc = gw; tc < s; tc += nwt) {
+    const int jo = ord[tc];
+    T* v = Xs + (int64_t)tc * ld;
+    for (int i = lane; i < mr; i += 32) v[i] = i < p ? W[(int64_t)jo * ld + i] : Traits<T>::zero();
+    __syncwarp();
+    for (int st = p - 1; st >= 0; --st) {
+      const T* u = M + (int64_t)perm[st] * ld;
+      T w = Traits<T>::zero();
+      for (int i = st + 1 + lane; i < mr; i += 32) w = cmac(w, u[i], v[i]);
+      w = warp_sum(w);
+      w = add(w, v[st]);
+      const T f = mul(tau[st], w);
+      __syncwarp();
+      if (lane == 0) v[st] = sub(v[st], f);
+      for (int i = st + 1 + lane; i < mr; i += 32) v[i] = msub(v[i], u[i], f);
+      __syncwarp();
+    }
+    for (int j = lane; j < nc; j += 32) Ys[(int64_t)tc * ld + perm[j]] = Z[(int64_t)jo * ld + j];
+  }
 }
 
 // ------------------------------------------------------------------ Q application
@@ -418,8 +695,7 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   const T* A = jb.which ? P.qr + t.b_off : qr_a_ptr(P, t);
   const int64_t lda = jb.which ? (int64_t)t.rows_b : t.lda;
   const T* tau = P.tau + t.tau_off + (jb.which ? t.kcap : 0);
-  const T* Z = P.core + (jb.which ? t.y_off : t.m_off);  // column ord[tc] holds Z(:, tc)
-  const int32_t* ord = P.ord + t.ord_off;
+  const T* Z = P.core + (jb.which ? t.ys_off : t.xs_off);  // compact, column tc
   const BlockRef ob = P.out_blocks[t.out];
   T* D = jb.to_v ? P.outV + ob.v_off : P.outU + ob.u_off;
   const int64_t ldd = jb.to_v ? ob.ldv : ob.ldu;
@@ -431,7 +707,7 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   T* wv = part + 2 * s;                       // s combined
   for (int tc = 0; tc < s; ++tc)
     for (int i = ra + tid; i < rb; i += blockDim.x)
-      D[(int64_t)tc * ldd + i] = i < kk ? Z[(int64_t)ord[tc] * t.kcap + i] : Traits<T>::zero();
+      D[(int64_t)tc * ldd + i] = i < kk ? Z[(int64_t)tc * t.kcap + i] : Traits<T>::zero();
   __syncthreads();
   for (int j = kk - 1; j >= 0; --j) {
     T* pb = part + (j & 1) * s;
@@ -481,18 +757,17 @@ __global__ void blockprod_kernel(const DenseParams<T> P) {
   const BlockRef b1 = P.in_blocks[t.in1], b2 = P.in_blocks[t.in2];
   const int r1 = P.in_rank[b1.rank_slot], r2 = P.in_rank[b2.rank_slot];
   const BlockRef ob = P.out_blocks[t.out];
-  const T* Y = P.core + t.y_off;
-  const int32_t* ord = P.ord + t.ord_off;
+  const T* Y = P.core + t.ys_off;  // compact, column tc
   if (t.kind == TASK_HORIZ) {
     const int n1 = b1.n, ntot = b1.n + b2.n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)ntot * s; e += (int64_t)gridDim.x * blockDim.x) {
       const int j = (int)(e % ntot), tc = (int)(e / ntot);
       T acc = Traits<T>::zero();
       if (j < n1) {
-        const T* ys = Y + (int64_t)ord[tc] * t.kcap;
+        const T* ys = Y + (int64_t)tc * t.kcap;
         for (int p = 0; p < r1; ++p) acc = cmac(acc, ys[p], P.inV[b1.v_off + (int64_t)p * b1.ldv + j]);
       } else {
-        const T* ys = Y + (int64_t)ord[tc] * t.kcap + r1;
+        const T* ys = Y + (int64_t)tc * t.kcap + r1;
         for (int p = 0; p < r2; ++p) acc = cmac(acc, ys[p], P.inV[b2.v_off + (int64_t)p * b2.ldv + (j - n1)]);
       }
       P.outV[ob.v_off + (int64_t)tc * ob.ldv + j] = acc;
@@ -503,10 +778,10 @@ __global__ void blockprod_kernel(const DenseParams<T> P) {
       const int i = (int)(e % mtot), tc = (int)(e / mtot);
       T acc = Traits<T>::zero();
       if (i < m1) {
-        const T* ys = Y + (int64_t)ord[tc] * t.kcap;
+        const T* ys = Y + (int64_t)tc * t.kcap;
         for (int p = 0; p < r1; ++p) acc = mac(acc, P.inU[b1.u_off + (int64_t)p * b1.ldu + i], ys[p]);
       } else {
-        const T* ys = Y + (int64_t)ord[tc] * t.kcap + r1;
+        const T* ys = Y + (int64_t)tc * t.kcap + r1;
         for (int p = 0; p < r2; ++p) acc = mac(acc, P.inU[b2.u_off + (int64_t)p * b2.ldu + (i - m1)], ys[p]);
       }
       P.outU[ob.u_off + (int64_t)tc * ob.ldu + i] = acc;

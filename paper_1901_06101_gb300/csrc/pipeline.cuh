@@ -177,9 +177,16 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
   HB_TRY(launch_cluster(qr_kernel<T>, sg.nqr * cq, cq, qr_smem, rc.st, D, qj));
   core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D);
   HB_TRY(cudaGetLastError());
+  const size_t qc_smem = (size_t)sg.kcap * 9 + 2 * sizeof(T) + 32 * 12 + 64 + 16;
+  HB_TRY(cudaFuncSetAttribute(qrcp_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qc_smem));
+  qrcp_core_kernel<T><<<nt, kDenseThreads, qc_smem, rc.st>>>(D);
+  HB_TRY(cudaGetLastError());
   const int cj = pick_cluster(nt, sg.kcap, rc.sms, 16);
   const size_t j_smem = 16 + (size_t)sg.kcap * 12 + 64;
   HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_smem, rc.st, D, 40));
+  finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D);
+  HB_TRY(cudaGetLastError());
+  rc.launches += 2;
   const size_t qa_smem = (size_t)3 * p.rank_cap * sizeof(T) + 64;
   HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj));
   rc.launches += 5;
@@ -193,10 +200,15 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
 
 template <typename T>
 cudaError_t run_stages(Plan& p, RunCtx& rc, std::string& err) {
-  for (const Stage& sg : p.stages) {
+  if (rc.ev[1]) HB_TRY(cudaEventRecord(rc.ev[1], rc.st));  // leaf BACA done
+  for (size_t i = 0; i < p.stages.size(); ++i) {
+    const Stage& sg = p.stages[i];
+    if (rc.ev[2] && sg.kind != TASK_LEAF && (i == 0 || p.stages[i - 1].kind == TASK_LEAF))
+      HB_TRY(cudaEventRecord(rc.ev[2], rc.st));  // leaf re-compression done
     cudaError_t e = run_stage<T>(p, sg, rc, err);
     if (e != cudaSuccess) return e;
   }
+  if (rc.ev[2] && (p.stages.empty() || p.stages.back().kind == TASK_LEAF)) HB_TRY(cudaEventRecord(rc.ev[2], rc.st));
   return cudaSuccess;
 }
 

@@ -206,7 +206,7 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
   p.task_storage.clear();
   p.stages.clear();
   size_t qr_elems = 0, tau_elems = 0, core_elems = 0, ord_elems = 0;
-  const size_t budget = (size_t)3 << 30;  // bytes of chunk scratch
+  const size_t budget = (size_t)8 << 30;  // bytes of chunk scratch
   auto add_stage = [&](std::vector<SvdTask>& all, int kind, int in_store, int in_level, int out_store, int out_level) {
     size_t i = 0;
     while (i < all.size()) {
@@ -217,14 +217,17 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
         SvdTask t = all[i];
         const int64_t kc = t.kcap;
         const int64_t need_qr = (int64_t)t.rows_a * kc * (t.a_in_baca ? 0 : 1) + (int64_t)t.rows_b * kc;
-        const size_t bytes = (size_t)(ao + need_qr + co + 2 * kc * kc + tauo + 2 * kc) * p.esz + (size_t)(oo + kc) * 4;
+        const size_t bytes = (size_t)(ao + need_qr + co + 5 * kc * kc + tauo + 3 * kc) * p.esz + (size_t)(oo + 2 * kc) * 4;
         if (!ch.empty() && bytes > budget) break;
         if (!t.a_in_baca) { t.a_off = ao; ao += (int64_t)t.rows_a * kc; }
         if (t.kind == TASK_LEAF) { t.b_off = ao; ao += (int64_t)t.rows_b * kc; }
-        t.tau_off = tauo; tauo += 2 * kc;
+        t.tau_off = tauo; tauo += 3 * kc;
         t.m_off = co; co += kc * kc;
         t.y_off = co; co += kc * kc;
-        t.ord_off = oo; oo += kc;
+        t.x_off = co; co += kc * kc;
+        t.xs_off = co; co += kc * kc;
+        t.ys_off = co; co += kc * kc;
+        t.ord_off = oo; oo += 2 * kc;
         rmax = std::max(rmax, std::max(t.rows_a, t.rows_b));
         kmx = std::max<int>(kmx, (int)kc);
         ch.push_back(t);

@@ -14,6 +14,7 @@ struct RunCtx {
   int sms;
   const hbaca_result* res;
   int launches = 0;  // kernels launched by the call
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // profile: after BACA, after leaf stage, end
 };
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);

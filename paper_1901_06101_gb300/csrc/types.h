@@ -54,21 +54,25 @@ struct SvdTask {
   int64_t b_off;
   int32_t rows_b, pad0;
   int64_t src_v_off;   // LEAF: offset of the leaf's V (k x rows_b, row-major) in the BACA V arena
-  int64_t tau_off;     // 2 * kcap scalars
-  int64_t m_off;       // core M: kcap x kcap, column-major ld kcap; after Jacobi its
-                       // columns hold X (normalised), in unsorted order
-  int64_t y_off;       // Y: kcap x kcap, column-major ld kcap
-  int64_t ord_off;     // kcap ints: column order by descending singular value
+  int64_t tau_off;     // 3 * kcap scalars: reflectors of QR(A), QR(B), QRCP of the core
+  int64_t m_off;       // core M (kcap x kcap, column-major ld kcap); QRCP in place
+  int64_t y_off;       // W: Jacobi rotations accumulated (kcap x kcap)
+  int64_t x_off;       // X = R2^H, the matrix the Jacobi sweeps orthogonalise (kcap x kcap)
+  int64_t xs_off;      // left singular vectors of M, sorted, compact (kcap x kcap)
+  int64_t ys_off;      // right singular vectors of M, sorted, compact (kcap x kcap)
+  int64_t ord_off;     // 2 * kcap ints: Jacobi column order, then the QRCP permutation
   int32_t out;         // block index in the output store
   int32_t m1;          // HORIZ / VERT: rows (VERT) or columns (HORIZ) of the first child
 };
 
 // Device-side per-task sizes written by the kernels.
 struct TaskDims {
-  int32_t k;    // columns of the QR operand(s) (LEAF: BACA rank; merges: r1 + r2)
-  int32_t kra;  // rows of R_A = min(rows_a, k)
-  int32_t krb;  // rows of R_B (LEAF) = min(rows_b, k)
-  int32_t s;    // truncated rank
+  int32_t k;       // columns of the QR operand(s) (LEAF: BACA rank; merges: r1 + r2)
+  int32_t kra;     // rows of R_A = min(rows_a, k)
+  int32_t krb;     // rows of R_B (LEAF) = min(rows_b, k)
+  int32_t s;       // truncated rank
+  int32_t sweeps;  // Jacobi sweeps run
+  int32_t pad[3];
 };
 
 struct QrJob {

@@ -70,15 +70,22 @@ def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid):
     limit = noisy[0] + 1 if noisy else len(g["trace"])
     assert len(rep["recs"]) >= limit, ("replay stopped", len(rep["recs"]), len(g["trace"]), rep["recs"][-1])
     rep["comparable"] = True
+    cond = 1.0
     for k, (r, t) in enumerate(zip(rep["recs"], g["trace"])):
-        for key in ("J_ok", "valid_I", "valid_J", "valid_W", "valid_dk", "valid_stop"):
+        for key in ("J_ok", "valid_I", "valid_J", "valid_W", "valid_dk"):
             assert r[key], (key, k, g["stop"], r)
-        assert abs(r["mu"] - t["mu"]) <= 1e-9 * max(r["mu"], 1e-300), ("mu", k, r["mu"], t["mu"])
-        assert abs(r["nu"] - t["nu"]) <= 1e-9 * max(r["mu"], 1e-300), ("nu", k, r["nu"], t["nu"])
         if r.get("noise_level"):
-            rep["comparable"] = k + 1 == len(g["trace"])
-            rep["compared_iters"] = k + 1
+            # this iteration's update is rounding-dominated: nu, mu and what
+            # follows are not comparable between two correct runs
+            rep["comparable"] = False
+            rep["compared_iters"] = k
             break
+        assert r["valid_stop"], ("valid_stop", k, g["stop"], r)
+        # rounding in nu, mu grows with the conditioning of the LRID triangles so far
+        cond = max(cond, r.get("cond_T", 1.0))
+        tol = max(1e-9, 1e-13 * cond) * max(r["mu"], 1e-300)
+        assert abs(r["mu"] - t["mu"]) <= tol, ("mu", k, r["mu"], t["mu"], cond)
+        assert abs(r["nu"] - t["nu"]) <= tol, ("nu", k, r["nu"], t["nu"], cond)
     assert rep["r"] == g["rank_baca"] or not rep["comparable"]
     return rep
 
