@@ -31,9 +31,18 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "H-BACA compress ms & entries/s at stated ε; batched vs per-block; bwd/fwd"
-WORKLOAD = dict(workload="helmholtz_c128_20000_d16_L4_eps1e-4", kernel="helmholtz exp(ikr)/r",
-                m=20000, n=20000, k=4 * np.pi, d=16, levels=4, eps=1e-4, seed=1,
-                rank_cap=256, leaf_rank_cap=256)
+WORKLOADS = {
+    # the benchmark configuration
+    "helmholtz20000": dict(workload="helmholtz_c128_20000_d16_L4_eps1e-4", kernel="helmholtz exp(ikr)/r",
+                           m=20000, n=20000, k=4 * np.pi, d=16, levels=4, eps=1e-4, seed=1,
+                           rank_cap=256, leaf_rank_cap=256),
+    # the same kernel at 8000^2 with 8 x 8 leaves of 1000^2: small enough for
+    # multi-pass profiler captures, larger than L2
+    "helmholtz8000": dict(workload="helmholtz_c128_8000_d16_L3_eps1e-4", kernel="helmholtz exp(ikr)/r",
+                          m=8000, n=8000, k=4 * np.pi, d=16, levels=3, eps=1e-4, seed=1,
+                          rank_cap=256, leaf_rank_cap=256),
+}
+WORKLOAD = WORKLOADS["helmholtz20000"]
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max SM clock
 
 
@@ -45,6 +54,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--workload", default="helmholtz20000", choices=sorted(WORKLOADS))
     return ap.parse_args()
 
 
@@ -299,7 +309,9 @@ def run_ours(args, rank, world):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -108,7 +108,7 @@ typedef struct hbaca_opts {
   int32_t levels;         /* L >= 0: n_b = 4^L leaves; 2^L <= min(m, n) */
   uint64_t seed;          /* seed of the random initial column blocks J_1 */
   int64_t rank_cap;       /* column capacity of U / rows of V (output and every
-                             merged block); 0 = min(m, n) */
+                             merged block); 0 = min(m, n, 1024) */
   int64_t leaf_rank_cap;  /* capacity of a leaf's BACA factors before
                              re-compression; 0 = min(m_leaf, n_leaf, 1024) */
   uint32_t flags;         /* HBACA_FLAG_* */
