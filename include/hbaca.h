@@ -105,7 +105,9 @@ typedef struct hbaca_gen {
 typedef struct hbaca_opts {
   double eps;             /* relative tolerance, 0 < eps < 1 */
   int32_t d;              /* BACA block size, 1 .. 32 (d = 1 is ACA, Sec. 3.2) */
-  int32_t levels;         /* L >= 0: n_b = 4^L leaves; 2^L <= min(m, n) */
+  int32_t levels;         /* L >= 0: n_b = 4^L leaves, 2^L <= min(m, n); L < 0: per
+                             block, the smallest L whose leaves have at most -L rows
+                             and columns (limited by 2^L <= min(m, n)) */
   uint64_t seed;          /* seed of the random initial column blocks J_1 */
   int64_t rank_cap;       /* column capacity of U / rows of V (output and every
                              merged block); 0 = min(m, n, 1024) */
@@ -148,6 +150,18 @@ size_t hbaca_workspace_size(const hbaca_gen* gen, const hbaca_opts* opts);
 hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts,
                             hbaca_result* out, void* workspace, void* stream);
 
+/* Batched H-BACA: `nblocks` independent matrices (HOST array `gens`, all the
+   same kind and dtype; kind GAUSSIAN when nblocks > 1), each compressed as by
+   hbaca_compress with its own tree depth (opts.levels, see above) and written
+   to its own result outs[b] (HOST array).  All leaves of all blocks share one
+   persistent BACA launch, largest leaves first; every merge level of all
+   blocks is one batch of launches.  The workspace must hold
+   hbaca_workspace_size_batched(nblocks, gens, opts) bytes, 256-byte aligned.
+   This is the batched form of Alg. 2 / Alg. 3 over many admissible blocks. */
+size_t hbaca_workspace_size_batched(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts);
+hbaca_status hbaca_compress_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                    hbaca_result* outs, void* workspace, void* stream);
+
 /* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
    by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index
    a * 2^L + b.  Arrays I, J, jbar hold `max_iters * d` entries (row-major by
@@ -177,6 +191,11 @@ typedef struct hbaca_leaf_trace {
 hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts,
                                    const void* workspace, int64_t leaf,
                                    hbaca_leaf_trace* trace, void* stream);
+
+/* The same record for leaf `leaf` of block `block` of a batched call. */
+hbaca_status hbaca_read_leaf_trace_batched(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                           const void* workspace, int32_t block, int64_t leaf,
+                                           hbaca_leaf_trace* trace, void* stream);
 
 /* Device time of the phases of the last hbaca_compress on `ctx` that ran with
    HBACA_FLAG_PROFILE, from CUDA events recorded on the call's stream:

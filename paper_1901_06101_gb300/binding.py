@@ -75,6 +75,13 @@ SIGNATURES = [
                                       ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_void_p]),
     ("hbaca_read_leaf_trace", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                              ctypes.c_int64, ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
+    ("hbaca_workspace_size_batched", ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Gen), ctypes.POINTER(Opts)]),
+    ("hbaca_compress_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Gen),
+                                              ctypes.POINTER(Opts), ctypes.POINTER(Result), ctypes.c_void_p,
+                                              ctypes.c_void_p]),
+    ("hbaca_read_leaf_trace_batched", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Gen), ctypes.POINTER(Opts),
+                                                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                                     ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
     ("hbaca_debug_read_block", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 4
@@ -261,13 +268,9 @@ def compress(ctx, spec, opts, stream=None, ws=None, out=None):
     return c
 
 
-def read_leaf_trace(spec, opts, ws, leaf, max_iters=None):
-    """Per-leaf BACA record (numpy arrays)."""
+def _trace_call(call, d, max_iters):
+    """Run a trace-reading call with fresh host arrays; returns the record dict."""
     import numpy as np
-    import torch
-    d = opts.d
-    if max_iters is None:
-        max_iters = 4096
     I = np.full(max_iters * d, -1, np.int32)
     J = np.full(max_iters * d, -1, np.int32)
     jb = np.full(max_iters * d, -1, np.int32)
@@ -279,15 +282,72 @@ def read_leaf_trace(spec, opts, ws, leaf, max_iters=None):
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     tr = LeafTrace(max_iters=max_iters, d=d, I=p(I), J=p(J), jbar=p(jb), dI=p(dI), dJ=p(dJ), dk=p(dk),
                    nu=p(nu), mu=p(mu))
-    check(lib().hbaca_read_leaf_trace(ctypes.byref(spec.gen), ctypes.byref(opts),
-                                      ctypes.c_void_p(ws.data_ptr()), leaf, ctypes.byref(tr),
-                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
-    it = tr.iters
+    check(call(tr))
     recs = []
-    for k in range(it):
+    for k in range(tr.iters):
         recs.append(dict(I=list(I[k * d:k * d + dI[k]]), J=list(J[k * d:k * d + dJ[k]]),
                          jbar=list(jb[k * d:k * d + dk[k]]), dk=int(dk[k]), nu=float(nu[k]), mu=float(mu[k])))
-    return dict(iters=it, rank_baca=tr.rank_baca, rank=tr.rank, stop=STOP.get(tr.stop, tr.stop), trace=recs)
+    return dict(iters=tr.iters, rank_baca=tr.rank_baca, rank=tr.rank, stop=STOP.get(tr.stop, tr.stop), trace=recs)
+
+
+def _gen_array(specs):
+    arr = (Gen * len(specs))()
+    for i, s in enumerate(specs):
+        arr[i] = s.gen
+    return arr
+
+
+def compress_batched(ctx, specs, opts, ws=None, stream=None):
+    """hbaca_compress_batched over a list of GenSpec (one per block); returns a
+    list of Compressed (one per block) sharing the workspace."""
+    import torch
+    n = len(specs)
+    gens = _gen_array(specs)
+    if ws is None:
+        nbytes = lib().hbaca_workspace_size_batched(n, gens, ctypes.byref(opts))
+        if nbytes == 0:
+            raise HbacaError(1, lib().hbaca_last_error().decode())
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    res = (Result * n)()
+    bufs = []
+    for i, s in enumerate(specs):
+        cap = min(opts.rank_cap, s.m, s.n) if opts.rank_cap else min(s.m, s.n, 1024)
+        dt = torch.complex128 if s.complex else torch.float64
+        Ut = torch.empty((cap, s.m), dtype=dt, device="cuda")
+        S = torch.empty(cap, dtype=torch.float64, device="cuda")
+        V = torch.empty((cap, s.n), dtype=dt, device="cuda")
+        res[i] = Result(U=Ut.data_ptr(), ldu=s.m, S=S.data_ptr(), V=V.data_ptr(), ldv=s.n)
+        bufs.append((Ut, S, V))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib().hbaca_compress_batched(ctx.ptr, n, gens, ctypes.byref(opts), res, ctypes.c_void_p(ws.data_ptr()),
+                                       ctypes.c_void_p(stream)))
+    out = []
+    for i in range(n):
+        r = int(res[i].rank)
+        Ut, S, V = bufs[i]
+        c = Compressed(Ut[:r].T, S[:r], V[:r], r, ws, res[i])
+        c.buffers = bufs[i]
+        out.append(c)
+    return out
+
+
+def read_leaf_trace_batched(specs, opts, ws, block, leaf, max_iters=4096):
+    import torch
+    gens = _gen_array(specs)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return _trace_call(lambda tr: lib().hbaca_read_leaf_trace_batched(len(specs), gens, ctypes.byref(opts),
+                                                                       ctypes.c_void_p(ws.data_ptr()), block, leaf,
+                                                                       ctypes.byref(tr), st), opts.d, max_iters)
+
+
+def read_leaf_trace(spec, opts, ws, leaf, max_iters=4096):
+    """Per-leaf BACA record of the last single-block compress into `ws`."""
+    import torch
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return _trace_call(lambda tr: lib().hbaca_read_leaf_trace(ctypes.byref(spec.gen), ctypes.byref(opts),
+                                                              ctypes.c_void_p(ws.data_ptr()), leaf,
+                                                              ctypes.byref(tr), st), opts.d, max_iters)
 
 
 def read_block(spec, opts, ws, store, level, block):

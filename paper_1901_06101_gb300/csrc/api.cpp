@@ -85,27 +85,34 @@ hbaca_status hbaca_destroy(hbaca_ctx* ctx) {
 }
 
 size_t hbaca_workspace_size(const hbaca_gen* gen, const hbaca_opts* opts) {
-  if (!gen || !opts) { tls_err = "gen or opts is NULL"; return 0; }
+  return hbaca_workspace_size_batched(1, gen, opts);
+}
+
+size_t hbaca_workspace_size_batched(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts) {
+  if (!gens || !opts || nblocks < 1) { tls_err = "gens or opts is NULL, or nblocks < 1"; return 0; }
   hbaca::Plan p;
   std::string err;
-  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) { tls_err = err; return 0; }
+  if (!hbaca::make_plan(gens, nblocks, *opts, current_sms(), p, err)) { tls_err = err; return 0; }
   return p.total;
 }
 
-hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts, hbaca_result* out,
-                            void* workspace, void* stream) {
-  if (!ctx || !gen || !opts || !out) return fail(HBACA_INVALID_ARG, "NULL ctx, gen, opts or result");
+static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                    hbaca_result* outs, void* workspace, void* stream) {
+  if (!ctx || !gens || !opts || !outs || nblocks < 1) return fail(HBACA_INVALID_ARG, "NULL ctx, gens, opts or results");
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return fail(HBACA_WORKSPACE, "workspace must be a non-NULL, 256-byte aligned device pointer");
-  if (!out->U || !out->S || !out->V) return fail(HBACA_INVALID_ARG, "result U, S and V must be set");
-  if (out->ldu < gen->m || out->ldv < gen->n) return fail(HBACA_INVALID_ARG, "result needs ldu >= m and ldv >= n");
+  for (int b = 0; b < nblocks; ++b) {
+    if (!outs[b].U || !outs[b].S || !outs[b].V) return fail(HBACA_INVALID_ARG, "result U, S and V must be set");
+    if (outs[b].ldu < gens[b].m || outs[b].ldv < gens[b].n)
+      return fail(HBACA_INVALID_ARG, "result needs ldu >= m and ldv >= n");
+  }
   hbaca::Plan p;
   std::string err;
-  if (!hbaca::make_plan(*gen, *opts, ctx->sms, p, err)) return fail(HBACA_INVALID_ARG, err);
-  hbaca::bind_user_result(p, *out);
+  if (!hbaca::make_plan(gens, nblocks, *opts, ctx->sms, p, err)) return fail(HBACA_INVALID_ARG, err);
+  for (int b = 0; b < nblocks; ++b) hbaca::bind_user_result(p, b, outs[b]);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
-  hbaca::RunCtx rc{ws, st, ctx->sms, out, 0};
+  hbaca::RunCtx rc{ws, st, ctx->sms, &outs[0], 0};
   const bool prof = (opts->flags & HBACA_FLAG_PROFILE) != 0;
   ctx->have_times = false;
   if (prof) {
@@ -117,7 +124,7 @@ hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_op
   cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.desc_region.off, p.desc.data(), p.desc.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.user_lv.rank_off, 0, 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.ranks_off, 0, (size_t)p.nrefs * 4, st);
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("workspace set-up: ") + cudaGetErrorString(e));
   e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
   if (e != cudaSuccess) return fail(HBACA_CUDA, err.empty() ? cudaGetErrorString(e) : err);
@@ -127,32 +134,38 @@ hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_op
     if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
     ctx->have_times = true;
   }
-  int32_t* d_rank_ws = reinterpret_cast<int32_t*>(ws + p.user_lv.rank_off);
-  if (out->d_rank) {
-    e = cudaMemcpyAsync(out->d_rank, d_rank_ws, 4, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("rank copy: ") + cudaGetErrorString(e));
+  const int32_t* d_ranks = reinterpret_cast<const int32_t*>(ws + p.ranks_off) + p.user_ref_first;
+  for (int b = 0; b < nblocks; ++b) {
+    outs[b].rank = -1;
+    if (outs[b].d_rank) {
+      e = cudaMemcpyAsync(outs[b].d_rank, d_ranks + b, 4, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("rank copy: ") + cudaGetErrorString(e));
+    }
   }
-  out->rank = -1;
   if (opts->flags & HBACA_FLAG_ASYNC) {
     tls_err.clear();
     return HBACA_OK;
   }
-  int status = 0, rank = 0;
+  int status = 0;
+  std::vector<int32_t> ranks(nblocks);
   std::vector<hbaca::LeafOut> lo(p.nleaves);
   e = cudaMemcpyAsync(&status, ws + p.status.off, 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&rank, d_rank_ws, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ranks.data(), d_ranks, (size_t)nblocks * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(lo.data(), ws + p.leafout_off, lo.size() * sizeof(hbaca::LeafOut), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("kernel execution: ") + cudaGetErrorString(e));
-  int rmax = 0, imax = 0;
-  for (const auto& l : lo) {
-    rmax = std::max(rmax, l.rank);
-    imax = std::max(imax, l.iters);
+  for (int b = 0; b < nblocks; ++b) {
+    int rmax = 0, imax = 0;
+    const int nl = 1 << (2 * p.Lb[b]);
+    for (int i = 0; i < nl; ++i) {
+      rmax = std::max(rmax, lo[p.leaf_first[b] + i].rank);
+      imax = std::max(imax, lo[p.leaf_first[b] + i].iters);
+    }
+    outs[b].rank = ranks[b];
+    outs[b].leaf_rank_max = rmax;
+    outs[b].leaf_iters_max = imax;
   }
-  out->rank = rank;
-  out->leaf_rank_max = rmax;
-  out->leaf_iters_max = imax;
   hbaca_status hs = map_device_status(status);
   if (hs != HBACA_OK) {
     const char* what = hs == HBACA_RANK_CAPACITY ? "a rank exceeded rank_cap or leaf_rank_cap"
@@ -164,24 +177,37 @@ hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_op
   return HBACA_OK;
 }
 
-hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t leaf,
-                                   hbaca_leaf_trace* tr, void* stream) {
-  if (!gen || !opts || !workspace || !tr) return fail(HBACA_INVALID_ARG, "NULL argument");
+hbaca_status hbaca_compress(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts, hbaca_result* out,
+                            void* workspace, void* stream) {
+  return compress_blocks(ctx, 1, gen, opts, out, workspace, stream);
+}
+
+hbaca_status hbaca_compress_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                    hbaca_result* outs, void* workspace, void* stream) {
+  return compress_blocks(ctx, nblocks, gens, opts, outs, workspace, stream);
+}
+
+static hbaca_status read_trace(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts, const void* workspace,
+                               int32_t block, int64_t leaf, hbaca_leaf_trace* tr, void* stream) {
+  if (!gens || !opts || !workspace || !tr || nblocks < 1) return fail(HBACA_INVALID_ARG, "NULL argument");
   hbaca::Plan p;
   std::string err;
-  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
-  if (leaf < 0 || leaf >= p.nleaves) return fail(HBACA_INVALID_ARG, "leaf index out of range");
+  if (!hbaca::make_plan(gens, nblocks, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
+  if (block < 0 || block >= nblocks) return fail(HBACA_INVALID_ARG, "block index out of range");
+  const int nl = 1 << (2 * p.Lb[block]);
+  if (leaf < 0 || leaf >= nl) return fail(HBACA_INVALID_ARG, "leaf index out of range");
   if (tr->d != p.d) return fail(HBACA_INVALID_ARG, "trace.d must equal opts.d");
+  const int64_t gl = p.leaf_first[block] + leaf;
   hbaca::LeafDesc L;
-  std::memcpy(&L, p.desc.data() + p.leafdesc_off + leaf * sizeof(hbaca::LeafDesc), sizeof(L));
+  std::memcpy(&L, p.desc.data() + p.leafdesc_off + gl * sizeof(hbaca::LeafDesc), sizeof(L));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const char* ws = reinterpret_cast<const char*>(workspace);
   hbaca::LeafOut lo;
   int rank_after = 0;
-  cudaError_t e = cudaMemcpyAsync(&lo, ws + p.leafout_off + leaf * sizeof(hbaca::LeafOut), sizeof(lo),
+  cudaError_t e = cudaMemcpyAsync(&lo, ws + p.leafout_off + gl * sizeof(hbaca::LeafOut), sizeof(lo),
                                   cudaMemcpyDeviceToHost, st);
-  const size_t rank_off = p.L == 0 ? p.user_lv.rank_off : p.full_lv[0].rank_off + leaf * 4;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&rank_after, ws + rank_off, 4, cudaMemcpyDeviceToHost, st);
+  const int ref = p.Lb[block] == 0 ? p.user_ref_first + block : p.full_idx[block][0][leaf];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rank_after, ws + p.ranks_off + (size_t)ref * 4, 4, cudaMemcpyDeviceToHost, st);
   const int rec = 4 + 3 * p.d;
   const int nit = std::min(L.tape_iters, tr->max_iters);
   std::vector<int32_t> ti((size_t)std::max(nit, 1) * rec);
@@ -202,16 +228,27 @@ hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts,
     if (tr->dI) tr->dI[it] = r[0];
     if (tr->dJ) tr->dJ[it] = r[1];
     if (tr->dk) tr->dk[it] = r[2];
-    for (int s = 0; s < d; ++s) {
-      if (tr->I) tr->I[(size_t)it * d + s] = r[4 + s];
-      if (tr->J) tr->J[(size_t)it * d + s] = r[4 + d + s];
-      if (tr->jbar) tr->jbar[(size_t)it * d + s] = r[4 + 2 * d + s];
+    for (int s2 = 0; s2 < d; ++s2) {
+      if (tr->I) tr->I[(size_t)it * d + s2] = r[4 + s2];
+      if (tr->J) tr->J[(size_t)it * d + s2] = r[4 + d + s2];
+      if (tr->jbar) tr->jbar[(size_t)it * d + s2] = r[4 + 2 * d + s2];
     }
     if (tr->nu) tr->nu[it] = td[2 * it];
     if (tr->mu) tr->mu[it] = td[2 * it + 1];
   }
   tls_err.clear();
   return HBACA_OK;
+}
+
+hbaca_status hbaca_read_leaf_trace(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t leaf,
+                                   hbaca_leaf_trace* trace, void* stream) {
+  return read_trace(1, gen, opts, workspace, 0, leaf, trace, stream);
+}
+
+hbaca_status hbaca_read_leaf_trace_batched(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                           const void* workspace, int32_t block, int64_t leaf,
+                                           hbaca_leaf_trace* trace, void* stream) {
+  return read_trace(nblocks, gens, opts, workspace, block, leaf, trace, stream);
 }
 
 hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace,
@@ -221,25 +258,25 @@ hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts
   if (!gen || !opts || !workspace) return fail(HBACA_INVALID_ARG, "NULL argument");
   hbaca::Plan p;
   std::string err;
-  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
-  const hbaca::StoreLevel* lv = nullptr;
+  if (!hbaca::make_plan(gen, 1, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
+  const std::vector<int>* idx = nullptr;
   const hbaca::Region *ru, *rs, *rv;
-  if (store == 0 && level >= 0 && level < p.L) {
-    lv = &p.full_lv[level];
+  if (store == 0 && level >= 0 && level < p.Lb[0]) {
+    idx = &p.full_idx[0][level];
     ru = &p.full_u; rs = &p.full_s; rv = &p.full_v;
-  } else if (store == 1 && level >= 1 && level <= p.L) {
-    lv = &p.half_lv[level];
+  } else if (store == 1 && level >= 1 && level <= p.Lb[0]) {
+    idx = &p.half_idx[0][level];
     ru = &p.half_u; rs = &p.half_s; rv = &p.half_v;
   } else {
     return fail(HBACA_INVALID_ARG, "no such store level");
   }
-  if (block < 0 || block >= lv->nblocks) return fail(HBACA_INVALID_ARG, "block index out of range");
+  if (block < 0 || block >= (int64_t)idx->size()) return fail(HBACA_INVALID_ARG, "block index out of range");
   hbaca::BlockRef b;
-  std::memcpy(&b, p.desc.data() + lv->refs_off + block * sizeof(b), sizeof(b));
+  std::memcpy(&b, p.desc.data() + p.refs_off + (size_t)(*idx)[block] * sizeof(b), sizeof(b));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const char* ws = reinterpret_cast<const char*>(workspace);
   int32_t rank = 0;
-  cudaError_t e = cudaMemcpyAsync(&rank, ws + lv->rank_off + b.rank_slot * 4, 4, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(&rank, ws + p.ranks_off + (size_t)b.rank_slot * 4, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && rank > 0) {
     if (U) e = cudaMemcpyAsync(U, ws + ru->off + b.u_off * p.esz, (size_t)b.m * rank * p.esz, cudaMemcpyDeviceToHost, st);
@@ -251,7 +288,7 @@ hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts
   if (m_out) *m_out = b.m;
   if (n_out) *n_out = b.n;
   if (rank_out) *rank_out = rank;
-  if (cap_out) *cap_out = p.rank_cap;
+  if (cap_out) *cap_out = b.cap;
   tls_err.clear();
   return HBACA_OK;
 }
@@ -278,7 +315,7 @@ size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char*
   if (!gen || !opts) return 0;
   hbaca::Plan p;
   std::string err;
-  if (!hbaca::make_plan(*gen, *opts, current_sms(), p, err)) { tls_err = err; return 0; }
+  if (!hbaca::make_plan(gen, 1, *opts, current_sms(), p, err)) { tls_err = err; return 0; }
   std::string j = "{";
   auto reg = [&](const char* name, const hbaca::Region& r) {
     j += std::string("\"") + name + "\": [" + std::to_string(r.off) + ", " + std::to_string(r.bytes) + "], ";
@@ -288,7 +325,7 @@ size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char*
   reg("full_u", p.full_u); reg("full_s", p.full_s); reg("full_v", p.full_v);
   reg("half_u", p.half_u); reg("half_s", p.half_s); reg("half_v", p.half_v);
   j += "\"leafout\": " + std::to_string(p.leafout_off) + ", \"leafdesc\": " + std::to_string(p.leafdesc_off) + ", ";
-  j += "\"baca_cluster\": " + std::to_string(p.baca_cluster) + ", \"rank_cap\": " + std::to_string(p.rank_cap) + ", ";
+  j += "\"baca_cluster\": " + std::to_string(p.baca_cluster) + ", \"rank_cap\": " + std::to_string(p.rank_cap_max) + ", ";
   j += "\"stages\": [";
   for (size_t si = 0; si < p.stages.size(); ++si) {
     const hbaca::Stage& st = p.stages[si];

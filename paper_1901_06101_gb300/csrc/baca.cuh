@@ -36,6 +36,7 @@ struct BacaParams {
   using T = typename Gen::scalar;
   Gen gen;
   const LeafDesc* leaves;
+  const int32_t* order;  // processing order of the leaves (largest first)
   LeafOut* out;
   int nleaves;
   int* queue;
@@ -385,7 +386,10 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
   unsigned ctr = 0;
 
   for (;;) {
-    if (q == 0 && tid == 0) S.sint[8] = atomicAdd(P.queue, 1);
+    if (q == 0 && tid == 0) {
+      const int slot = atomicAdd(P.queue, 1);
+      S.sint[8] = slot < P.nleaves ? P.order[slot] : P.nleaves;
+    }
     cl.sync();
     int leaf;
     {
@@ -394,6 +398,7 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
     }
     if (leaf >= P.nleaves) break;
     const LeafDesc Lf = P.leaves[leaf];
+    const auto gen = P.gen.bind(Lf.block);
     const int m = Lf.m, n = Lf.n;
     const int mchunk = (m + c - 1) / c, nchunk = (n + c - 1) / c;
     const int ra = min(m, q * mchunk), mr = min(m, ra + mchunk) - ra;
@@ -422,7 +427,7 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
         const T* vp = V + jc;
 #pragma unroll 4
         for (int p = 0; p < r; ++p) acc = mac(acc, up[(size_t)p * m], ldcg(vp + (size_t)p * n));
-        T val = sub(P.gen(Lf.row0 + i, Lf.col0 + jc), acc);
+        T val = sub(gen(Lf.row0 + i, Lf.col0 + jc), acc);
         S.work[(size_t)j * mr + il] = val;
         Cg[(size_t)j * m + i] = val;
       }
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
         const T* vp = V + j;
 #pragma unroll 4
         for (int p = 0; p < r; ++p) acc = mac(acc, ldcg(up + (size_t)p * m), vp[(size_t)p * n]);
-        T val = sub(P.gen(Lf.row0 + i, Lf.col0 + j), acc);
+        T val = sub(gen(Lf.row0 + i, Lf.col0 + j), acc);
         S.work[(size_t)s * nc + jl] = val;
         Rg[(size_t)s * n + j] = val;
       }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "hbaca.h"
+#include "types.h"
 
 namespace hbaca {
 
@@ -127,12 +128,14 @@ __device__ __forceinline__ void householder(T alpha, double sig2, double& beta, 
 // Each generator maps global (row, column) indices to one entry.  They are
 // passed by value into the kernels and inlined into the residual updates.
 struct GenDense {
+  __device__ __forceinline__ GenDense bind(int) const { return *this; }
   using scalar = double;
   const double* a;
   int64_t lda;
   __device__ __forceinline__ double operator()(int64_t i, int64_t j) const { return a[j * lda + i]; }
 };
 struct GenDenseC {
+  __device__ __forceinline__ GenDenseC bind(int) const { return *this; }
   using scalar = cplx;
   const cplx* a;
   int64_t lda;
@@ -140,6 +143,7 @@ struct GenDenseC {
 };
 
 struct GenGaussian {
+  __device__ __forceinline__ GenGaussian bind(int) const { return *this; }
   using scalar = double;
   const double* x;
   const double* y;
@@ -163,6 +167,7 @@ struct GenGaussian {
 };
 
 struct GenHelmholtz {
+  __device__ __forceinline__ GenHelmholtz bind(int) const { return *this; }
   using scalar = cplx;
   const double* x;
   const double* y;
@@ -185,6 +190,7 @@ struct GenHelmholtz {
 };
 
 struct GenLowRank {
+  __device__ __forceinline__ GenLowRank bind(int) const { return *this; }
   using scalar = double;
   const double* lu;  // m x lr, column-major, ld = m
   const double* lv;  // lr x n, row-major, ld = n
@@ -196,6 +202,7 @@ struct GenLowRank {
   }
 };
 struct GenLowRankC {
+  __device__ __forceinline__ GenLowRankC bind(int) const { return *this; }
   using scalar = cplx;
   const cplx* lu;
   const cplx* lv;
@@ -210,6 +217,7 @@ struct GenLowRankC {
 // A(i,j) = sum_k P(i,k) Q(k,j) + sum_t P2(i,t) Q2(t,j): a sorted-list
 // intersection of row i of P (CSR) with column j of Q (CSC), then the dense term.
 struct GenSparseProduct {
+  __device__ __forceinline__ GenSparseProduct bind(int) const { return *this; }
   using scalar = double;
   const int32_t* prp;
   const int32_t* pci;
@@ -240,6 +248,22 @@ struct GenSparseProduct {
     double t = 0.0;
     for (int u = 0; u < r2; ++u) t = fma(p2[i * r2 + u], q2[u * n + j], t);
     return s + t;
+  }
+};
+
+// Batched Gaussian blocks: each block b has its own points and width; a leaf
+// binds the generator of its block once (batched form of Alg. 2 / Alg. 3).
+struct GenGaussianBatch {
+  using scalar = double;
+  const GaussBlockParams* blocks;
+  __device__ __forceinline__ GenGaussian bind(int b) const {
+    const GaussBlockParams q = blocks[b];
+    GenGaussian g;
+    g.x = q.x;
+    g.y = q.y;
+    g.dim = q.dim;
+    g.c = q.c;
+    return g;
   }
 };
 

@@ -70,6 +70,21 @@ __device__ __forceinline__ T* qr_a_ptr(const DenseParams<T>& P, const SvdTask& t
   return (t.a_in_baca ? P.Uar : P.qr) + t.a_off;
 }
 
+// Output addresses of a block: the caller's buffers for a block's final
+// result, otherwise the output store arena plus the block's offsets.
+template <typename T>
+__device__ __forceinline__ T* out_u(const DenseParams<T>& P, const BlockRef& b) {
+  return b.U ? reinterpret_cast<T*>(b.U) : P.outU + b.u_off;
+}
+template <typename T>
+__device__ __forceinline__ T* out_v(const DenseParams<T>& P, const BlockRef& b) {
+  return b.V ? reinterpret_cast<T*>(b.V) : P.outV + b.v_off;
+}
+template <typename T>
+__device__ __forceinline__ double* out_s(const DenseParams<T>& P, const BlockRef& b) {
+  return b.S ? b.S : P.outS + b.s_off;
+}
+
 // ------------------------------------------------------------------ pack
 // Build the QR operands and the task dimensions.
 template <typename T>
@@ -603,11 +618,11 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
       if (s1 > 0.0 && isfinite(s1))
         while (s < nc && s < mr && sv[ord[s]] >= P.eps * s1) ++s;
       if (!isfinite(s1)) set_status(P.status, DS_NUMERICAL);
-      if (s > P.out_cap) { set_status(P.status, DS_RANK_CAPACITY); s = (int)P.out_cap; }
+      const BlockRef ob = P.out_blocks[t.out];
+      if (s > ob.cap) { set_status(P.status, DS_RANK_CAPACITY); s = ob.cap; }
       sshare[0] = s;
       P.dims[ti].s = s;
       P.dims[ti].sweeps = sweep;
-      const BlockRef ob = P.out_blocks[t.out];
       P.out_rank[ob.rank_slot] = s;
     }
   }
@@ -622,7 +637,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
       const double sg = sv0[j];
       const double inv = 1.0 / sg;
       for (int i = lane; i < mr; i += 32) M[(int64_t)j * ld + i] = scale(ldcg(M + (int64_t)j * ld + i), inv);
-      if (lane == 0) P.outS[ob.s_off + tc] = sg;
+      if (lane == 0) out_s(P, ob)[tc] = sg;
     }
   }
   cl.sync();
@@ -697,7 +712,7 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   const T* tau = P.tau + t.tau_off + (jb.which ? t.kcap : 0);
   const T* Z = P.core + (jb.which ? t.ys_off : t.xs_off);  // compact, column tc
   const BlockRef ob = P.out_blocks[t.out];
-  T* D = jb.to_v ? P.outV + ob.v_off : P.outU + ob.u_off;
+  T* D = jb.to_v ? out_v(P, ob) : out_u(P, ob);
   const int64_t ldd = jb.to_v ? ob.ldv : ob.ldu;
   if (s <= 0) return;
   const int chunk = (rows + c - 1) / c;
@@ -770,7 +785,7 @@ __global__ void blockprod_kernel(const DenseParams<T> P) {
         const T* ys = Y + (int64_t)tc * t.kcap + r1;
         for (int p = 0; p < r2; ++p) acc = cmac(acc, ys[p], P.inV[b2.v_off + (int64_t)p * b2.ldv + (j - n1)]);
       }
-      P.outV[ob.v_off + (int64_t)tc * ob.ldv + j] = acc;
+      out_v(P, ob)[(int64_t)tc * ob.ldv + j] = acc;
     }
   } else {
     const int m1 = b1.m, mtot = b1.m + b2.m;
@@ -784,7 +799,7 @@ __global__ void blockprod_kernel(const DenseParams<T> P) {
         const T* ys = Y + (int64_t)tc * t.kcap + r1;
         for (int p = 0; p < r2; ++p) acc = mac(acc, P.inU[b2.u_off + (int64_t)p * b2.ldu + (i - m1)], ys[p]);
       }
-      P.outU[ob.u_off + (int64_t)tc * ob.ldu + i] = acc;
+      out_u(P, ob)[(int64_t)tc * ob.ldu + i] = acc;
     }
   }
 }

@@ -5,7 +5,7 @@
 namespace hbaca {
 
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err) {
-  const hbaca_gen& g = p.gen;
+  const hbaca_gen& g = p.gens[0];
   cudaError_t e = cudaErrorInvalidValue;
   switch (g.kind) {
     case HBACA_GEN_DENSE: {

@@ -5,7 +5,7 @@
 namespace hbaca {
 
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err) {
-  const hbaca_gen& g = p.gen;
+  const hbaca_gen& g = p.gens[0];
   cudaError_t e = cudaErrorInvalidValue;
   switch (g.kind) {
     case HBACA_GEN_DENSE: {
@@ -13,8 +13,8 @@ cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err) {
       e = run_baca(p, gd, rc, err);
       break;
     }
-    case HBACA_GEN_GAUSSIAN: {
-      GenGaussian gg{g.x, g.y, g.dim, -1.0 / (2.0 * g.h * g.h)};
+    case HBACA_GEN_GAUSSIAN: {  // one block or many: per-block points and widths
+      GenGaussianBatch gg{reinterpret_cast<const GaussBlockParams*>(rc.ws + p.desc_region.off + p.gparams_off)};
       e = run_baca(p, gg, rc, err);
       break;
     }

@@ -58,6 +58,7 @@ cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
   BacaParams<Gen> P;
   P.gen = gen;
   P.leaves = reinterpret_cast<const LeafDesc*>(ws + p.desc_region.off + p.leafdesc_off);
+  P.order = reinterpret_cast<const int32_t*>(ws + p.desc_region.off + p.order_off);
   P.out = reinterpret_cast<LeafOut*>(ws + p.leafout_off);
   P.nleaves = p.nleaves;
   P.queue = reinterpret_cast<int*>(ws + p.queue.off);
@@ -120,46 +121,36 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
   D.Var = reinterpret_cast<T*>(ws + p.var.off);
   D.leaf_rank = reinterpret_cast<const int32_t*>(ws + p.leafout_off);
   D.leaf_rank_stride = (int)(sizeof(LeafOut) / sizeof(int32_t));
-  auto store = [&](int id, int level, const BlockRef*& refs, int32_t*& rank, T*& U, double*& S, T*& V) {
+  // every block reference and its rank live in one table / one array; the
+  // stage's input and output store arenas are the full (0) or half (1) store
+  auto arena = [&](int id, T*& U, double*& S, T*& V) {
     if (id == 0) {
-      refs = reinterpret_cast<const BlockRef*>(desc + p.full_lv[level].refs_off);
-      rank = reinterpret_cast<int32_t*>(ws + p.full_lv[level].rank_off);
       U = reinterpret_cast<T*>(ws + p.full_u.off);
       S = reinterpret_cast<double*>(ws + p.full_s.off);
       V = reinterpret_cast<T*>(ws + p.full_v.off);
     } else if (id == 1) {
-      refs = reinterpret_cast<const BlockRef*>(desc + p.half_lv[level].refs_off);
-      rank = reinterpret_cast<int32_t*>(ws + p.half_lv[level].rank_off);
       U = reinterpret_cast<T*>(ws + p.half_u.off);
       S = reinterpret_cast<double*>(ws + p.half_s.off);
       V = reinterpret_cast<T*>(ws + p.half_v.off);
     } else {
-      refs = reinterpret_cast<const BlockRef*>(desc + p.user_ref_off);
-      rank = reinterpret_cast<int32_t*>(ws + p.user_lv.rank_off);
-      U = reinterpret_cast<T*>(rc.res->U);
-      S = rc.res->S;
-      V = reinterpret_cast<T*>(rc.res->V);
+      U = nullptr;
+      S = nullptr;
+      V = nullptr;
     }
   };
+  const BlockRef* refs = reinterpret_cast<const BlockRef*>(desc + p.refs_off);
+  int32_t* ranks = reinterpret_cast<int32_t*>(ws + p.ranks_off);
+  D.in_blocks = refs;
+  D.in_rank = ranks;
+  D.out_blocks = refs;
+  D.out_rank = ranks;
   {
-    const BlockRef* r = nullptr;
-    int32_t* rk = nullptr;
-    T *U = nullptr, *V = nullptr;
-    double* S = nullptr;
-    if (sg.in_store >= 0) store(sg.in_store, sg.in_level, r, rk, U, S, V);
-    D.in_blocks = r;
-    D.in_rank = rk;
-    D.inU = U;
-    D.inS = S;
-    D.inV = V;
-    store(sg.out_store, sg.out_level, r, rk, U, S, V);
-    D.out_blocks = r;
-    D.out_rank = rk;
-    D.outU = U;
-    D.outS = S;
-    D.outV = V;
+    double* in_s = nullptr;
+    arena(sg.in_store, D.inU, in_s, D.inV);
+    D.inS = in_s;
+    arena(sg.out_store, D.outU, D.outS, D.outV);
   }
-  D.out_cap = p.rank_cap;
+  D.out_cap = p.rank_cap_max;
   D.qr = reinterpret_cast<T*>(ws + p.qr.off);
   D.tau = reinterpret_cast<T*>(ws + p.tau.off);
   D.core = reinterpret_cast<T*>(ws + p.core.off);
@@ -187,7 +178,7 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
   finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D);
   HB_TRY(cudaGetLastError());
   rc.launches += 2;
-  const size_t qa_smem = (size_t)3 * p.rank_cap * sizeof(T) + 64;
+  const size_t qa_smem = (size_t)3 * p.rank_cap_max * sizeof(T) + 64;
   HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj));
   rc.launches += 5;
   if (sg.kind != TASK_LEAF) {

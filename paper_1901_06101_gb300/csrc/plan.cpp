@@ -1,8 +1,10 @@
-// Host planning of an H-BACA call (trees, leaves, merge stages, workspace).
+// Host planning of an H-BACA call over one or many blocks (trees, leaves,
+// merge stages, workspace layout).
 #include "plan.h"
 
 #include <algorithm>
 #include <cstring>
+#include <numeric>
 
 #include "types.h"
 
@@ -36,22 +38,7 @@ size_t baca_smem(size_t esz, int mr, int nc, int d) {
   return b;
 }
 
-}  // namespace
-
-std::vector<std::vector<Span>> tree_levels(int64_t n, int L) {
-  std::vector<std::vector<Span>> lv(L + 1);
-  lv[L] = {Span(0, n)};
-  for (int l = L; l > 0; --l) {
-    for (const Span& s : lv[l]) {
-      int64_t a = (s.second + 1) / 2;
-      lv[l - 1].push_back(Span(s.first, a));
-      lv[l - 1].push_back(Span(s.first + a, s.second - a));
-    }
-  }
-  return lv;
-}
-
-static bool check_gen(const hbaca_gen& g, std::string& err) {
+bool check_gen(const hbaca_gen& g, std::string& err) {
   if (g.m < 1 || g.n < 1 || g.m >= (1ll << 31) || g.n >= (1ll << 31)) { err = "m and n must be in [1, 2^31)"; return false; }
   if (g.dtype != HBACA_F64 && g.dtype != HBACA_C128) { err = "unknown dtype"; return false; }
   switch (g.kind) {
@@ -84,62 +71,123 @@ static bool check_gen(const hbaca_gen& g, std::string& err) {
   return true;
 }
 
-bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::string& err) {
-  if (!check_gen(g, err)) return false;
-  if (!(o.eps > 0.0 && o.eps < 1.0)) { err = "eps must be in (0, 1)"; return false; }
-  if (o.d < 1 || o.d > 32) { err = "d must be in [1, 32]"; return false; }
-  if (o.levels < 0 || o.levels > 12 || (1ll << o.levels) > std::min(g.m, g.n)) {
-    err = "levels L needs 0 <= L <= 12 and 2^L <= min(m, n)";
+}  // namespace
+
+std::vector<std::vector<Span>> tree_levels(int64_t n, int L) {
+  std::vector<std::vector<Span>> lv(L + 1);
+  lv[L] = {Span(0, n)};
+  for (int l = L; l > 0; --l) {
+    for (const Span& s : lv[l]) {
+      int64_t a = (s.second + 1) / 2;
+      lv[l - 1].push_back(Span(s.first, a));
+      lv[l - 1].push_back(Span(s.first + a, s.second - a));
+    }
+  }
+  return lv;
+}
+
+int block_levels(int64_t m, int64_t n, int levels) {
+  int L = levels;
+  if (levels < 0) {
+    const int64_t target = -(int64_t)levels;
+    L = 0;
+    while ((std::max(m, n) + (1ll << L) - 1) / (1ll << L) > target) ++L;
+    while (L > 0 && (1ll << L) > std::min(m, n)) --L;
+    return L;
+  }
+  if ((1ll << L) > std::min(m, n)) return -1;
+  return L;
+}
+
+bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms, Plan& p, std::string& err) {
+  if (!gens || nblocks < 1) { err = "need at least one block"; return false; }
+  for (int b = 0; b < nblocks; ++b) {
+    if (!check_gen(gens[b], err)) { err = "block " + std::to_string(b) + ": " + err; return false; }
+    if (gens[b].kind != gens[0].kind || gens[b].dtype != gens[0].dtype) {
+      err = "all blocks must share the generator kind and dtype";
+      return false;
+    }
+  }
+  if (nblocks > 1 && gens[0].kind != HBACA_GEN_GAUSSIAN) {
+    err = "batched compression is available for the GAUSSIAN generator";
     return false;
   }
+  if (!(o.eps > 0.0 && o.eps < 1.0)) { err = "eps must be in (0, 1)"; return false; }
+  if (o.d < 1 || o.d > 32) { err = "d must be in [1, 32]"; return false; }
+  if (o.levels > 12 || o.levels < -(1 << 30)) { err = "levels out of range"; return false; }
   if (o.cluster != 0 && (o.cluster < 1 || o.cluster > 16 || (o.cluster & (o.cluster - 1)))) {
     err = "cluster must be 0 or a power of two <= 16";
     return false;
   }
   if (o.rank_cap < 0 || o.leaf_rank_cap < 0) { err = "rank caps must be >= 0"; return false; }
   if (sms <= 0) sms = 152;
-  p.gen = g;
+  p.gens.assign(gens, gens + nblocks);
   p.opts = o;
-  p.cplx = g.dtype == HBACA_C128;
+  p.cplx = gens[0].dtype == HBACA_C128;
   p.esz = p.cplx ? 16 : 8;
-  p.L = o.levels;
   p.d = o.d;
-  p.m = g.m;
-  p.n = g.n;
-  const int64_t mn = std::min(g.m, g.n);
-  p.rank_cap = o.rank_cap ? std::min<int64_t>(o.rank_cap, mn) : std::min<int64_t>(mn, 1024);
-  p.rows = tree_levels(g.m, p.L);
-  p.cols = tree_levels(g.n, p.L);
-  const int nb = 1 << p.L;
-  p.nleaves = nb * nb;
+  p.nblocks = nblocks;
+  p.Lb.resize(nblocks);
+  p.cap_b.resize(nblocks);
+  p.Lmax = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    const int L = block_levels(gens[b].m, gens[b].n, o.levels);
+    if (L < 0) {
+      err = "block " + std::to_string(b) + ": levels L needs 2^L <= min(m, n)";
+      return false;
+    }
+    p.Lb[b] = L;
+    p.Lmax = std::max(p.Lmax, L);
+    const int64_t mn = std::min(gens[b].m, gens[b].n);
+    p.cap_b[b] = o.rank_cap ? std::min<int64_t>(o.rank_cap, mn) : std::min<int64_t>(mn, 1024);
+    p.rank_cap_max = std::max(p.rank_cap_max, p.cap_b[b]);
+  }
 
-  // ---- leaves
-  std::vector<LeafDesc> leaves(p.nleaves);
+  // ---- leaves (block by block, row-major over the leaf grid)
+  std::vector<LeafDesc> leaves;
+  std::vector<std::vector<std::vector<Span>>> rows(nblocks), cols(nblocks);
+  p.leaf_first.assign(nblocks, 0);
   int64_t uo = 0, vo = 0, to = 0, tdo = 0;
   const int rec = 4 + 3 * p.d;
-  for (int a = 0; a < nb; ++a)
-    for (int b = 0; b < nb; ++b) {
-      LeafDesc& L = leaves[a * nb + b];
-      L.row0 = p.rows[0][a].first;
-      L.col0 = p.cols[0][b].first;
-      L.m = (int32_t)p.rows[0][a].second;
-      L.n = (int32_t)p.cols[0][b].second;
-      int64_t lc = o.leaf_rank_cap ? o.leaf_rank_cap : 1024;
-      L.rcap = (int32_t)std::min<int64_t>(std::min<int64_t>(L.m, L.n), lc);
-      L.tape_iters = std::min(L.m, L.n);
-      L.stream_id = ((int64_t)a << 12) | b;
-      L.u_off = uo;
-      L.v_off = vo;
-      L.tape_off = to;
-      L.taped_off = tdo;
-      uo += (int64_t)L.m * L.rcap;
-      vo += (int64_t)L.rcap * L.n;
-      to += (int64_t)L.tape_iters * rec;
-      tdo += (int64_t)L.tape_iters * 2;
-      p.mmax = std::max(p.mmax, L.m);
-      p.nmax = std::max(p.nmax, L.n);
-      p.rcap_max = std::max(p.rcap_max, L.rcap);
-    }
+  for (int b = 0; b < nblocks; ++b) {
+    rows[b] = tree_levels(gens[b].m, p.Lb[b]);
+    cols[b] = tree_levels(gens[b].n, p.Lb[b]);
+    p.leaf_first[b] = (int)leaves.size();
+    const int nb = 1 << p.Lb[b];
+    for (int a = 0; a < nb; ++a)
+      for (int c = 0; c < nb; ++c) {
+        LeafDesc L;
+        std::memset(&L, 0, sizeof(L));
+        L.row0 = rows[b][0][a].first;
+        L.col0 = cols[b][0][c].first;
+        L.m = (int32_t)rows[b][0][a].second;
+        L.n = (int32_t)cols[b][0][c].second;
+        int64_t lc = o.leaf_rank_cap ? o.leaf_rank_cap : 1024;
+        L.rcap = (int32_t)std::min<int64_t>(std::min<int64_t>(L.m, L.n), lc);
+        L.tape_iters = std::min(L.m, L.n);
+        L.stream_id = ((int64_t)b << 24) | ((int64_t)a << 12) | c;
+        L.u_off = uo;
+        L.v_off = vo;
+        L.tape_off = to;
+        L.taped_off = tdo;
+        L.block = b;
+        uo += (int64_t)L.m * L.rcap;
+        vo += (int64_t)L.rcap * L.n;
+        to += (int64_t)L.tape_iters * rec;
+        tdo += (int64_t)L.tape_iters * 2;
+        p.mmax = std::max(p.mmax, L.m);
+        p.nmax = std::max(p.nmax, L.n);
+        p.rcap_max = std::max(p.rcap_max, L.rcap);
+        leaves.push_back(L);
+      }
+  }
+  p.nleaves = (int)leaves.size();
+  // processing order: largest leaves first, so the persistent clusters finish together
+  std::vector<int32_t> order(p.nleaves);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return (int64_t)leaves[x].m * leaves[x].n > (int64_t)leaves[y].m * leaves[y].n;
+  });
 
   // ---- BACA cluster size: enough CTAs to cover the SMs, shared memory within budget
   int c = o.cluster;
@@ -154,7 +202,6 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
   p.baca_smem = baca_smem(p.esz, p.mr_max, p.nc_max, p.d);
   if (p.baca_smem > 227 * 1024) { err = "leaf too large for shared memory even with 16-CTA clusters"; return false; }
   {
-    // resident clusters are bounded by SMs x CTAs per SM / c
     size_t per_sm = std::min<size_t>(8, std::max<size_t>(1, (228 * 1024) / (p.baca_smem + 1024)));
     p.max_clusters_scratch = (int)std::max<int64_t>(1, std::min<int64_t>(p.nleaves, (int64_t)sms * per_sm / c));
   }
@@ -162,52 +209,64 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
   p.rscr_stride = (int64_t)p.d * p.nmax;
   p.gscr_stride = (int64_t)2 * c * p.rcap_max * p.d;
 
-  // ---- stores and stages
-  const int64_t cap = p.rank_cap;
-  // full store levels 0..L-1 (level L goes to the user), half store levels 1..L
-  struct BlockPlan { std::vector<BlockRef> refs; };
-  std::vector<BlockPlan> full(p.L + 1), half(p.L + 1);
+  // ---- block references: full store (after the vertical merge of level l),
+  // half store (after the horizontal merge of level l), one result per block;
+  // every reference's rank lives at its own index of one rank array
+  std::vector<BlockRef> refs;
+  p.full_idx.assign(nblocks, std::vector<std::vector<int>>(p.Lmax + 1));
+  p.half_idx.assign(nblocks, std::vector<std::vector<int>>(p.Lmax + 1));
   size_t full_u = 0, full_s = 0, full_v = 0, half_u = 0, half_s = 0, half_v = 0;
-  for (int l = 0; l < p.L; ++l) {
+  auto add_ref = [&](int64_t m, int64_t n, int64_t cap, int64_t& u, int64_t& s, int64_t& v) {
+    BlockRef r;
+    std::memset(&r, 0, sizeof(r));
+    r.m = (int32_t)m;
+    r.n = (int32_t)n;
+    r.u_off = u; r.s_off = s; r.v_off = v;
+    r.ldu = m; r.ldv = n;
+    r.rank_slot = (int32_t)refs.size();
+    r.cap = (int32_t)cap;
+    u += m * cap; s += cap; v += cap * n;
+    refs.push_back(r);
+    return (int)refs.size() - 1;
+  };
+  for (int l = 0; l < p.Lmax; ++l) {  // full store level l: blocks with L_b > l
     int64_t u = 0, s = 0, v = 0;
-    const int nr = (int)p.rows[l].size(), ncn = (int)p.cols[l].size();
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < ncn; ++b) {
-        BlockRef r{};
-        r.m = (int32_t)p.rows[l][a].second;
-        r.n = (int32_t)p.cols[l][b].second;
-        r.u_off = u; r.s_off = s; r.v_off = v;
-        r.ldu = r.m; r.ldv = r.n;
-        r.rank_slot = a * ncn + b;
-        u += r.m * cap; s += cap; v += cap * r.n;
-        full[l].refs.push_back(r);
-      }
+    for (int b = 0; b < nblocks; ++b) {
+      if (p.Lb[b] <= l) continue;
+      const int nr = (int)rows[b][l].size(), ncn = (int)cols[b][l].size();
+      p.full_idx[b][l].assign(nr * ncn, -1);
+      for (int a = 0; a < nr; ++a)
+        for (int cc = 0; cc < ncn; ++cc)
+          p.full_idx[b][l][a * ncn + cc] = add_ref(rows[b][l][a].second, cols[b][l][cc].second, p.cap_b[b], u, s, v);
+    }
     full_u = std::max<size_t>(full_u, u); full_s = std::max<size_t>(full_s, s); full_v = std::max<size_t>(full_v, v);
   }
-  for (int l = 1; l <= p.L; ++l) {
+  for (int l = 1; l <= p.Lmax; ++l) {  // half store level l: blocks with L_b >= l
     int64_t u = 0, s = 0, v = 0;
-    const int nr = (int)p.rows[l - 1].size(), ncn = (int)p.cols[l].size();
-    for (int a = 0; a < nr; ++a)
-      for (int b = 0; b < ncn; ++b) {
-        BlockRef r{};
-        r.m = (int32_t)p.rows[l - 1][a].second;
-        r.n = (int32_t)p.cols[l][b].second;
-        r.u_off = u; r.s_off = s; r.v_off = v;
-        r.ldu = r.m; r.ldv = r.n;
-        r.rank_slot = a * ncn + b;
-        u += r.m * cap; s += cap; v += cap * r.n;
-        half[l].refs.push_back(r);
-      }
+    for (int b = 0; b < nblocks; ++b) {
+      if (p.Lb[b] < l) continue;
+      const int nr = (int)rows[b][l - 1].size(), ncn = (int)cols[b][l].size();
+      p.half_idx[b][l].assign(nr * ncn, -1);
+      for (int a = 0; a < nr; ++a)
+        for (int cc = 0; cc < ncn; ++cc)
+          p.half_idx[b][l][a * ncn + cc] = add_ref(rows[b][l - 1][a].second, cols[b][l][cc].second, p.cap_b[b], u, s, v);
+    }
     half_u = std::max<size_t>(half_u, u); half_s = std::max<size_t>(half_s, s); half_v = std::max<size_t>(half_v, v);
   }
+  p.user_ref_first = (int)refs.size();
+  for (int b = 0; b < nblocks; ++b) {
+    int64_t z = 0, z2 = 0, z3 = 0;
+    add_ref(gens[b].m, gens[b].n, p.cap_b[b], z, z2, z3);
+  }
+  p.nrefs = (int)refs.size();
 
-  // tasks, grouped into chunks whose scratch (QR operands, cores) fits the budget;
-  // scratch offsets are local to a chunk, chunks of a stage run one after another
+  // ---- tasks, grouped into chunks whose scratch (QR operands, cores) fits the
+  // budget; scratch offsets are local to a chunk, chunks run one after another
   p.task_storage.clear();
   p.stages.clear();
   size_t qr_elems = 0, tau_elems = 0, core_elems = 0, ord_elems = 0;
   const size_t budget = (size_t)8 << 30;  // bytes of chunk scratch
-  auto add_stage = [&](std::vector<SvdTask>& all, int kind, int in_store, int in_level, int out_store, int out_level) {
+  auto add_stage = [&](std::vector<SvdTask>& all, int kind, int in_store, int out_store) {
     size_t i = 0;
     while (i < all.size()) {
       std::vector<SvdTask> ch;
@@ -242,8 +301,8 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
       st.ntasks = (int)ch.size();
       st.kcap = kmx;
       st.rows_max = rmax;
-      st.in_store = in_store; st.in_level = in_level;
-      st.out_store = out_store; st.out_level = out_level;
+      st.in_store = in_store;
+      st.out_store = out_store;
       p.task_storage.push_back(ch);
       p.stages.push_back(st);
     }
@@ -251,65 +310,71 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
   {
     std::vector<SvdTask> ts(p.nleaves);
     for (int i = 0; i < p.nleaves; ++i) {
+      const LeafDesc& L = leaves[i];
+      const int b = L.block;
+      const int nb = 1 << p.Lb[b];
+      const int a = (i - p.leaf_first[b]) / nb, cc = (i - p.leaf_first[b]) % nb;
       SvdTask& t = ts[i];
       std::memset(&t, 0, sizeof(t));
       t.kind = TASK_LEAF;
-      t.kcap = leaves[i].rcap;
+      t.kcap = L.rcap;
       t.in1 = i;
-      t.a_off = leaves[i].u_off;
+      t.a_off = L.u_off;
       t.a_in_baca = 1;
-      t.rows_a = leaves[i].m;
-      t.lda = leaves[i].m;
-      t.rows_b = leaves[i].n;
-      t.src_v_off = leaves[i].v_off;
-      t.out = i;
+      t.rows_a = L.m;
+      t.lda = L.m;
+      t.rows_b = L.n;
+      t.src_v_off = L.v_off;
+      t.out = p.Lb[b] == 0 ? p.user_ref_first + b : p.full_idx[b][0][a * nb + cc];
     }
-    add_stage(ts, TASK_LEAF, -1, 0, p.L == 0 ? 2 : 0, 0);
+    add_stage(ts, TASK_LEAF, -1, 0);
   }
-  for (int l = 1; l <= p.L; ++l) {
-    const int64_t kc = std::min<int64_t>(2 * cap, 2 * mn);
-    {  // horizontal: row nodes at level l-1, column nodes at level l
-      const int nr = (int)p.rows[l - 1].size(), ncn = (int)p.cols[l].size(), ncp = (int)p.cols[l - 1].size();
-      std::vector<SvdTask> ts;
-      for (int a = 0; a < nr; ++a)
-        for (int b = 0; b < ncn; ++b) {
-          SvdTask t;
-          std::memset(&t, 0, sizeof(t));
-          t.kind = TASK_HORIZ;
-          t.kcap = (int32_t)kc;
-          t.in1 = a * ncp + 2 * b;
-          t.in2 = a * ncp + 2 * b + 1;
-          t.rows_a = (int32_t)p.rows[l - 1][a].second;
-          t.lda = t.rows_a;
-          t.out = a * ncn + b;
-          t.m1 = (int32_t)p.cols[l - 1][2 * b].second;
-          ts.push_back(t);
-        }
-      add_stage(ts, TASK_HORIZ, 0, l - 1, 1, l);
+  for (int l = 1; l <= p.Lmax; ++l) {
+    std::vector<SvdTask> th, tv;
+    for (int b = 0; b < nblocks; ++b) {
+      if (p.Lb[b] < l) continue;
+      const int64_t kc = std::min<int64_t>(2 * p.cap_b[b], 2 * std::min(gens[b].m, gens[b].n));
+      {  // horizontal: row nodes at level l-1, column nodes at level l
+        const int nr = (int)rows[b][l - 1].size(), ncn = (int)cols[b][l].size(), ncp = (int)cols[b][l - 1].size();
+        for (int a = 0; a < nr; ++a)
+          for (int cc = 0; cc < ncn; ++cc) {
+            SvdTask t;
+            std::memset(&t, 0, sizeof(t));
+            t.kind = TASK_HORIZ;
+            t.kcap = (int32_t)kc;
+            t.in1 = p.full_idx[b][l - 1][a * ncp + 2 * cc];
+            t.in2 = p.full_idx[b][l - 1][a * ncp + 2 * cc + 1];
+            t.rows_a = (int32_t)rows[b][l - 1][a].second;
+            t.lda = t.rows_a;
+            t.out = p.half_idx[b][l][a * ncn + cc];
+            t.m1 = (int32_t)cols[b][l - 1][2 * cc].second;
+            th.push_back(t);
+          }
+      }
+      {  // vertical: row and column nodes at level l; children in the half store
+        const int nr = (int)rows[b][l].size(), ncn = (int)cols[b][l].size();
+        for (int a = 0; a < nr; ++a)
+          for (int cc = 0; cc < ncn; ++cc) {
+            SvdTask t;
+            std::memset(&t, 0, sizeof(t));
+            t.kind = TASK_VERT;
+            t.kcap = (int32_t)kc;
+            t.in1 = p.half_idx[b][l][(2 * a) * ncn + cc];
+            t.in2 = p.half_idx[b][l][(2 * a + 1) * ncn + cc];
+            t.rows_a = (int32_t)cols[b][l][cc].second;
+            t.lda = t.rows_a;
+            t.out = p.Lb[b] == l ? p.user_ref_first + b : p.full_idx[b][l][a * ncn + cc];
+            t.m1 = (int32_t)rows[b][l - 1][2 * a].second;
+            tv.push_back(t);
+          }
+      }
     }
-    {  // vertical: row and column nodes at level l; children in the half store
-      const int nr = (int)p.rows[l].size(), ncn = (int)p.cols[l].size();
-      std::vector<SvdTask> ts;
-      for (int a = 0; a < nr; ++a)
-        for (int b = 0; b < ncn; ++b) {
-          SvdTask t;
-          std::memset(&t, 0, sizeof(t));
-          t.kind = TASK_VERT;
-          t.kcap = (int32_t)kc;
-          t.in1 = (2 * a) * ncn + b;
-          t.in2 = (2 * a + 1) * ncn + b;
-          t.rows_a = (int32_t)p.cols[l][b].second;
-          t.lda = t.rows_a;
-          t.out = a * ncn + b;
-          t.m1 = (int32_t)p.rows[l - 1][2 * a].second;
-          ts.push_back(t);
-        }
-      add_stage(ts, TASK_VERT, 1, l, l == p.L ? 2 : 0, l);
-    }
+    add_stage(th, TASK_HORIZ, 0, 1);
+    add_stage(tv, TASK_VERT, 1, 0);
   }
   for (size_t i = 0; i < p.stages.size(); ++i) p.stages[i].tasks_h = &p.task_storage[i];
 
-  // ---- descriptor staging (host-written) and device-written tables
+  // ---- descriptor staging (host-written)
   std::vector<char>& D = p.desc;
   D.clear();
   auto put = [&](const void* src, size_t bytes) {
@@ -319,6 +384,19 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
     return off;
   };
   p.leafdesc_off = put(leaves.data(), leaves.size() * sizeof(LeafDesc));
+  p.order_off = put(order.data(), order.size() * sizeof(int32_t));
+  {
+    std::vector<GaussBlockParams> gp(nblocks);
+    for (int b = 0; b < nblocks; ++b) {
+      gp[b].x = gens[b].x;
+      gp[b].y = gens[b].y;
+      gp[b].dim = gens[b].dim;
+      gp[b].pad = 0;
+      gp[b].c = gens[b].h > 0.0 ? -1.0 / (2.0 * gens[b].h * gens[b].h) : 0.0;
+    }
+    p.gparams_off = put(gp.data(), gp.size() * sizeof(GaussBlockParams));
+  }
+  p.refs_off = put(refs.data(), refs.size() * sizeof(BlockRef));
   for (size_t si = 0; si < p.stages.size(); ++si) {
     Stage& st = p.stages[si];
     const std::vector<SvdTask>& ts = *st.tasks_h;
@@ -334,11 +412,11 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
       a.to_v = st.kind == TASK_VERT ? 1 : 0;
       aj.push_back(a);
       if (st.kind == TASK_LEAF) {
-        QJob b{};
-        b.task = i;
-        b.which = 1;
-        b.to_v = 1;
-        aj.push_back(b);
+        QJob bq{};
+        bq.task = i;
+        bq.which = 1;
+        bq.to_v = 1;
+        aj.push_back(bq);
       }
     }
     st.nqr = (int)qj.size();
@@ -346,37 +424,14 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
     st.qrjobs_off = put(qj.data(), qj.size() * sizeof(QrJob));
     st.qjobs_off = put(aj.data(), aj.size() * sizeof(QJob));
   }
-  p.full_lv.assign(p.L + 1, StoreLevel());
-  p.half_lv.assign(p.L + 1, StoreLevel());
-  for (int l = 0; l < p.L; ++l) {
-    p.full_lv[l].nblocks = (int)full[l].refs.size();
-    p.full_lv[l].refs_off = put(full[l].refs.data(), full[l].refs.size() * sizeof(BlockRef));
-  }
-  for (int l = 1; l <= p.L; ++l) {
-    p.half_lv[l].nblocks = (int)half[l].refs.size();
-    p.half_lv[l].refs_off = put(half[l].refs.data(), half[l].refs.size() * sizeof(BlockRef));
-  }
-  {
-    BlockRef u{};
-    u.m = (int32_t)g.m;
-    u.n = (int32_t)g.n;
-    u.ldu = g.m;
-    u.ldv = g.n;
-    p.user_ref_off = put(&u, sizeof(u));
-    p.user_lv.nblocks = 1;
-    p.user_lv.refs_off = p.user_ref_off;
-  }
 
+  // ---- workspace layout
   Layout Lo;
   p.status = Lo.take(64);
   p.queue = Lo.take(64);
   p.desc_region = Lo.take(D.size());
-  Region leafout = Lo.take((size_t)p.nleaves * sizeof(LeafOut));
-  p.leafout_off = leafout.off;
-  // device-written rank tables and task dims
-  for (int l = 0; l < p.L; ++l) p.full_lv[l].rank_off = Lo.take((size_t)p.full_lv[l].nblocks * 4).off;
-  for (int l = 1; l <= p.L; ++l) p.half_lv[l].rank_off = Lo.take((size_t)p.half_lv[l].nblocks * 4).off;
-  p.user_lv.rank_off = Lo.take(4).off;
+  p.leafout_off = Lo.take((size_t)p.nleaves * sizeof(LeafOut)).off;
+  p.ranks_off = Lo.take((size_t)p.nrefs * 4).off;
   for (Stage& st : p.stages) st.dims_off = Lo.take((size_t)st.ntasks * sizeof(TaskDims)).off;
   p.uar = Lo.take((size_t)uo * p.esz);
   p.var = Lo.take((size_t)vo * p.esz);
@@ -399,14 +454,16 @@ bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::s
   return true;
 }
 
-void bind_user_result(Plan& p, const hbaca_result& r) {
-  BlockRef u{};
-  u.m = (int32_t)p.m;
-  u.n = (int32_t)p.n;
+void bind_user_result(Plan& p, int b, const hbaca_result& r) {
+  BlockRef u;
+  const size_t off = p.refs_off + (size_t)(p.user_ref_first + b) * sizeof(BlockRef);
+  std::memcpy(&u, p.desc.data() + off, sizeof(u));
   u.ldu = r.ldu;
   u.ldv = r.ldv;
-  u.rank_slot = 0;
-  std::memcpy(p.desc.data() + p.user_ref_off, &u, sizeof(u));
+  u.U = r.U;
+  u.S = r.S;
+  u.V = r.V;
+  std::memcpy(p.desc.data() + off, &u, sizeof(u));
 }
 
 }  // namespace hbaca

@@ -1,7 +1,8 @@
-// Host-side planning of one H-BACA call: the two L-level index trees
-// (Alg. 3 line 1; first child of a node of size s has ceil(s/2) indices),
-// the leaf table, the per-level merge tasks and the byte layout of the
-// caller's workspace.  Everything here is plain host C++.
+// Host-side planning of an H-BACA call over one or many blocks: the two
+// index trees of every block (Alg. 3 line 1; first child of a node of size s
+// has ceil(s/2) indices), the leaf table and its processing order, the merge
+// tasks of every level, and the byte layout of the caller's workspace.
+// Everything here is plain host C++.
 #pragma once
 
 #include <stdint.h>
@@ -30,7 +31,7 @@ struct Region {
   size_t off = 0, bytes = 0;
 };
 
-// One merge (or leaf re-compression) stage: a batch of tasks launched together.
+// One batch of tasks launched together (a stage of Alg. 3, or a chunk of one).
 struct Stage {
   int kind;                      // TaskKind
   std::vector<SvdTask>* tasks_h; // host copy (owned by Plan)
@@ -39,26 +40,22 @@ struct Stage {
   int nqr = 0, nq = 0;
   int kcap = 0;
   int rows_max = 0;
-  int in_store = -1, out_store = -1;  // store ids: 0 = full, 1 = half, 2 = user
-  int in_level = 0, out_level = 0;    // level index into the BlockRef tables
-};
-
-struct StoreLevel {
-  size_t refs_off = 0;   // BlockRef array (device)
-  size_t rank_off = 0;   // int32 ranks (device)
-  int nblocks = 0;
+  int in_store = -1, out_store = -1;  // block-store arenas: 0 = full, 1 = half
 };
 
 struct Plan {
   // inputs
-  hbaca_gen gen;
+  std::vector<hbaca_gen> gens;  // one per block
   hbaca_opts opts;
   bool cplx = false;
   size_t esz = 8;
-  int L = 0, d = 1;
-  int64_t m = 0, n = 0;
-  int64_t rank_cap = 0, leaf_cap_opt = 0;
-  std::vector<std::vector<Span>> rows, cols;
+  int d = 1;
+  int nblocks = 0;
+  int Lmax = 0;
+  std::vector<int> Lb;            // levels of each block
+  std::vector<int64_t> cap_b;     // rank capacity of each block's output
+  int64_t rank_cap_max = 0;
+  std::vector<int> leaf_first;    // first leaf of each block
   // leaves
   int nleaves = 0;
   int mmax = 0, nmax = 0, rcap_max = 0;
@@ -66,31 +63,38 @@ struct Plan {
   int mr_max = 0, nc_max = 0;
   size_t baca_smem = 0;
   int baca_clusters = 0;  // persistent clusters launched (set at launch time)
-  // host descriptor tables
-  std::vector<char> desc;  // staged descriptor bytes, uploaded to ws + desc_region.off
+  // host descriptor tables, uploaded to ws + desc_region.off
+  std::vector<char> desc;
   Region desc_region;
-  size_t leafdesc_off = 0, leafout_off = 0;
+  size_t leafdesc_off = 0, order_off = 0, gparams_off = 0, refs_off = 0;
+  int nrefs = 0;
+  int user_ref_first = 0;         // global ref index of block 0's result
+  // device-written tables
+  size_t leafout_off = 0, ranks_off = 0;
   // workspace regions
   Region status, queue, uar, var, cscr, rscr, gscr, tape_int, tape_dbl;
   Region full_u, full_s, full_v, half_u, half_s, half_v;
   Region qr, tau, core, ord;
   int64_t cscr_stride = 0, rscr_stride = 0, gscr_stride = 0;
   int max_clusters_scratch = 0;
-  // stores: [level] for full (0..L) and half (1..L)
-  std::vector<StoreLevel> full_lv, half_lv;
-  StoreLevel user_lv;
-  size_t user_ref_off = 0;
+  // global ref index of node (a, c) of block b: full store at level l, half store at level l
+  std::vector<std::vector<std::vector<int>>> full_idx, half_idx;  // [b][l][a * ncols + c]
   // stages
   std::vector<std::vector<SvdTask>> task_storage;
   std::vector<Stage> stages;
   size_t total = 0;
 };
 
-// Validate the arguments and lay out the workspace.  `sms` is the SM count of
-// the device (0 when only the size is wanted).  Returns false with a message.
-bool make_plan(const hbaca_gen& g, const hbaca_opts& o, int sms, Plan& p, std::string& err);
+// Validate the arguments and lay out the workspace for `nblocks` matrices
+// (one generator each, same kind and dtype).  `sms` is the device's SM count
+// (0 when unknown).  Returns false with a message.
+bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms, Plan& p, std::string& err);
 
-// Fill the descriptor tables that depend on the caller's result buffers.
-void bind_user_result(Plan& p, const hbaca_result& r);
+// Point block b's result entry at the caller's buffers.
+void bind_user_result(Plan& p, int b, const hbaca_result& r);
+
+// Levels of a block for opts.levels (>= 0: that L; < 0: leaves of at most
+// -levels rows and columns), or -1 when invalid.
+int block_levels(int64_t m, int64_t n, int levels);
 
 }  // namespace hbaca

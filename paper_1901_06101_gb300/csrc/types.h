@@ -5,8 +5,17 @@
 
 namespace hbaca {
 
+// Per-block parameters of a batched Gaussian compression.
+struct GaussBlockParams {
+  const double* x;
+  const double* y;
+  int dim;
+  int pad;
+  double c;  // -1 / (2 h^2)
+};
+
 struct LeafDesc {
-  int64_t row0, col0;     // global offsets of the leaf
+  int64_t row0, col0;     // offsets of the leaf in its block's matrix
   int32_t m, n;           // leaf size
   int32_t rcap;           // BACA rank capacity of this leaf
   int32_t tape_iters;     // iteration capacity of the tape
@@ -14,6 +23,8 @@ struct LeafDesc {
   int64_t u_off, v_off;   // element offsets of U (m x rcap, ld m) and V (rcap x n, ld n)
   int64_t tape_off;       // int offset into tape_int (records of 4 + 3d ints)
   int64_t taped_off;      // double offset into tape_dbl (records of 2 doubles)
+  int32_t block;          // block of a batched call (0 for a single matrix)
+  int32_t pad;
 };
 
 struct LeafOut {
@@ -34,11 +45,14 @@ enum TaskKind : int { TASK_LEAF = 0, TASK_HORIZ = 1, TASK_VERT = 2 };
 
 // A stored low-rank block U diag(S) V (U column-major ld m, V row-major ld n).
 struct BlockRef {
-  int64_t u_off, s_off, v_off;  // element offsets (U, V: scalars; S: doubles)
+  int64_t u_off, s_off, v_off;  // element offsets (U, V: scalars; S: doubles) in the store arenas
   int64_t ldu, ldv;             // U column-major (ld >= m), V row-major (ld >= n)
   int32_t m, n;
-  int32_t rank_slot;            // index into the rank array of its store
-  int32_t pad;
+  int32_t rank_slot;            // index into the rank array
+  int32_t cap;                  // rank capacity (columns of U, rows of V)
+  void* U;                      // caller buffers of a block's final factors: when set they
+  double* S;                    // replace the arena + offset addresses
+  void* V;
 };
 
 struct SvdTask {
