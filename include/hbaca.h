@@ -162,6 +162,24 @@ size_t hbaca_workspace_size_batched(int32_t nblocks, const hbaca_gen* gens, cons
 hbaca_status hbaca_compress_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
                                     hbaca_result* outs, void* workspace, void* stream);
 
+/* hbaca_compress with a workspace built into the library instead of one from
+   the caller; the paper has no counterpart (it is an interface convenience).
+   Meant for callers that cannot allocate device memory themselves: a C
+   program with no device allocator of its own, a caller whose device memory
+   all belongs to another runtime's pool, or a latency-bound caller that must
+   not allocate per call.  The area is HBACA_NOALLOC_WORKSPACE_BYTES per
+   device; a problem whose hbaca_workspace_size exceeds it is rejected with
+   HBACA_WORKSPACE before anything is enqueued.  The first call on a device
+   (with that device current) looks up the area's address; make that first
+   call before any stream capture.  No device memory is allocated or freed.
+   All calls on one device share the area, so calls that overlap in time
+   (other threads, or other streams with work still pending) race on it:
+   serialise them.  Results, ranks and status are as for hbaca_compress; the
+   leaf records in the area are overwritten by the next call. */
+#define HBACA_NOALLOC_WORKSPACE_BYTES (64u << 20)
+hbaca_status hbaca_compress_noalloc(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts,
+                                    hbaca_result* out, void* stream);
+
 /* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
    by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index
    a * 2^L + b.  Arrays I, J, jbar hold `max_iters * d` entries (row-major by

@@ -75,6 +75,8 @@ SIGNATURES = [
                                       ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_void_p]),
     ("hbaca_read_leaf_trace", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                              ctypes.c_int64, ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
+    ("hbaca_compress_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Opts),
+                                              ctypes.POINTER(Result), ctypes.c_void_p]),
     ("hbaca_workspace_size_batched", ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Gen), ctypes.POINTER(Opts)]),
     ("hbaca_compress_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Gen),
                                               ctypes.POINTER(Opts), ctypes.POINTER(Result), ctypes.c_void_p,
@@ -265,6 +267,28 @@ def compress(ctx, spec, opts, stream=None, ws=None, out=None):
     r = int(res.rank)
     c = Compressed(Ut[:r].T, S[:r], V[:r], r, ws, res)
     c.buffers = (Ut, S, V)
+    return c
+
+
+def compress_noalloc(ctx, spec, opts, stream=None, out=None):
+    """hbaca_compress_noalloc: the library's built-in workspace (the call
+    itself allocates no device memory; ``out`` buffers are the caller's)."""
+    import torch
+    m, n = spec.m, spec.n
+    cap = opts.rank_cap if opts.rank_cap else min(m, n, 1024)
+    dt = torch.complex128 if spec.complex else torch.float64
+    if out is None:
+        out = (torch.empty((cap, m), dtype=dt, device="cuda"), torch.empty(cap, dtype=torch.float64, device="cuda"),
+               torch.empty((cap, n), dtype=dt, device="cuda"))
+    Ut, S, V = out
+    res = Result(U=Ut.data_ptr(), ldu=m, S=S.data_ptr(), V=V.data_ptr(), ldv=n)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib().hbaca_compress_noalloc(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.byref(res),
+                                       ctypes.c_void_p(stream)))
+    r = int(res.rank)
+    c = Compressed(Ut[:r].T, S[:r], V[:r], r, None, res)
+    c.buffers = out
     return c
 
 

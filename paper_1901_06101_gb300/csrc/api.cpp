@@ -49,6 +49,10 @@ hbaca_status map_device_status(int ds) {
 
 }  // namespace
 
+namespace hbaca {
+hbaca_status record_error(hbaca_status s, const std::string& msg) { return fail(s, msg); }
+}  // namespace hbaca
+
 extern "C" {
 
 const char* hbaca_version(void) { return "hbaca-gb300 0.1 (sm_103a)"; }

@@ -18,4 +18,6 @@ struct RunCtx {
 };
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);
+// Set the calling thread's hbaca_last_error() message; returns s.
+hbaca_status record_error(hbaca_status s, const std::string& msg);
 }  // namespace hbaca
