@@ -100,6 +100,11 @@ typedef struct hbaca_gen {
 #define HBACA_FLAG_ASYNC 1u    /* do not synchronise; the rank goes to result.d_rank only */
 #define HBACA_FLAG_PROFILE 2u  /* record CUDA events around each phase on `stream`
                                   (read with hbaca_phase_times after the call) */
+#define HBACA_FLAG_TAPE 4u     /* keep, in the workspace, every intermediate block of the
+                                  merge tree with ALL singular triplets of its core (not
+                                  only the eps-rank kept ones), for hbaca_apply_backward.
+                                  The kept results are the same as without the flag; the
+                                  workspace is larger (no store is reused across levels) */
 
 /* Options of one compression (Alg. 3 inputs n_b, d, eps). */
 typedef struct hbaca_opts {
@@ -179,6 +184,42 @@ hbaca_status hbaca_compress_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca
 #define HBACA_NOALLOC_WORKSPACE_BYTES (64u << 20)
 hbaca_status hbaca_compress_noalloc(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts,
                                     hbaca_result* out, void* stream);
+
+/* ---- Apply and reverse pass (real F64; the reverse pass: GAUSSIAN generator) ----
+
+   y = U diag(S) V X for a compressed result (A ~ U diag(S) V, the output of
+   Alg. 3).  X: n x nrhs, column-major (ldx >= n); Y: m x nrhs, column-major
+   (ldy >= m), overwritten.  `workspace` (device, 256-byte aligned) holds
+   hbaca_apply_workspace_size(rank, nrhs) bytes.  Synchronises `stream`. */
+size_t hbaca_apply_workspace_size(int64_t rank, int64_t nrhs);
+hbaca_status hbaca_apply(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_result* res, const void* X, int64_t nrhs,
+                         int64_t ldx, void* Y, int64_t ldy, void* workspace, void* stream);
+
+/* Reverse pass of Y = (U diag(S) V) X with every discrete choice of the
+   forward frozen: the BACA pivots and LRID ranks of each leaf (Alg. 2), and
+   the truncation rank of the leaf re-compression and of every merge
+   (Sec. 3.2; Alg. 3).  Given dY = dL/dY it returns
+     d_x = dL/dx (m x dim, row-major like x), d_y = dL/dy (n x dim),
+     d_h = dL/dh (one double), dX = dL/dX = (U diag(S) V)^T dY (n x nrhs,
+     column-major, ldx >= n; NULL to skip),
+   for the GAUSSIAN generator A(i, j) = exp(-||x_i - y_j||^2 / (2 h^2)),
+   real F64.  Each truncated SVD is differentiated with the singular-value-gap
+   coefficients 1 / (sigma_i^2 - sigma_j^2) (i kept, j discarded), which is
+   why the forward must run with HBACA_FLAG_TAPE (every merge node keeps all
+   its singular triplets); the BACA residual rows are regenerated from the
+   factors, not stored.  gen, opts and workspace are those of the forward
+   call, res its result; all output arrays are device memory and are
+   overwritten (any of d_h, d_x, d_y may be NULL).  `bwd_workspace` (device,
+   256-byte aligned) holds hbaca_backward_workspace_size(...) bytes, a size
+   that depends on the ranks of the forward: the size query reads them from
+   `workspace` (and synchronises `stream`).  No counterpart in the paper,
+   which has no reverse pass; the adjoint is of the map the paper defines. */
+size_t hbaca_backward_workspace_size(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
+                                     void* stream);
+hbaca_status hbaca_apply_backward(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts, const hbaca_result* res,
+                                  const void* workspace, const void* X, int64_t nrhs, int64_t ldx, const void* dY,
+                                  int64_t lddy, double* d_h, double* d_x, double* d_y, void* dX, int64_t lddx,
+                                  void* bwd_workspace, size_t bwd_bytes, void* stream);
 
 /* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
    by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index

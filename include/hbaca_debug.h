@@ -36,6 +36,16 @@ size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char*
    benchmark to report the unit rates beside the derived FP64 peak. */
 hbaca_status hbaca_debug_fp64_probe(double* dfma_tflops, double* dmma_tflops);
 
+/* Layout of the reverse pass for a taped forward (gen, opts, workspace) with
+   nrhs right-hand sides, as JSON in buf (NUL-terminated, truncated to len):
+   per leaf the byte offsets, in the backward workspace, of the BACA factor
+   adjoints, the column and row adjoint arrays and their index maps; per merge
+   node its kept and stored triplet counts and buffer offsets.  Reads the
+   sizes from `workspace` (synchronises `stream`).  Returns the length the
+   full text needs, or -1. */
+int64_t hbaca_debug_backward_json(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
+                                  char* buf, int64_t len, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -187,17 +187,17 @@ def aca(gen, eps, seed=0, bid=0):
     return dict(U=U, V=V, r=U.shape[1], piv=piv, mu=mu)
 
 
-def recompress(U, V, eps):
+def recompress(U, V, eps, rank=None):
     """SVD re-compression of U V (Sec. 3.2, last paragraph):
     [Q_U, T_U] = QR(U), [Q_V, T_V] = QR(V^H), SVD(T_U T_V^H, eps) = X S Y^H;
-    returns (Q_U X, s, Y^H Q_V^H)."""
+    returns (Q_U X, s, Y^H Q_V^H).  ``rank`` freezes the truncation rank."""
     m, r = U.shape
     n = V.shape[1]
     if r == 0:
         return U[:, :0], np.zeros(0), V[:0, :]
     Qu, Tu = np.linalg.qr(U)
     Qv, Tv = np.linalg.qr(V.conj().T)
-    X, s, Yh = truncated_svd(Tu @ Tv.conj().T, eps)
+    X, s, Yh = truncated_svd(Tu @ Tv.conj().T, eps, rank)
     return Qu @ X, s, Yh @ Qv.conj().T
 
 

@@ -31,7 +31,7 @@ def tree_levels(n, L):
     return levels
 
 
-def horizontal_merge(U1, s1, V1, U2, s2, V2, eps):
+def horizontal_merge(U1, s1, V1, U2, s2, V2, eps, rank=None):
     """Eqs. columncomb, columnsvdmerge: U_bar = [U1 S1, U2 S2],
     V_bar = diag(V1, V2); [U, S, V'] = SVD(U_bar, eps); V = V' V_bar."""
     Ub = np.concatenate([U1 * s1[None, :], U2 * s2[None, :]], axis=1)
@@ -39,11 +39,11 @@ def horizontal_merge(U1, s1, V1, U2, s2, V2, eps):
     Vb = np.zeros((r1 + r2, V1.shape[1] + V2.shape[1]), np.result_type(V1, V2))
     Vb[:r1, :V1.shape[1]] = V1
     Vb[r1:, V1.shape[1]:] = V2
-    U, s, Vp = truncated_svd(Ub, eps)
+    U, s, Vp = truncated_svd(Ub, eps, rank)
     return U, s, Vp @ Vb
 
 
-def vertical_merge(U1, s1, V1, U2, s2, V2, eps):
+def vertical_merge(U1, s1, V1, U2, s2, V2, eps, rank=None):
     """Alg. 3 lines 17-20: U_bar = diag(U1, U2), V_bar = [S1 V1; S2 V2];
     [U', S, V] = SVD(V_bar, eps); U = U_bar U'."""
     r1, r2 = U1.shape[1], U2.shape[1]
@@ -51,17 +51,25 @@ def vertical_merge(U1, s1, V1, U2, s2, V2, eps):
     Ub[:U1.shape[0], :r1] = U1
     Ub[U1.shape[0]:, r1:] = U2
     Vb = np.concatenate([s1[:, None] * V1, s2[:, None] * V2], axis=0)
-    Up, s, V = truncated_svd(Vb, eps)
+    Up, s, V = truncated_svd(Vb, eps, rank)
     return Ub @ Up, s, V
 
 
-def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None):
+def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None, ranks=None):
     """H-BACA(A, n_b = 4^L, d, eps) of Alg. 3.  Returns a dict with U, s, V,
     rank r, the leaf BACA results (if ``keep_leaves``), the leaf ranks before
     and after re-compression, and the merge ranks per level.  ``forced``
     maps a leaf index a * 2^L + b to a pivot record {"trace": [...], "stop":
     reason}; those leaves are run by
-    the frozen-pivot replay (baca_replay) instead of the greedy choices."""
+    the frozen-pivot replay (baca_replay) instead of the greedy choices.
+    ``ranks`` freezes truncation ranks: it maps ("full", 0, a, b) (leaf
+    re-compression), ("half", l, a, b) and ("full", l, a, b) (merges) to a
+    rank; the result's "ranks" entry lists every truncation rank taken, in the
+    same keys, so that one run's choices can be frozen in another."""
+    taken = {}
+
+    def rk(key):
+        return None if ranks is None else ranks.get(key)
     rows = tree_levels(gen.m, L)
     cols = tree_levels(gen.n, L)
     blocks = {}
@@ -78,7 +86,8 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None)
                 res["stop"] = "replayed"
             else:
                 res = baca(w, d, eps, seed=seed, bid=block_id(batch_index, a, b))
-            U, s, V = recompress(res["U"], res["V"], eps)
+            U, s, V = recompress(res["U"], res["V"], eps, rk(("full", 0, a, b)))
+            taken[("full", 0, a, b)] = len(s)
             blocks[(a, b)] = (U, s, V)
             info = dict(r_baca=res["r"], r=len(s), iters=len(res["trace"]), stop=res["stop"])
             if keep_leaves:
@@ -92,13 +101,15 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None)
             for b in range(len(cols[l])):
                 U1, s1, V1 = blocks[(a, 2 * b)]
                 U2, s2, V2 = blocks[(a, 2 * b + 1)]
-                half[(a, b)] = horizontal_merge(U1, s1, V1, U2, s2, V2, eps)
+                half[(a, b)] = horizontal_merge(U1, s1, V1, U2, s2, V2, eps, rk(("half", l, a, b)))
+                taken[("half", l, a, b)] = len(half[(a, b)][1])
         full = {}
         for a in range(len(rows[l])):
             for b in range(len(cols[l])):
                 U1, s1, V1 = half[(2 * a, b)]
                 U2, s2, V2 = half[(2 * a + 1, b)]
-                full[(a, b)] = vertical_merge(U1, s1, V1, U2, s2, V2, eps)
+                full[(a, b)] = vertical_merge(U1, s1, V1, U2, s2, V2, eps, rk(("full", l, a, b)))
+                taken[("full", l, a, b)] = len(full[(a, b)][1])
         merge_ranks.append(dict(half={k: len(v[1]) for k, v in half.items()},
                                 full={k: len(v[1]) for k, v in full.items()}))
         if keep_leaves:
@@ -106,4 +117,4 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None)
             stages.append(("full", l, full))
         blocks = full
     U, s, V = blocks[(0, 0)]
-    return dict(U=U, s=s, V=V, r=len(s), leaves=leaf_info, merges=merge_ranks, stages=stages)
+    return dict(U=U, s=s, V=V, r=len(s), leaves=leaf_info, merges=merge_ranks, stages=stages, ranks=taken)

@@ -120,9 +120,11 @@ def eps_rank(s, eps):
     return int(np.count_nonzero(s >= eps * s[0]))
 
 
-def truncated_svd(A, eps):
+def truncated_svd(A, eps, rank=None):
     """[U, Sigma, V, r] = SVD(A, eps) (Sec. 2): LAPACK gesdd with a gesvd
-    fallback, truncated at the eps-rank.  Returns U (m x r), s (r), Vh (r x n)."""
+    fallback, truncated at the eps-rank, or at ``rank`` when given (a frozen
+    truncation rank, used to differentiate the map with its discrete choices
+    held fixed).  Returns U (m x r), s (r), Vh (r x n)."""
     A = np.asarray(A)
     m, n = A.shape
     if m == 0 or n == 0:
@@ -132,5 +134,5 @@ def truncated_svd(A, eps):
     except np.linalg.LinAlgError:
         import scipy.linalg
         U, s, Vh = scipy.linalg.svd(A, full_matrices=False, lapack_driver="gesvd")
-    r = eps_rank(s, eps)
+    r = eps_rank(s, eps) if rank is None else min(int(rank), s.size)
     return U[:, :r], s[:r], Vh[:r]

@@ -16,6 +16,7 @@ GEN_DENSE, GEN_GAUSSIAN, GEN_HELMHOLTZ, GEN_SPARSE_PRODUCT, GEN_LOWRANK = 0, 1, 
 F64, C128 = 0, 1
 FLAG_ASYNC = 1
 FLAG_PROFILE = 2
+FLAG_TAPE = 4
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
           5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE"}
 STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}
@@ -75,6 +76,19 @@ SIGNATURES = [
                                       ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_void_p]),
     ("hbaca_read_leaf_trace", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                              ctypes.c_int64, ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
+    ("hbaca_debug_backward_json", ctypes.c_int64, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
+                                                   ctypes.c_int64, ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("hbaca_apply_workspace_size", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
+    ("hbaca_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Result), ctypes.c_void_p,
+                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    ("hbaca_backward_workspace_size", ctypes.c_size_t, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
+                                                        ctypes.c_int64, ctypes.c_void_p]),
+    ("hbaca_apply_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Opts),
+                                            ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("hbaca_compress_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Opts),
                                               ctypes.POINTER(Result), ctypes.c_void_p]),
     ("hbaca_workspace_size_batched", ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Gen), ctypes.POINTER(Opts)]),
@@ -292,6 +306,104 @@ def compress_noalloc(ctx, spec, opts, stream=None, out=None):
     return c
 
 
+def _colmajor(X, rows):
+    """A (rows, nrhs) torch float64 CUDA tensor as a column-major buffer:
+    returns (buffer tensor of shape (nrhs, rows), ld)."""
+    import torch
+    Xt = X.detach().to(device="cuda", dtype=torch.float64)
+    if Xt.dim() == 1:
+        Xt = Xt[:, None]
+    assert Xt.shape[0] == rows
+    return Xt.t().contiguous(), rows
+
+
+def apply(ctx, spec, comp, X, stream=None):
+    """Y = U diag(S) V X (hbaca_apply); X (n, nrhs) -> Y (m, nrhs), float64."""
+    import torch
+    Xc, ldx = _colmajor(X, spec.n)
+    nrhs = Xc.shape[0]
+    Yc = torch.empty((nrhs, spec.m), dtype=torch.float64, device="cuda")
+    ws = torch.empty(lib().hbaca_apply_workspace_size(max(comp.rank, 1), nrhs), dtype=torch.uint8, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib().hbaca_apply(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(comp.res), ctypes.c_void_p(Xc.data_ptr()),
+                            nrhs, ldx, ctypes.c_void_p(Yc.data_ptr()), spec.m, ctypes.c_void_p(ws.data_ptr()),
+                            ctypes.c_void_p(stream)))
+    return Yc.t()
+
+
+def apply_backward(ctx, spec, opts, comp, X, dY, stream=None, want_dX=True, keep_workspace=False):
+    """hbaca_apply_backward: (d_h, d_x, d_y, dX) for Y = (U diag(S) V) X with
+    the forward's pivots and ranks frozen (the forward must have run with
+    FLAG_TAPE; ``comp`` is its result)."""
+    import torch
+    Xc, ldx = _colmajor(X, spec.n)
+    dYc, lddy = _colmajor(dY, spec.m)
+    nrhs = Xc.shape[0]
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = ctypes.c_void_p(stream)
+    nb = lib().hbaca_backward_workspace_size(ctypes.byref(spec.gen), ctypes.byref(opts),
+                                             ctypes.c_void_p(comp.ws.data_ptr()), nrhs, st)
+    if nb == 0:
+        raise HbacaError(1, lib().hbaca_last_error().decode())
+    bws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    dh = torch.empty(1, dtype=torch.float64, device="cuda")
+    dx = torch.empty((spec.m, spec.gen.dim), dtype=torch.float64, device="cuda")
+    dy = torch.empty((spec.n, spec.gen.dim), dtype=torch.float64, device="cuda")
+    dXc = torch.empty((nrhs, spec.n), dtype=torch.float64, device="cuda") if want_dX else None
+    check(lib().hbaca_apply_backward(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.byref(comp.res),
+                                     ctypes.c_void_p(comp.ws.data_ptr()), ctypes.c_void_p(Xc.data_ptr()), nrhs, ldx,
+                                     ctypes.c_void_p(dYc.data_ptr()), lddy, ctypes.c_void_p(dh.data_ptr()),
+                                     ctypes.c_void_p(dx.data_ptr()), ctypes.c_void_p(dy.data_ptr()),
+                                     ctypes.c_void_p(dXc.data_ptr() if want_dX else None), spec.n,
+                                     ctypes.c_void_p(bws.data_ptr()), nb, st))
+    if keep_workspace:
+        return dh[0], dx, dy, (dXc.t() if want_dX else None), bws
+    return dh[0], dx, dy, (dXc.t() if want_dX else None)
+
+
+def _autograd_function():
+    import torch
+
+    class GaussianHBACAApply(torch.autograd.Function):
+        """Y = A_hat(h, x, y) X where A_hat = U diag(S) V is the H-BACA
+        compression (Alg. 3) of the Gaussian kernel matrix
+        exp(-||x_i - y_j||^2 / (2 h^2)); the backward differentiates A_hat with
+        the forward's pivots and truncation ranks frozen."""
+
+        @staticmethod
+        def forward(fctx, h, x, y, X, hctx, eps, d, levels, seed, rank_cap, leaf_rank_cap):
+            spec = gaussian(x, y, float(h))
+            opts = make_opts(eps, d, levels, seed=seed, rank_cap=rank_cap, leaf_rank_cap=leaf_rank_cap,
+                             flags=FLAG_TAPE)
+            comp = compress(hctx, spec, opts)
+            Y = apply(hctx, spec, comp, X)
+            fctx.state = (hctx, spec, opts, comp)
+            fctx.save_for_backward(X)
+            return Y
+
+        @staticmethod
+        def backward(fctx, dY):
+            hctx, spec, opts, comp = fctx.state
+            (X,) = fctx.saved_tensors
+            dh, dx, dy, dX = apply_backward(hctx, spec, opts, comp, X, dY.contiguous())
+            return dh.reshape(()), dx, dy, dX, None, None, None, None, None, None, None
+
+    return GaussianHBACAApply
+
+
+_AUTOGRAD = None
+
+
+def gaussian_hbaca_apply(h, x, y, X, ctx, eps, d, levels, seed=0, rank_cap=0, leaf_rank_cap=0):
+    """Differentiable Y = A_hat(h, x, y) X (torch.autograd), see GaussianHBACAApply."""
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _autograd_function()
+    return _AUTOGRAD.apply(h, x, y, X, ctx, eps, d, levels, seed, rank_cap, leaf_rank_cap)
+
+
 def _trace_call(call, d, max_iters):
     """Run a trace-reading call with fresh host arrays; returns the record dict."""
     import numpy as np
@@ -321,39 +433,60 @@ def _gen_array(specs):
     return arr
 
 
+class Batch:
+    """A batched call set up once: the host arrays of generators and results,
+    the workspace and the per-block output buffers, so that repeated calls
+    (timing, training loops) do no Python-side work but the ABI call."""
+
+    def __init__(self, ctx, specs, opts, ws=None):
+        import torch
+        self.ctx, self.specs, self.opts = ctx, list(specs), opts
+        n = len(self.specs)
+        self.gens = _gen_array(self.specs)
+        if ws is None:
+            nbytes = lib().hbaca_workspace_size_batched(n, self.gens, ctypes.byref(opts))
+            if nbytes == 0:
+                raise HbacaError(1, lib().hbaca_last_error().decode())
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.ws = ws
+        self.res = (Result * n)()
+        self.bufs = []
+        for i, s in enumerate(self.specs):
+            cap = min(opts.rank_cap, s.m, s.n) if opts.rank_cap else min(s.m, s.n, 1024)
+            dt = torch.complex128 if s.complex else torch.float64
+            Ut = torch.empty((cap, s.m), dtype=dt, device="cuda")
+            S = torch.empty(cap, dtype=torch.float64, device="cuda")
+            V = torch.empty((cap, s.n), dtype=dt, device="cuda")
+            self.res[i] = Result(U=Ut.data_ptr(), ldu=s.m, S=S.data_ptr(), V=V.data_ptr(), ldv=s.n)
+            self.bufs.append((Ut, S, V))
+
+    def run(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        check(lib().hbaca_compress_batched(self.ctx.ptr, len(self.specs), self.gens, ctypes.byref(self.opts),
+                                           self.res, ctypes.c_void_p(self.ws.data_ptr()),
+                                           ctypes.c_void_p(stream)))
+        return self
+
+    def ranks(self):
+        return [int(self.res[i].rank) for i in range(len(self.specs))]
+
+    def results(self):
+        out = []
+        for i in range(len(self.specs)):
+            r = int(self.res[i].rank)
+            Ut, S, V = self.bufs[i]
+            c = Compressed(Ut[:r].T, S[:r], V[:r], r, self.ws, self.res[i])
+            c.buffers = self.bufs[i]
+            out.append(c)
+        return out
+
+
 def compress_batched(ctx, specs, opts, ws=None, stream=None):
     """hbaca_compress_batched over a list of GenSpec (one per block); returns a
     list of Compressed (one per block) sharing the workspace."""
-    import torch
-    n = len(specs)
-    gens = _gen_array(specs)
-    if ws is None:
-        nbytes = lib().hbaca_workspace_size_batched(n, gens, ctypes.byref(opts))
-        if nbytes == 0:
-            raise HbacaError(1, lib().hbaca_last_error().decode())
-        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    res = (Result * n)()
-    bufs = []
-    for i, s in enumerate(specs):
-        cap = min(opts.rank_cap, s.m, s.n) if opts.rank_cap else min(s.m, s.n, 1024)
-        dt = torch.complex128 if s.complex else torch.float64
-        Ut = torch.empty((cap, s.m), dtype=dt, device="cuda")
-        S = torch.empty(cap, dtype=torch.float64, device="cuda")
-        V = torch.empty((cap, s.n), dtype=dt, device="cuda")
-        res[i] = Result(U=Ut.data_ptr(), ldu=s.m, S=S.data_ptr(), V=V.data_ptr(), ldv=s.n)
-        bufs.append((Ut, S, V))
-    if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
-    check(lib().hbaca_compress_batched(ctx.ptr, n, gens, ctypes.byref(opts), res, ctypes.c_void_p(ws.data_ptr()),
-                                       ctypes.c_void_p(stream)))
-    out = []
-    for i in range(n):
-        r = int(res[i].rank)
-        Ut, S, V = bufs[i]
-        c = Compressed(Ut[:r].T, S[:r], V[:r], r, ws, res[i])
-        c.buffers = bufs[i]
-        out.append(c)
-    return out
+    return Batch(ctx, specs, opts, ws).run(stream).results()
 
 
 def read_leaf_trace_batched(specs, opts, ws, block, leaf, max_iters=4096):
@@ -405,6 +538,21 @@ def plan_json(spec, opts):
     n = lib().hbaca_debug_plan_json(ctypes.byref(spec.gen), ctypes.byref(opts), None, 0)
     buf = ctypes.create_string_buffer(n)
     lib().hbaca_debug_plan_json(ctypes.byref(spec.gen), ctypes.byref(opts), buf, n)
+    return json.loads(buf.value.decode())
+
+
+def backward_json(spec, opts, ws, nrhs):
+    """Layout of the reverse pass (debugging aid), as a dict."""
+    import json
+    import torch
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n = lib().hbaca_debug_backward_json(ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()),
+                                        nrhs, None, 0, st)
+    if n < 0:
+        raise HbacaError(1, lib().hbaca_last_error().decode())
+    buf = ctypes.create_string_buffer(int(n))
+    lib().hbaca_debug_backward_json(ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()), nrhs,
+                                    buf, n, st)
     return json.loads(buf.value.decode())
 
 

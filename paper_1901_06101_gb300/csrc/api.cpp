@@ -25,6 +25,11 @@ namespace {
 
 thread_local std::string tls_err;
 
+// A taped call leaves this byte pattern in the status region (after the
+// status word); hbaca_apply_backward refuses a workspace without it.
+constexpr size_t kTapeMarkOffset = 16;
+constexpr int kTapeMarkByte = 0x5A;
+
 hbaca_status fail(hbaca_status s, const std::string& m) {
   tls_err = m;
   return s;
@@ -128,11 +133,15 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
   cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.desc_region.off, p.desc.data(), p.desc.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.ranks_off, 0, (size_t)p.nrefs * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.ranks_off, 0, (size_t)p.nslots * 4, st);
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("workspace set-up: ") + cudaGetErrorString(e));
   e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
   if (e != cudaSuccess) return fail(HBACA_CUDA, err.empty() ? cudaGetErrorString(e) : err);
   ctx->launches = rc.launches;
+  if (p.tape) {  // mark the workspace as holding a complete tape of this call
+    e = cudaMemsetAsync(ws + p.status.off + kTapeMarkOffset, kTapeMarkByte, 4, st);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("tape mark: ") + cudaGetErrorString(e));
+  }
   if (prof) {
     e = cudaEventRecord(ctx->ev[3], st);
     if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));

@@ -108,6 +108,13 @@ __global__ void pack_kernel(const DenseParams<T> P) {
       const int64_t j = e % t.rows_b, p = e / t.rows_b;
       B[p * t.rows_b + j] = conj_(V[p * t.rows_b + j]);
     }
+    if (!t.a_in_baca) {  // QR operand A = a copy of the leaf's U (m x k, ld m)
+      const T* U = P.Uar + t.src_u_off;
+      T* A = P.qr + t.a_off;
+      const int64_t tu = (int64_t)t.rows_a * k;
+      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tu; e += (int64_t)gridDim.x * blockDim.x)
+        A[e] = U[e];
+    }
   } else {
     const BlockRef b1 = P.in_blocks[t.in1], b2 = P.in_blocks[t.in2];
     const int r1 = P.in_rank[b1.rank_slot], r2 = P.in_rank[b2.rank_slot];
@@ -137,6 +144,8 @@ __global__ void pack_kernel(const DenseParams<T> P) {
     dm.krb = t.kind == TASK_LEAF ? min(t.rows_b, k) : 0;
     dm.s = 0;
     dm.sweeps = 0;
+    dm.nout = 0;
+    dm.pad[0] = dm.pad[1] = 0;
     P.dims[ti] = dm;
   }
 }
@@ -451,7 +460,9 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
   if (mr <= 0 || nc <= 0) {
     if (q == 0 && tid == 0) {
       P.dims[ti].s = 0;
+      P.dims[ti].nout = 0;
       P.out_rank[P.out_blocks[t.out].rank_slot] = 0;
+      if (P.out_blocks[t.out].full_slot >= 0) P.out_rank[P.out_blocks[t.out].full_slot] = 0;
     }
     return;
   }
@@ -620,10 +631,14 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
       if (!isfinite(s1)) set_status(P.status, DS_NUMERICAL);
       const BlockRef ob = P.out_blocks[t.out];
       if (s > ob.cap) { set_status(P.status, DS_RANK_CAPACITY); s = ob.cap; }
-      sshare[0] = s;
+      // a taped output keeps every triplet of the core (the kept ones first)
+      const int nout = ob.full_slot >= 0 ? min(min(nc, mr), ob.store_cap) : s;
+      sshare[0] = nout;
       P.dims[ti].s = s;
+      P.dims[ti].nout = nout;
       P.dims[ti].sweeps = sweep;
       P.out_rank[ob.rank_slot] = s;
+      if (ob.full_slot >= 0) P.out_rank[ob.full_slot] = nout;
     }
   }
   cl.sync();
@@ -635,7 +650,7 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
     for (int tc = q * nw + warp; tc < s; tc += c * nw) {
       const int j = ord0[tc];
       const double sg = sv0[j];
-      const double inv = 1.0 / sg;
+      const double inv = sg > 0.0 ? 1.0 / sg : 0.0;  // a zero singular value (taped outputs only)
       for (int i = lane; i < mr; i += 32) M[(int64_t)j * ld + i] = scale(ldcg(M + (int64_t)j * ld + i), inv);
       if (lane == 0) out_s(P, ob)[tc] = sg;
     }
@@ -653,7 +668,7 @@ __global__ void finish_kernel(const DenseParams<T> P) {
   const int ti = blockIdx.y;
   const SvdTask t = P.tasks[ti];
   const TaskDims dm = P.dims[ti];
-  const int s = dm.s;
+  const int s = dm.nout;  // columns written (the kept s, or all when taped)
   const int mr = dm.kra;
   const int nc = t.kind == TASK_LEAF ? dm.krb : dm.k;
   const int p = min(mr, nc);
@@ -704,7 +719,7 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   const QJob jb = jobs[blockIdx.x / c];
   const SvdTask t = P.tasks[jb.task];
   const TaskDims dm = P.dims[jb.task];
-  const int s = dm.s;
+  const int s = dm.nout;  // columns written (the kept s, or all when taped)
   const int rows = jb.which ? t.rows_b : t.rows_a;
   const int kk = jb.which ? dm.krb : dm.kra;
   const T* A = jb.which ? P.qr + t.b_off : qr_a_ptr(P, t);
@@ -768,7 +783,7 @@ __global__ void blockprod_kernel(const DenseParams<T> P) {
   const SvdTask t = P.tasks[ti];
   if (t.kind == TASK_LEAF) return;
   const TaskDims dm = P.dims[ti];
-  const int s = dm.s;
+  const int s = dm.nout;  // columns written (the kept s, or all when taped)
   const BlockRef b1 = P.in_blocks[t.in1], b2 = P.in_blocks[t.in2];
   const int r1 = P.in_rank[b1.rank_slot], r2 = P.in_rank[b2.rank_slot];
   const BlockRef ob = P.out_blocks[t.out];
@@ -802,6 +817,31 @@ __global__ void blockprod_kernel(const DenseParams<T> P) {
       out_u(P, ob)[(int64_t)tc * ob.ldu + i] = acc;
     }
   }
+}
+
+// ------------------------------------------------------------------ taped root
+// With a tape the root node of block b is kept (all triplets) in the store;
+// its first s triplets (s = its eps-rank) go to the caller's result.
+template <typename T>
+__global__ void copyroot_kernel(const BlockRef* refs, int32_t* ranks, const T* fullU, const double* fullS,
+                                const T* fullV, int root_first, int user_first) {
+  const int b = blockIdx.y;
+  const BlockRef src = refs[root_first + b], dst = refs[user_first + b];
+  const int s = ranks[src.rank_slot];
+  T* U = reinterpret_cast<T*>(dst.U);
+  T* V = reinterpret_cast<T*>(dst.V);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t e = t0; e < (int64_t)src.m * s; e += stride) {
+    const int64_t i = e % src.m, p = e / src.m;
+    U[p * dst.ldu + i] = fullU[src.u_off + p * src.ldu + i];
+  }
+  for (int64_t e = t0; e < (int64_t)src.n * s; e += stride) {
+    const int64_t j = e % src.n, p = e / src.n;
+    V[p * dst.ldv + j] = fullV[src.v_off + p * src.ldv + j];
+  }
+  for (int64_t e = t0; e < s; e += stride) dst.S[e] = fullS[src.s_off + e];
+  if (t0 == 0) ranks[dst.rank_slot] = s;
 }
 
 }  // namespace hbaca

@@ -178,7 +178,8 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
   finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D);
   HB_TRY(cudaGetLastError());
   rc.launches += 2;
-  const size_t qa_smem = (size_t)3 * p.rank_cap_max * sizeof(T) + 64;
+  const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
+  const size_t qa_smem = 3 * qa_cols * sizeof(T) + 64;
   HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj));
   rc.launches += 5;
   if (sg.kind != TASK_LEAF) {
@@ -200,6 +201,16 @@ cudaError_t run_stages(Plan& p, RunCtx& rc, std::string& err) {
     if (e != cudaSuccess) return e;
   }
   if (rc.ev[2] && (p.stages.empty() || p.stages.back().kind == TASK_LEAF)) HB_TRY(cudaEventRecord(rc.ev[2], rc.st));
+  if (p.tape) {
+    char* ws = rc.ws;
+    copyroot_kernel<T><<<dim3(64, p.nblocks), 256, 0, rc.st>>>(
+        reinterpret_cast<const BlockRef*>(ws + p.desc_region.off + p.refs_off),
+        reinterpret_cast<int32_t*>(ws + p.ranks_off), reinterpret_cast<const T*>(ws + p.full_u.off),
+        reinterpret_cast<const double*>(ws + p.full_s.off), reinterpret_cast<const T*>(ws + p.full_v.off),
+        p.root_tape_first, p.user_ref_first);
+    HB_TRY(cudaGetLastError());
+    ++rc.launches;
+  }
   return cudaSuccess;
 }
 

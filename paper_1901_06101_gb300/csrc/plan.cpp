@@ -212,11 +212,18 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
   // ---- block references: full store (after the vertical merge of level l),
   // half store (after the horizontal merge of level l), one result per block;
   // every reference's rank lives at its own index of one rank array
+  // (with HBACA_FLAG_TAPE no store is reused across levels, and every node
+  // keeps all singular triplets of its core: storage capacity = the producing
+  // task's k capacity, the number stored goes to a second rank-array slot)
+  p.tape = (o.flags & HBACA_FLAG_TAPE) != 0;
+  std::vector<int64_t> kc_b(nblocks);
+  for (int b = 0; b < nblocks; ++b) kc_b[b] = std::min<int64_t>(2 * p.cap_b[b], 2 * std::min(gens[b].m, gens[b].n));
   std::vector<BlockRef> refs;
+  int ntaped = 0;
   p.full_idx.assign(nblocks, std::vector<std::vector<int>>(p.Lmax + 1));
   p.half_idx.assign(nblocks, std::vector<std::vector<int>>(p.Lmax + 1));
   size_t full_u = 0, full_s = 0, full_v = 0, half_u = 0, half_s = 0, half_v = 0;
-  auto add_ref = [&](int64_t m, int64_t n, int64_t cap, int64_t& u, int64_t& s, int64_t& v) {
+  auto add_ref = [&](int64_t m, int64_t n, int64_t cap, int64_t store_cap, int64_t& u, int64_t& s, int64_t& v) {
     BlockRef r;
     std::memset(&r, 0, sizeof(r));
     r.m = (int32_t)m;
@@ -225,40 +232,65 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
     r.ldu = m; r.ldv = n;
     r.rank_slot = (int32_t)refs.size();
     r.cap = (int32_t)cap;
-    u += m * cap; s += cap; v += cap * n;
+    r.store_cap = (int32_t)(p.tape ? std::max(store_cap, cap) : cap);
+    r.full_slot = p.tape ? -2 - ntaped++ : -1;  // resolved once the number of refs is known
+    u += m * r.store_cap; s += r.store_cap; v += r.store_cap * n;
     refs.push_back(r);
     return (int)refs.size() - 1;
   };
+  int64_t fu = 0, fs = 0, fv = 0, hu = 0, hs = 0, hv = 0;  // running offsets (tape)
   for (int l = 0; l < p.Lmax; ++l) {  // full store level l: blocks with L_b > l
-    int64_t u = 0, s = 0, v = 0;
+    int64_t u = p.tape ? fu : 0, s = p.tape ? fs : 0, v = p.tape ? fv : 0;
     for (int b = 0; b < nblocks; ++b) {
       if (p.Lb[b] <= l) continue;
       const int nr = (int)rows[b][l].size(), ncn = (int)cols[b][l].size();
       p.full_idx[b][l].assign(nr * ncn, -1);
       for (int a = 0; a < nr; ++a)
-        for (int cc = 0; cc < ncn; ++cc)
-          p.full_idx[b][l][a * ncn + cc] = add_ref(rows[b][l][a].second, cols[b][l][cc].second, p.cap_b[b], u, s, v);
+        for (int cc = 0; cc < ncn; ++cc) {
+          const int64_t sc = l == 0 ? leaves[p.leaf_first[b] + a * ncn + cc].rcap : kc_b[b];
+          p.full_idx[b][l][a * ncn + cc] =
+              add_ref(rows[b][l][a].second, cols[b][l][cc].second, p.cap_b[b], sc, u, s, v);
+        }
     }
+    fu = u; fs = s; fv = v;
     full_u = std::max<size_t>(full_u, u); full_s = std::max<size_t>(full_s, s); full_v = std::max<size_t>(full_v, v);
   }
   for (int l = 1; l <= p.Lmax; ++l) {  // half store level l: blocks with L_b >= l
-    int64_t u = 0, s = 0, v = 0;
+    int64_t u = p.tape ? hu : 0, s = p.tape ? hs : 0, v = p.tape ? hv : 0;
     for (int b = 0; b < nblocks; ++b) {
       if (p.Lb[b] < l) continue;
       const int nr = (int)rows[b][l - 1].size(), ncn = (int)cols[b][l].size();
       p.half_idx[b][l].assign(nr * ncn, -1);
       for (int a = 0; a < nr; ++a)
         for (int cc = 0; cc < ncn; ++cc)
-          p.half_idx[b][l][a * ncn + cc] = add_ref(rows[b][l - 1][a].second, cols[b][l][cc].second, p.cap_b[b], u, s, v);
+          p.half_idx[b][l][a * ncn + cc] =
+              add_ref(rows[b][l - 1][a].second, cols[b][l][cc].second, p.cap_b[b], kc_b[b], u, s, v);
     }
+    hu = u; hs = s; hv = v;
     half_u = std::max<size_t>(half_u, u); half_s = std::max<size_t>(half_s, s); half_v = std::max<size_t>(half_v, v);
   }
   p.user_ref_first = (int)refs.size();
   for (int b = 0; b < nblocks; ++b) {
     int64_t z = 0, z2 = 0, z3 = 0;
-    add_ref(gens[b].m, gens[b].n, p.cap_b[b], z, z2, z3);
+    const int keep = ntaped;
+    add_ref(gens[b].m, gens[b].n, p.cap_b[b], p.cap_b[b], z, z2, z3);
+    refs.back().store_cap = (int32_t)p.cap_b[b];
+    refs.back().full_slot = -1;  // the caller's buffers hold the kept triplets only
+    ntaped = keep;
+  }
+  if (p.tape) {  // root node of every block, in the full store after all levels
+    p.root_tape_first = (int)refs.size();
+    int64_t u = fu, s = fs, v = fv;
+    for (int b = 0; b < nblocks; ++b) {
+      const int64_t sc = p.Lb[b] == 0 ? leaves[p.leaf_first[b]].rcap : kc_b[b];
+      add_ref(gens[b].m, gens[b].n, p.cap_b[b], sc, u, s, v);
+    }
+    full_u = std::max<size_t>(full_u, u); full_s = std::max<size_t>(full_s, s); full_v = std::max<size_t>(full_v, v);
   }
   p.nrefs = (int)refs.size();
+  for (BlockRef& r : refs)
+    if (r.full_slot <= -2) r.full_slot = p.nrefs + (-r.full_slot - 2);
+  p.nslots = p.nrefs + ntaped;
 
   // ---- tasks, grouped into chunks whose scratch (QR operands, cores) fits the
   // budget; scratch offsets are local to a chunk, chunks run one after another
@@ -320,12 +352,13 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
       t.kcap = L.rcap;
       t.in1 = i;
       t.a_off = L.u_off;
-      t.a_in_baca = 1;
+      t.src_u_off = L.u_off;
+      t.a_in_baca = p.tape ? 0 : 1;  // a tape keeps the BACA factors for the reverse pass
       t.rows_a = L.m;
       t.lda = L.m;
       t.rows_b = L.n;
       t.src_v_off = L.v_off;
-      t.out = p.Lb[b] == 0 ? p.user_ref_first + b : p.full_idx[b][0][a * nb + cc];
+      t.out = p.Lb[b] == 0 ? (p.tape ? p.root_tape_first + b : p.user_ref_first + b) : p.full_idx[b][0][a * nb + cc];
     }
     add_stage(ts, TASK_LEAF, -1, 0);
   }
@@ -363,7 +396,8 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
             t.in2 = p.half_idx[b][l][(2 * a + 1) * ncn + cc];
             t.rows_a = (int32_t)cols[b][l][cc].second;
             t.lda = t.rows_a;
-            t.out = p.Lb[b] == l ? p.user_ref_first + b : p.full_idx[b][l][a * ncn + cc];
+            t.out = p.Lb[b] == l ? (p.tape ? p.root_tape_first + b : p.user_ref_first + b)
+                                 : p.full_idx[b][l][a * ncn + cc];
             t.m1 = (int32_t)rows[b][l - 1][2 * a].second;
             tv.push_back(t);
           }
@@ -431,7 +465,7 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
   p.queue = Lo.take(64);
   p.desc_region = Lo.take(D.size());
   p.leafout_off = Lo.take((size_t)p.nleaves * sizeof(LeafOut)).off;
-  p.ranks_off = Lo.take((size_t)p.nrefs * 4).off;
+  p.ranks_off = Lo.take((size_t)p.nslots * 4).off;
   for (Stage& st : p.stages) st.dims_off = Lo.take((size_t)st.ntasks * sizeof(TaskDims)).off;
   p.uar = Lo.take((size_t)uo * p.esz);
   p.var = Lo.take((size_t)vo * p.esz);

@@ -68,7 +68,10 @@ struct Plan {
   Region desc_region;
   size_t leafdesc_off = 0, order_off = 0, gparams_off = 0, refs_off = 0;
   int nrefs = 0;
+  int nslots = 0;                 // length of the rank array (refs, then full-triplet counts)
   int user_ref_first = 0;         // global ref index of block 0's result
+  bool tape = false;              // HBACA_FLAG_TAPE: every node keeps all its singular triplets
+  int root_tape_first = -1;       // tape: global ref index of block 0's root node
   // device-written tables
   size_t leafout_off = 0, ranks_off = 0;
   // workspace regions

@@ -50,6 +50,9 @@ struct BlockRef {
   int32_t m, n;
   int32_t rank_slot;            // index into the rank array
   int32_t cap;                  // rank capacity (columns of U, rows of V)
+  int32_t store_cap;            // columns of U / rows of V the storage holds (>= cap)
+  int32_t full_slot;            // rank-array index receiving the number of stored singular
+                                // triplets (all of them, not only the kept ones), or -1
   void* U;                      // caller buffers of a block's final factors: when set they
   double* S;                    // replace the arena + offset addresses
   void* V;
@@ -77,6 +80,8 @@ struct SvdTask {
   int64_t ord_off;     // 2 * kcap ints: Jacobi column order, then the QRCP permutation
   int32_t out;         // block index in the output store
   int32_t m1;          // HORIZ / VERT: rows (VERT) or columns (HORIZ) of the first child
+  int64_t src_u_off;   // LEAF with a_in_baca = 0: offset of the leaf's U in the BACA U arena
+                       // (the QR then works on a copy and the BACA factors survive the call)
 };
 
 // Device-side per-task sizes written by the kernels.
@@ -86,7 +91,8 @@ struct TaskDims {
   int32_t krb;     // rows of R_B (LEAF) = min(rows_b, k)
   int32_t s;       // truncated rank
   int32_t sweeps;  // Jacobi sweeps run
-  int32_t pad[3];
+  int32_t nout;    // singular triplets written to the output (s, or all of them when taped)
+  int32_t pad[2];
 };
 
 struct QrJob {

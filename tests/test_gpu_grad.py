@@ -1,0 +1,149 @@
+"""GPU parity of y = U(S(V X)) and of its reverse pass with frozen pivots
+(hbaca_apply, hbaca_apply_backward) through the C ABI.  The reference
+gradient is the central finite difference of the oracle H-BACA with the
+GPU's pivots (frozen-pivot replay of every leaf) and the oracle's own
+truncation ranks frozen; a second reference is autograd through the dense
+kernel matrix, which differs from the gradient of the compressed map by
+O(eps).  Needs a GB300."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import generators as og
+from oracle import hbaca as oh
+from paper_1901_06101_gb300 import binding as B
+from paper_1901_06101_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return B.Context()
+
+
+def _case(seed, m, n, nrhs):
+    x, y = inputs.gaussian_pair(seed=seed, m=m, n=n)
+    X = inputs.rhs(seed + 100, n, nrhs)
+    return x, y, X
+
+
+def _forward(ctx, x, y, h, X, L, d, eps, cap=256, flags=B.FLAG_TAPE):
+    spec = B.gaussian(x, y, h)
+    opts = B.make_opts(eps, d, L, seed=0, rank_cap=cap, leaf_rank_cap=cap, flags=flags)
+    comp = B.compress(ctx, spec, opts)
+    Y = B.apply(ctx, spec, comp, torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    return spec, opts, comp, Y
+
+
+def _oracle_loss(x, y, h, X, L, d, eps, traces, ranks=None):
+    g = og.Gaussian(x, y, h)
+    r = oh.hbaca(g, L, d, eps, seed=0, forced=traces, ranks=ranks)
+    Ah = (r["U"] * r["s"][None, :]) @ r["V"]
+    Y = Ah @ X
+    return 0.5 * float(np.sum(Y * Y)), r
+
+
+def test_tape_mode_leaves_the_result_unchanged(ctx):
+    x, y, X = _case(11, 700, 650, 3)
+    a = _forward(ctx, x, y, 0.7, X, 1, 8, 1e-8, flags=0)[2]
+    b = _forward(ctx, x, y, 0.7, X, 1, 8, 1e-8, flags=B.FLAG_TAPE)[2]
+    assert a.rank == b.rank
+    assert torch.equal(a.S, b.S) and torch.equal(a.U, b.U) and torch.equal(a.V, b.V)
+
+
+def test_apply_and_dX_match_dense_products(ctx):
+    x, y, X = _case(12, 900, 800, 5)
+    spec, opts, comp, Y = _forward(ctx, x, y, 0.7, X, 2, 8, 1e-8)
+    Ah = (comp.U * comp.S[None, :]) @ comp.V
+    Xt = torch.from_numpy(X).cuda()
+    ref = Ah @ Xt
+    assert float(torch.linalg.norm(Y - ref)) <= 1e-13 * float(torch.linalg.norm(ref))
+    dY = torch.from_numpy(inputs.rhs(5, 900, 5)).cuda()
+    dh, dx, dy, dX = B.apply_backward(ctx, spec, opts, comp, Xt, dY)
+    refX = Ah.T @ dY
+    assert float(torch.linalg.norm(dX - refX)) <= 1e-13 * float(torch.linalg.norm(refX))
+
+
+@pytest.mark.parametrize("m,n,L,d", [(600, 520, 1, 8), (777, 513, 2, 8)])
+def test_gradient_matches_frozen_pivot_finite_differences(ctx, m, n, L, d):
+    eps, h, nrhs = 1e-8, 0.7, 4
+    x, y, X = _case(21 + L, m, n, nrhs)
+    spec, opts, comp, Y = _forward(ctx, x, y, h, X, L, d, eps)
+    dh, dx, dy, _ = B.apply_backward(ctx, spec, opts, comp, torch.from_numpy(X).cuda(), Y, want_dX=False)
+    dh = float(dh)
+    dx = dx.cpu().numpy()
+    dy = dy.cpu().numpy()
+    nb = 1 << L
+    traces = {leaf: B.read_leaf_trace(spec, opts, comp.ws, leaf) for leaf in range(nb * nb)}
+    loss0, r0 = _oracle_loss(x, y, h, X, L, d, eps, traces)
+    assert r0["r"] == comp.rank
+    Ygpu = Y.cpu().numpy()
+    assert abs(0.5 * float(np.sum(Ygpu * Ygpu)) - loss0) <= 1e-10 * loss0
+    frozen = r0["ranks"]
+    # d/dh by central differences, step 1e-6 h
+    dlt = 1e-6 * h
+    lp, rp = _oracle_loss(x, y, h + dlt, X, L, d, eps, traces, frozen)
+    lm, rm = _oracle_loss(x, y, h - dlt, X, L, d, eps, traces, frozen)
+    fd = (lp - lm) / (2 * dlt)
+    assert abs(dh - fd) <= 1e-6 * abs(fd), (dh, fd)
+    # directional derivatives in the point coordinates
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        px = rng.standard_normal(x.shape)
+        py = rng.standard_normal(y.shape)
+        t = 1e-6
+        lp, _ = _oracle_loss(x + t * px, y + t * py, h, X, L, d, eps, traces, frozen)
+        lm, _ = _oracle_loss(x - t * px, y - t * py, h, X, L, d, eps, traces, frozen)
+        fd = (lp - lm) / (2 * t)
+        an = float(np.sum(dx * px) + np.sum(dy * py))
+        assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-12 * loss0), (an, fd)
+
+
+def test_gradient_close_to_dense_autograd(ctx):
+    """The compressed map differs from A by O(eps): its gradient agrees with
+    autograd through the dense matrix to well within 1e-6 (relative, in norm)."""
+    eps, h, nrhs = 1e-10, 0.7, 4
+    x, y, X = _case(31, 640, 600, nrhs)
+    spec, opts, comp, Y = _forward(ctx, x, y, h, X, 1, 8, eps)
+    dh, dx, dy, _ = B.apply_backward(ctx, spec, opts, comp, torch.from_numpy(X).cuda(), Y, want_dX=False)
+    ht = torch.tensor(h, dtype=torch.float64, requires_grad=True)
+    xt = torch.tensor(x, requires_grad=True)
+    yt = torch.tensor(y, requires_grad=True)
+    A = torch.exp(-torch.cdist(xt, yt) ** 2 / (2 * ht ** 2))
+    loss = 0.5 * torch.sum((A @ torch.from_numpy(X)) ** 2)
+    gh, gx, gy = torch.autograd.grad(loss, (ht, xt, yt))
+    assert abs(float(dh) - float(gh)) <= 1e-6 * abs(float(gh))
+    assert float(torch.linalg.norm(dx.cpu() - gx)) <= 1e-6 * float(torch.linalg.norm(gx))
+    assert float(torch.linalg.norm(dy.cpu() - gy)) <= 1e-6 * float(torch.linalg.norm(gy))
+
+
+def test_autograd_function(ctx):
+    eps, h0, nrhs = 1e-8, 0.7, 2
+    x, y, X = _case(41, 500, 450, nrhs)
+    h = torch.tensor(h0, dtype=torch.float64, device="cuda", requires_grad=True)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    yt = torch.tensor(y, device="cuda", requires_grad=True)
+    Xt = torch.tensor(X, device="cuda", requires_grad=True)
+    Yh = B.gaussian_hbaca_apply(h, xt, yt, Xt, ctx, eps, 8, 1, rank_cap=256, leaf_rank_cap=256)
+    loss = 0.5 * (Yh ** 2).sum()
+    loss.backward()
+    spec, opts, comp, Y = _forward(ctx, x, y, h0, X, 1, 8, eps)
+    dh, dx, dy, dX = B.apply_backward(ctx, spec, opts, comp, torch.from_numpy(X).cuda(), Y)
+    # two runs of the reverse pass differ only in the order of their atomic sums
+    assert abs(float(h.grad) - float(dh)) <= 1e-9 * abs(float(dh))
+    assert float(torch.linalg.norm(xt.grad - dx)) <= 1e-9 * float(torch.linalg.norm(dx))
+    assert float(torch.linalg.norm(yt.grad - dy)) <= 1e-9 * float(torch.linalg.norm(dy))
+    assert float(torch.linalg.norm(Xt.grad - dX)) <= 1e-9 * float(torch.linalg.norm(dX))
+
+
+def test_backward_refuses_untaped_workspace(ctx):
+    x, y, X = _case(51, 300, 280, 2)
+    spec, opts, comp, Y = _forward(ctx, x, y, 0.7, X, 1, 8, 1e-8, flags=0)
+    tape_opts = B.make_opts(1e-8, 8, 1, seed=0, rank_cap=256, leaf_rank_cap=256, flags=B.FLAG_TAPE)
+    with pytest.raises(B.HbacaError):
+        B.apply_backward(ctx, spec, tape_opts, comp, torch.from_numpy(X).cuda(), Y)

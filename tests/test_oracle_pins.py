@@ -381,3 +381,46 @@ def test_replay_flags_a_non_greedy_pivot():
     bad[0] = dict(bad[0], dk=bad[0]["dk"] - 1, jbar=bad[0]["jbar"][:-1])
     rep = ob.baca_replay(g, 6, 1e-9, bad, seed=5)
     assert not rep["recs"][0]["valid_dk"]
+
+
+def test_replay_with_full_blocks_is_the_skeleton_approximation():
+    """With every kept block full (d_k = d), the cross approximation after K
+    iterations is the skeleton A(:, J*) A(I*, J*)^-1 A(I*, :) over the kept
+    rows I* and columns J* (Alg. 2 is a block partial LU): the identity the
+    frozen-pivot reverse pass rests on."""
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (80, 3))
+    y = rng.uniform(0, 1, (70, 3)) + np.array([1.5, 0.0, 0.0])
+    g = og.Gaussian(x, y, 0.6)
+    d = 4
+    r = ob.baca(g, d, 1e-13, seed=0, bid=0)
+    K = 0
+    for t in r["trace"]:
+        if t["dk"] != d or len(t["I"]) != d:
+            break
+        K += 1
+    K = min(K, 3)
+    assert K >= 2
+    rep = ob.baca_replay(g, d, 1e-13, r["trace"][:K], seed=0, bid=0, stop="iterations")
+    Istar = [i for t in r["trace"][:K] for i in t["I"][:t["dk"]]]
+    Jstar = [t["J"][p] for t in r["trace"][:K] for p in t["jbar"][:t["dk"]]]
+    A = g(np.arange(g.m), np.arange(g.n))
+    skel = A[:, Jstar] @ np.linalg.solve(A[np.ix_(Istar, Jstar)], A[Istar, :])
+    assert np.linalg.norm(rep["U"] @ rep["V"] - skel) <= 1e-9 * np.linalg.norm(A)
+    # and it is not the trivial case: A itself is not reproduced yet
+    assert np.linalg.norm(A - skel) > 1e-6 * np.linalg.norm(A)
+
+
+def test_frozen_truncation_rank_reproduces_eps_rank():
+    """H-BACA with every truncation rank frozen at the ranks an unfrozen run
+    took is the same computation; a smaller frozen rank truncates further."""
+    x, y = inputs.gaussian_pair(seed=4, m=240, n=200)
+    g = og.Gaussian(x, y, 0.7)
+    a = oh.hbaca(g, 1, 8, 1e-8, seed=0)
+    b = oh.hbaca(g, 1, 8, 1e-8, seed=0, ranks=a["ranks"])
+    assert a["r"] == b["r"]
+    np.testing.assert_array_equal(a["s"], b["s"])
+    root = ("full", 1, 0, 0)
+    c = oh.hbaca(g, 1, 8, 1e-8, seed=0, ranks={root: a["r"] - 3})
+    assert c["r"] == a["r"] - 3
+    np.testing.assert_allclose(c["s"], a["s"][:a["r"] - 3], rtol=1e-12)
