@@ -41,6 +41,19 @@ WORKLOADS = {
     "helmholtz8000": dict(workload="helmholtz_c128_8000_d16_L3_eps1e-4", kernel="helmholtz exp(ikr)/r",
                           m=8000, n=8000, k=4 * np.pi, d=16, levels=3, eps=1e-4, seed=1,
                           rank_cap=256, leaf_rank_cap=256),
+    # 4096 independent admissible Gaussian-kernel blocks of uneven sizes
+    # (m, n log-uniform in [64, 2048], h log-uniform in [0.1, 10], seed 3),
+    # leaves of at most 512 rows and columns: one batched call against the
+    # plain loop of one call per block at the same eps
+    # differentiated H-BACA: Gaussian kernel between 16384 points in [0,1]^3
+    # and 16384 in [2,3]x[0,1]^2, h = 0.7, eps = 1e-8, d = 16, 8 x 8 leaves;
+    # forward = taped compression + y = U(S(VX)) for 64 N(0,1) right-hand
+    # sides, backward = dL/dh, dL/dx, dL/dy, dL/dX of L = 0.5 ||y||^2
+    "grad16384": dict(workload="gaussian_f64_16384_d16_L3_eps1e-8_nrhs64_grad", kernel="gaussian",
+                      m=16384, n=16384, h=0.7, d=16, levels=3, eps=1e-8, seed=0, nrhs=64,
+                      rank_cap=512, leaf_rank_cap=384),
+    "batched4096": dict(workload="gaussian_f64_4096_blocks_64-2048_d8_leaf512_eps1e-8", kernel="gaussian",
+                        nblocks=4096, d=8, levels=-512, eps=1e-8, seed=3, rank_cap=256, leaf_rank_cap=256),
 }
 WORKLOAD = WORKLOADS["helmholtz20000"]
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max SM clock
@@ -55,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--workload", default="helmholtz20000", choices=sorted(WORKLOADS))
+    ap.add_argument("--nblocks", type=int, default=None, help="batched workload: first N blocks only")
+    ap.add_argument("--no-loop", action="store_true", help="batched workload: skip the per-block loop")
     return ap.parse_args()
 
 
@@ -308,12 +323,163 @@ def run_ours(args, rank, world):
                 h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, seconds_per_step=e2e_s), x=x, y=y)
 
 
+def run_grad(args):
+    """One step = forward (taped compression + apply) and backward of the
+    differentiated workload; reports both times and their ratio."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+
+    cfg = WORKLOAD
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    x, y = inputs.gaussian_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
+    X = torch.from_numpy(inputs.rhs(cfg["seed"] + 1, cfg["n"], cfg["nrhs"])).to(dev)
+    ctx = B.Context()
+    spec = B.gaussian(x, y, cfg["h"])
+    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
+    plain = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+                        leaf_rank_cap=cfg["leaf_rank_cap"])
+    ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
+    wsp = torch.empty(B.workspace_size(spec.gen, plain), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    fwd, bwd, fwd_plain = [], [], []
+    comp = Y = None
+    with ClockSampler(dev.index) as clk:
+        for it in range(args.warmup + args.steps):
+            tf, (comp, Y) = timed(lambda: (lambda c: (c, B.apply(ctx, spec, c, X)))(B.compress(ctx, spec, opts, ws=ws)))
+            tb, grads = timed(lambda: B.apply_backward(ctx, spec, opts, comp, X, Y))
+            tp, _ = timed(lambda: B.compress(ctx, spec, plain, ws=wsp))
+            if it >= args.warmup:
+                fwd.append(tf)
+                bwd.append(tb)
+                fwd_plain.append(tp)
+    f, b = float(np.mean(fwd)), float(np.mean(bwd))
+    dh = float(grads[0])
+    line = {"metric": METRIC, "value": b / f, "unit": "backward ms / forward ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f + b, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, l2="flushed between timed calls (512 MiB write)", parallelism="1 GPU"),
+            "forward_ms": f, "backward_ms": b, "forward_untaped_compress_ms": float(np.mean(fwd_plain)),
+            "rank": comp.rank, "dL_dh": dh, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
+def run_batched(args):
+    """One step = hbaca_compress_batched over all blocks.  The plain per-block
+    loop (one hbaca_compress per block, same d, eps, leaf size and caps) is
+    timed beside it on the same stream."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+
+    cfg = WORKLOAD
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    if args.nblocks:
+        cfg = dict(cfg, nblocks=args.nblocks, workload=cfg["workload"].replace("4096", str(args.nblocks)))
+    blocks = inputs.batched_blocks(seed=cfg["seed"], nblocks=cfg["nblocks"])
+    ctx = B.Context()
+    specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
+    entries = float(sum(x.shape[0] * y.shape[0] for (x, y, _) in blocks))
+    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE)
+    batch = B.Batch(ctx, specs, opts)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize(dev)
+    ranks = batch.ranks()
+    step_ms, phase = [], []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.run()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            phase.append(B.phase_times(ctx))
+    ms = float(np.mean(step_ms))
+    (tb, tr, tm, tt), launches = phase[-1]
+    # the plain loop: one compress per block, shared workspace and outputs
+    lopts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+                        leaf_rank_cap=cfg["leaf_rank_cap"])
+    wsz = max(B.workspace_size(s.gen, lopts) for s in specs)
+    lws = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    mmax = max(s.m for s in specs)
+    nmax = max(s.n for s in specs)
+    cap = cfg["rank_cap"]
+    lout = (torch.empty(cap * mmax, dtype=torch.float64, device=dev),
+            torch.empty(cap, dtype=torch.float64, device=dev),
+            torch.empty(cap * nmax, dtype=torch.float64, device=dev))
+
+    def loop():
+        rk = []
+        for s in specs:
+            c = min(cap, s.m, s.n)
+            out = (lout[0][:c * s.m].view(c, s.m), lout[1][:c], lout[2][:c * s.n].view(c, s.n))
+            rk.append(B.compress(ctx, s, lopts, ws=lws, out=out).rank)
+        return rk
+
+    loop_ranks = loop() if not args.no_loop else [0]  # warm-up
+    loop_steps = max(1, min(args.steps, 2)) if not args.no_loop else 0
+    loop_ms = [float("nan")]
+    for _ in range(loop_steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loop()
+        e1.record(stream)
+        e1.synchronize()
+        loop_ms.append(e0.elapsed_time(e1))
+    lms = float(np.mean(loop_ms[1:] if loop_steps else loop_ms))
+    line = {"metric": METRIC, "value": entries / (ms / 1e3), "unit": "matrix entries compressed/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, l2="flushed between timed steps (512 MiB write)", parallelism="1 GPU"),
+            "batched_vs_loop": {"batched_ms": ms, "per_block_loop_ms": lms, "speedup": lms / ms,
+                                "loop_steps": loop_steps},
+            "phases_ms": {"leaf_baca_ms": tb, "leaf_recompression_ms": tr, "merge_ms": tm},
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "ranks": {"max": max(ranks), "mean": float(np.mean(ranks)), "loop_mean": float(np.mean(loop_ranks))},
+            "workspace_gib": batch.ws.numel() / 2 ** 30}
+    print(json.dumps(line))
+
+
 def main():
     global WORKLOAD
     args = parse()
     WORKLOAD = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "grad16384":
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("the gradient workload is a single-GPU forward/backward comparison")
+        run_grad(args)
+        return
+    if args.workload == "batched4096":
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("the batched workload is a single-GPU comparison of the two call forms")
+        run_batched(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

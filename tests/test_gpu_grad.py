@@ -147,3 +147,31 @@ def test_backward_refuses_untaped_workspace(ctx):
     tape_opts = B.make_opts(1e-8, 8, 1, seed=0, rank_cap=256, leaf_rank_cap=256, flags=B.FLAG_TAPE)
     with pytest.raises(B.HbacaError):
         B.apply_backward(ctx, spec, tape_opts, comp, torch.from_numpy(X).cuda(), Y)
+
+
+def test_cfg5_full_size_gradient_against_dense_autograd(ctx):
+    """The differentiated workload at full size (16384 x 16384, 8 x 8 leaves,
+    d = 16, eps = 1e-8, 64 right-hand sides) against autograd through the
+    dense kernel matrix on the GPU (torch, test-side reference only); the two
+    differ by O(eps) relative."""
+    m = n = 16384
+    eps, h, nrhs = 1e-8, 0.7, 64
+    x, y = inputs.gaussian_pair(seed=0, m=m, n=n)
+    X = inputs.rhs(1, n, nrhs)
+    spec, opts, comp, Y = _forward(ctx, x, y, h, X, 3, 16, eps, cap=512)
+    Xt = torch.from_numpy(X).cuda()
+    dh, dx, dy, dX = B.apply_backward(ctx, spec, opts, comp, Xt, Y)
+    ht = torch.tensor(h, dtype=torch.float64, device="cuda", requires_grad=True)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    yt = torch.tensor(y, device="cuda", requires_grad=True)
+    d2 = (xt * xt).sum(1)[:, None] + (yt * yt).sum(1)[None, :] - 2.0 * xt @ yt.T
+    A = torch.exp(-d2 / (2 * ht ** 2))
+    Yd = A @ Xt
+    loss = 0.5 * torch.sum(Yd ** 2)
+    gh, gx, gy = torch.autograd.grad(loss, (ht, xt, yt))
+    assert float(torch.linalg.norm(Y - Yd)) <= 1e-6 * float(torch.linalg.norm(Yd))
+    assert abs(float(dh) - float(gh)) <= 1e-5 * abs(float(gh)), (float(dh), float(gh))
+    assert float(torch.linalg.norm(dx - gx)) <= 1e-5 * float(torch.linalg.norm(gx))
+    assert float(torch.linalg.norm(dy - gy)) <= 1e-5 * float(torch.linalg.norm(gy))
+    refX = A.detach().T @ Y
+    assert float(torch.linalg.norm(dX - refX)) <= 1e-6 * float(torch.linalg.norm(refX))
