@@ -440,7 +440,7 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, doub
 constexpr int kJacRegs = 8;  // columns of up to 256 rows are held in registers
 
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams<T> P, int max_sweeps) {
+__global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DenseParams<T> P, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
@@ -520,16 +520,15 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
         T* cb = M + (int64_t)b * ld;
         T* ya = Y + (int64_t)a * ld;
         T* yb = Y + (int64_t)b * ld;
-        if (mr <= 32 * kJacRegs && nc <= 32 * kJacRegs) {
-          // both columns of M and of Y in registers: one L2 round trip per pair
-          T ra[kJacRegs], rb[kJacRegs], qa[kJacRegs], qb[kJacRegs];
+        if (mr <= 32 * kJacRegs) {
+          // both columns of M in registers: one L2 round trip per pair; the
+          // accumulated rotation W is streamed (it does not feed the dots)
+          T ra[kJacRegs], rb[kJacRegs];
 #pragma unroll
           for (int u = 0; u < kJacRegs; ++u) {
             const int i = lane + 32 * u;
             ra[u] = i < mr ? ldcg(ca + i) : Traits<T>::zero();
             rb[u] = i < mr ? ldcg(cb + i) : Traits<T>::zero();
-            qa[u] = i < nc ? ldcg(ya + i) : Traits<T>::zero();
-            qb[u] = i < nc ? ldcg(yb + i) : Traits<T>::zero();
           }
           double al = 0.0, be = 0.0;
           T ga = Traits<T>::zero();
@@ -557,12 +556,8 @@ __global__ void __launch_bounds__(kDenseThreads) jacobi_kernel(const DenseParams
               ca[i] = sub(scale(x, cs), scale(yv, sn));
               cb[i] = add(scale(x, sn), scale(yv, cs));
             }
-            if (i < nc) {
-              const T x = qa[u], yv = mul(ph, qb[u]);
-              ya[i] = sub(scale(x, cs), scale(yv, sn));
-              yb[i] = add(scale(x, sn), scale(yv, cs));
-            }
           }
+          rotate_pair(ya, yb, nc, cs, sn, ph, lane);
         } else {
           double al = 0.0, be = 0.0;
           T ga = Traits<T>::zero();
