@@ -263,6 +263,16 @@ hbaca_status hbaca_read_leaf_trace_batched(int32_t nblocks, const hbaca_gen* gen
    the number of kernels the call launched.  Synchronises on the events. */
 hbaca_status hbaca_phase_times(hbaca_ctx* ctx, double ms[4], int32_t* launches);
 
+/* Device time per kernel class of the last hbaca_compress(_batched) on `ctx`
+   that ran with HBACA_FLAG_PROFILE (CUDA events around every launch, on the
+   call's stream).  Classes, in order: leaf BACA (Alg. 2), QR-operand
+   packing, Householder QR, core product, pivoted QR of the core, Jacobi SVD
+   of the core, singular vectors of the core, reflector application,
+   block-diagonal product, root copy (taped calls).  ms[c] is the summed
+   duration, launches[c] the number of launches.  Synchronises on the events. */
+#define HBACA_KERNEL_CLASSES 10
+hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES], int32_t launches[HBACA_KERNEL_CLASSES]);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* hbaca_last_error(void);
 

@@ -78,6 +78,8 @@ SIGNATURES = [
                                              ctypes.c_int64, ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
     ("hbaca_debug_backward_json", ctypes.c_int64, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                                    ctypes.c_int64, ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("hbaca_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int32)]),
     ("hbaca_apply_workspace_size", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("hbaca_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Result), ctypes.c_void_p,
                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -554,6 +556,18 @@ def backward_json(spec, opts, ws, nrhs):
     lib().hbaca_debug_backward_json(ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()), nrhs,
                                     buf, n, st)
     return json.loads(buf.value.decode())
+
+
+KERNEL_CLASSES = ["baca_leaf_kernel", "pack_kernel", "qr_kernel", "core_kernel", "qrcp_core_kernel",
+                  "jacobi_kernel", "finish_kernel", "qapply_kernel", "blockprod_kernel", "copyroot_kernel"]
+
+
+def kernel_times(ctx):
+    """{kernel: (ms, launches)} of the last profiled call (CUDA events)."""
+    ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+    nl = (ctypes.c_int32 * len(KERNEL_CLASSES))()
+    check(lib().hbaca_kernel_times(ctx.ptr, ms, nl))
+    return {k: (ms[i], nl[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def phase_times(ctx):

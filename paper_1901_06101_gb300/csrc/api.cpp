@@ -19,6 +19,7 @@ struct hbaca_ctx {
   cudaEvent_t ev[4];
   bool have_times;
   int launches;
+  hbaca::KernelTimer kt;
 };
 
 namespace {
@@ -75,7 +76,7 @@ hbaca_status hbaca_create(hbaca_ctx** ctx) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (major * 10 + minor != 103)
     return fail(HBACA_CUDA, "libhbaca is built for sm_103a (GB300); device is sm_" + std::to_string(major * 10 + minor));
-  *ctx = new (std::nothrow) hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0};
+  *ctx = new (std::nothrow) hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0, {}};
   if (!*ctx) return fail(HBACA_INVALID_ARG, "out of host memory");
   for (int i = 0; i < 4; ++i) {
     e = cudaEventCreate(&(*ctx)->ev[i]);
@@ -122,10 +123,13 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
   hbaca::RunCtx rc{ws, st, ctx->sms, &outs[0], 0};
+  rc.sizes_known = (opts->flags & HBACA_FLAG_ASYNC) == 0;
   const bool prof = (opts->flags & HBACA_FLAG_PROFILE) != 0;
   ctx->have_times = false;
   if (prof) {
     for (int i = 0; i < 4; ++i) rc.ev[i] = ctx->ev[i];
+    ctx->kt.reset();
+    rc.kt = &ctx->kt;
     cudaError_t pe = cudaEventRecord(ctx->ev[0], st);
     if (pe != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(pe));
   }
@@ -320,6 +324,28 @@ hbaca_status hbaca_phase_times(hbaca_ctx* ctx, double ms[4], int32_t* launches) 
   ms[1] = t[1];
   ms[2] = t[2];
   ms[3] = (double)t[0] + t[1] + t[2];
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES], int32_t launches[HBACA_KERNEL_CLASSES]) {
+  if (!ctx || !ms || !launches) return fail(HBACA_INVALID_ARG, "NULL argument");
+  if (!ctx->have_times) return fail(HBACA_INVALID_ARG, "the last call did not run with HBACA_FLAG_PROFILE");
+  for (int i = 0; i < HBACA_KERNEL_CLASSES; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+  for (const auto& mk : ctx->kt.marks) {
+    if (e != cudaSuccess) break;
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, ctx->kt.pool[mk.second], ctx->kt.pool[mk.second + 1]);
+    if (mk.first >= 0 && mk.first < HBACA_KERNEL_CLASSES) {
+      ms[mk.first] += t;
+      launches[mk.first] += 1;
+    }
+  }
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("event timing: ") + cudaGetErrorString(e));
   tls_err.clear();
   return HBACA_OK;
 }

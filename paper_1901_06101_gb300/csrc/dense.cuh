@@ -145,7 +145,8 @@ __global__ void pack_kernel(const DenseParams<T> P) {
     dm.s = 0;
     dm.sweeps = 0;
     dm.nout = 0;
-    dm.pad[0] = dm.pad[1] = 0;
+    dm.rotations = 0;
+    dm.pad = 0;
     P.dims[ti] = dm;
   }
 }
@@ -439,12 +440,201 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, doub
 
 constexpr int kJacRegs = 8;  // columns of up to 256 rows are held in registers
 
+// Loads of the Jacobi sweeps: columns in another CTA's shared memory are read
+// with plain (distributed shared memory) loads, columns in global memory
+// through L2.
+template <typename T, bool kDsm>
+__device__ __forceinline__ T jld(const T* p) {
+  if constexpr (kDsm) return *p;
+  else return ldcg(p);
+}
+
+// One element of a Jacobi rotation with the phase folded in:
+// a' = cs a - sp b, b' = sn a + cp b with sp = sn ph, cp = cs ph (ph = e^{-i phi}).
+__device__ __forceinline__ void rot_elem(double& a, double& b, double cs, double sn, double sp, double cp) {
+  const double a0 = a, b0 = b;
+  a = fma(-sp, b0, cs * a0);
+  b = fma(cp, b0, sn * a0);
+}
+__device__ __forceinline__ void rot_elem(cplx& a, cplx& b, double cs, double sn, cplx sp, cplx cp) {
+  const cplx a0 = a, b0 = b;
+  a.re = fma(sp.im, b0.im, fma(-sp.re, b0.re, cs * a0.re));
+  a.im = fma(-sp.im, b0.re, fma(-sp.re, b0.im, cs * a0.im));
+  b.re = fma(-cp.im, b0.im, fma(cp.re, b0.re, sn * a0.re));
+  b.im = fma(cp.im, b0.re, fma(cp.re, b0.im, sn * a0.im));
+}
+
+template <typename T, bool kDsm>
+__device__ __forceinline__ void rotate_pair_t(T* a, T* b, int len, double cs, double sn, T sp, T cp, int lane) {
+  for (int i = lane; i < len; i += 32) {
+    T ai = jld<T, kDsm>(a + i), bi = jld<T, kDsm>(b + i);
+    rot_elem(ai, bi, cs, sn, sp, cp);
+    a[i] = ai;
+    b[i] = bi;
+  }
+}
+
+// Inner products of a pair posted by its warp, and the rotation computed for
+// it by one lane of warp 0 (all pairs of a CTA's batch at once).
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DenseParams<T> P, int max_sweeps) {
+struct JPair {
+  double al, be;
+  T ga;
+  double cs, sn;
+  T sp, cp;
+  int ok, pad;
+};
+constexpr int kJSlotBytes = 1024;  // room for 8 JPair<cplx>
+
+// The sweeps of one task.  kDsm: column j of X and of the accumulated rotation
+// W live in the shared memory of CTA j mod c of the cluster, slot j / c
+// ([X(0..mr-1), W(0..nc-1)], stride ldc); otherwise X and W are in global
+// memory (column j at M + j ld, Y + j ld).  A round's pairs are taken in
+// batches of one pair per warp of the cluster: the warps form their pairs'
+// inner products, one warp turns them into rotations (a lane per pair), then
+// every warp rotates its pair.
+template <typename T, bool kDsm>
+__device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
+                              T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
+                              int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  auto colX = [&](int j) -> T* {
+    if constexpr (kDsm) return cl.map_shared_rank(dsm, j % c) + (int64_t)(j / c) * ldc;
+    else return M + (int64_t)j * ld;
+  };
+  auto colW = [&](int j) -> T* {
+    if constexpr (kDsm) return colX(j) + mr;
+    else return Y + (int64_t)j * ld;
+  };
+  const int npairs = K / 2;
+  const int per_batch = c * nw;
+  const int nbatch = (npairs + per_batch - 1) / per_batch;
+  const bool regs = mr <= 32 * kJacRegs;
+  unsigned fb = 0;
+  for (; sweep < max_sweeps && K > 1; ++sweep) {
+    const double tau2 = 0.01 * eps * eps * cmax;
+    double wmax = 0.0;
+    if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; }
+    __syncthreads();
+    for (int rd = 0; rd < K - 1; ++rd) {
+      for (int bt = 0; bt < nbatch; ++bt) {
+        // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
+        const int pi = bt * per_batch + q * nw + warp;
+        int a = 0, b = 0;
+        bool act = pi < npairs;
+        if (act) {
+          if (pi == 0) { a = rd; b = K - 1; }
+          else { a = (rd + pi) % (K - 1); b = (rd - pi + K - 1) % (K - 1); }
+          if (a > b) { int tmp = a; a = b; b = tmp; }
+          act = b < nc;  // else a padding column
+        }
+        T* ca = act ? colX(a) : nullptr;
+        T* cb = act ? colX(b) : nullptr;
+        T ra[kJacRegs], rb[kJacRegs];
+        double al = 0.0, be = 0.0;
+        T ga = Traits<T>::zero();
+        if (act) {
+          if (regs) {
+#pragma unroll
+            for (int u = 0; u < kJacRegs; ++u) {
+              const int i = lane + 32 * u;
+              ra[u] = i < mr ? jld<T, kDsm>(ca + i) : Traits<T>::zero();
+              rb[u] = i < mr ? jld<T, kDsm>(cb + i) : Traits<T>::zero();
+            }
+#pragma unroll
+            for (int u = 0; u < kJacRegs; ++u) {
+              if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
+                al += abs2(ra[u]);
+                be += abs2(rb[u]);
+                ga = cmac(ga, ra[u], rb[u]);
+              }
+            }
+          } else {
+            for (int i = lane; i < mr; i += 32) {
+              const T xa = jld<T, kDsm>(ca + i), xb = jld<T, kDsm>(cb + i);
+              al += abs2(xa);
+              be += abs2(xb);
+              ga = cmac(ga, xa, xb);
+            }
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          wmax = fmax(wmax, fmax(al, be));
+        }
+        if (lane == 0) {
+          slots[warp].al = al;
+          slots[warp].be = be;
+          slots[warp].ga = ga;
+          slots[warp].ok = act ? 1 : 0;
+        }
+        __syncthreads();
+        if (warp == 0 && lane < nw) {
+          JPair<T>& sp = slots[lane];
+          if (sp.ok) {
+            double cs, sn;
+            T ph;
+            if (jacobi_rotation(sp.al, sp.be, sp.ga, tol, negl, fro2, cs, sn, ph)) {
+              sp.cs = cs;
+              sp.sn = sn;
+              sp.sp = scale(ph, sn);
+              sp.cp = scale(ph, cs);
+            } else {
+              sp.ok = 0;
+            }
+          }
+        }
+        __syncthreads();
+        if (act && slots[warp].ok) {
+          const double cs = slots[warp].cs, sn = slots[warp].sn;
+          const T spv = slots[warp].sp, cpv = slots[warp].cp;
+          if (lane == 0 && fmax(al, be) >= tau2) flag[fb & 1] = 1;
+          ++nrot;
+          if (regs) {
+#pragma unroll
+            for (int u = 0; u < kJacRegs; ++u) {
+              const int i = lane + 32 * u;
+              if (i < mr) {
+                rot_elem(ra[u], rb[u], cs, sn, spv, cpv);
+                ca[i] = ra[u];
+                cb[i] = rb[u];
+              }
+            }
+          } else {
+            rotate_pair_t<T, kDsm>(ca, cb, mr, cs, sn, spv, cpv, lane);
+          }
+          rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
+        }
+      }
+      __syncthreads();
+      cl.sync();
+    }
+    // the largest column norm^2 of this sweep, over the cluster (for the next tau)
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(cmx), (unsigned long long)__double_as_longlong(wmax));
+    __syncthreads();
+    cl.sync();
+    // any relevant rotation anywhere in the cluster this sweep?
+    int any = 0;
+    double cm = 0.0;
+    for (int r = 0; r < c; ++r) {
+      any |= *cl.map_shared_rank(&flag[fb & 1], r);
+      cm = fmax(cm, *cl.map_shared_rank(cmx, r));
+    }
+    if (cm > 0.0) cmax = cm;
+    ++fb;
+    cl.sync();
+    if (!any) break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DenseParams<T> P, int max_sweeps,
+                                                                   int hdr_bytes, int64_t dsm_bytes,
+                                                                   const int32_t* task_list) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
-  const int ti = blockIdx.x / c;
+  const int ti = task_list ? task_list[blockIdx.x / c] : (int)(blockIdx.x / c);
   const SvdTask t = P.tasks[ti];
   const TaskDims dm = P.dims[ti];
   // the sweeps orthogonalise the columns of X = R2^H (nc_M x p), accumulating W
@@ -466,9 +656,21 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
     }
     return;
   }
-  // Y = I
-  {
-    const int per = (nc + c - 1) / c;
+  // the task's columns fit the cluster's shared memory: sweep there (column j
+  // in CTA j mod c), else in global memory
+  const int per = (nc + c - 1) / c;
+  const int64_t ldc = (int64_t)mr + nc;
+  T* dsm = reinterpret_cast<T*>(smem_raw + hdr_bytes);
+  const bool use_dsm = (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
+  if (use_dsm) {  // own columns: X from global memory, W = I
+    for (int l = warp; l < per; l += nw) {
+      const int j = l * c + q;
+      if (j >= nc) continue;
+      T* dst = dsm + (int64_t)l * ldc;
+      for (int i = lane; i < mr; i += 32) dst[i] = M[(int64_t)j * ld + i];
+      for (int i = lane; i < nc; i += 32) dst[mr + i] = from_re<T>(i == j ? 1.0 : 0.0);
+    }
+  } else {  // Y = I
     const int j0 = q * per, j1 = min(nc, j0 + per);
     for (int j = j0; j < j1; ++j)
       for (int i = tid; i < nc; i += blockDim.x) Y[(int64_t)j * ld + i] = from_re<T>(i == j ? 1.0 : 0.0);
@@ -500,104 +702,27 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   // cannot cross the eps-rank threshold.  All pairs are still rotated.
   double* cmx = reinterpret_cast<double*>(smem_raw + 8);  // largest column norm^2 seen this sweep
   int sweep = 0;
-  unsigned fb = 0;
+  int nrot = 0;  // rotations applied by this warp
   if (tid == 0) { flag[0] = 0; flag[1] = 0; }
   cl.sync();
-  for (; sweep < max_sweeps && K > 1; ++sweep) {
-    const double tau2 = 0.01 * P.eps * P.eps * cmax;
-    double wmax = 0.0;
-    if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; }
-    __syncthreads();
-    for (int rd = 0; rd < K - 1; ++rd) {
-      // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
-      for (int pi = q * nw + warp; pi < K / 2; pi += c * nw) {
-        int a, b;
-        if (pi == 0) { a = rd; b = K - 1; }
-        else { a = (rd + pi) % (K - 1); b = (rd - pi + K - 1) % (K - 1); }
-        if (a > b) { int tmp = a; a = b; b = tmp; }
-        if (b >= nc) continue;  // padding column
-        T* ca = M + (int64_t)a * ld;
-        T* cb = M + (int64_t)b * ld;
-        T* ya = Y + (int64_t)a * ld;
-        T* yb = Y + (int64_t)b * ld;
-        if (mr <= 32 * kJacRegs) {
-          // both columns of M in registers: one L2 round trip per pair; the
-          // accumulated rotation W is streamed (it does not feed the dots)
-          T ra[kJacRegs], rb[kJacRegs];
-#pragma unroll
-          for (int u = 0; u < kJacRegs; ++u) {
-            const int i = lane + 32 * u;
-            ra[u] = i < mr ? ldcg(ca + i) : Traits<T>::zero();
-            rb[u] = i < mr ? ldcg(cb + i) : Traits<T>::zero();
-          }
-          double al = 0.0, be = 0.0;
-          T ga = Traits<T>::zero();
-#pragma unroll
-          for (int u = 0; u < kJacRegs; ++u) {
-            if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
-              al += abs2(ra[u]);
-              be += abs2(rb[u]);
-              ga = cmac(ga, ra[u], rb[u]);
-            }
-          }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
-          wmax = fmax(wmax, fmax(al, be));
-          double cs, sn;
-          T ph;
-          if (!jacobi_rotation(al, be, ga, tol, negl, fro2, cs, sn, ph)) continue;
-          if (lane == 0 && fmax(al, be) >= tau2) flag[fb & 1] = 1;
-#pragma unroll
-          for (int u = 0; u < kJacRegs; ++u) {
-            const int i = lane + 32 * u;
-            if (i < mr) {
-              const T x = ra[u], yv = mul(ph, rb[u]);
-              ca[i] = sub(scale(x, cs), scale(yv, sn));
-              cb[i] = add(scale(x, sn), scale(yv, cs));
-            }
-          }
-          rotate_pair(ya, yb, nc, cs, sn, ph, lane);
-        } else {
-          double al = 0.0, be = 0.0;
-          T ga = Traits<T>::zero();
-          for (int i = lane; i < mr; i += 32) {
-            const T xa = ldcg(ca + i), xb = ldcg(cb + i);
-            al += abs2(xa);
-            be += abs2(xb);
-            ga = cmac(ga, xa, xb);
-          }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
-          wmax = fmax(wmax, fmax(al, be));
-          double cs, sn;
-          T ph;
-          if (!jacobi_rotation(al, be, ga, tol, negl, fro2, cs, sn, ph)) continue;
-          if (lane == 0 && fmax(al, be) >= tau2) flag[fb & 1] = 1;
-          rotate_pair(ca, cb, mr, cs, sn, ph, lane);
-          rotate_pair(ya, yb, nc, cs, sn, ph, lane);
-        }
-      }
-      __syncthreads();
-      cl.sync();
+  JPair<T>* slots = reinterpret_cast<JPair<T>*>(smem_raw + hdr_bytes - kJSlotBytes);
+  if (use_dsm)
+    jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
+                           slots, sweep, nrot);
+  else
+    jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
+                            cmx, slots, sweep, nrot);
+  if (use_dsm) {  // the sweeps' result back to global memory for the epilogue and finish_kernel
+    for (int l = warp; l < per; l += nw) {
+      const int j = l * c + q;
+      if (j >= nc) continue;
+      const T* src = dsm + (int64_t)l * ldc;
+      for (int i = lane; i < mr; i += 32) M[(int64_t)j * ld + i] = src[i];
+      for (int i = lane; i < nc; i += 32) Y[(int64_t)j * ld + i] = src[mr + i];
     }
-    // the largest column norm^2 of this sweep, over the cluster (for the next tau)
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(cmx), (unsigned long long)__double_as_longlong(wmax));
-    __syncthreads();
-    cl.sync();
-    // any relevant rotation anywhere in the cluster this sweep?
-    int any = 0;
-    double cm = 0.0;
-    for (int r = 0; r < c; ++r) {
-      any |= *cl.map_shared_rank(&flag[fb & 1], r);
-      cm = fmax(cm, *cl.map_shared_rank(cmx, r));
-    }
-    if (cm > 0.0) cmax = cm;
-    ++fb;
-    cl.sync();
-    if (!any) break;
   }
+  cl.sync();
+  if (lane == 0 && nrot) atomicAdd(&P.dims[ti].rotations, nrot);
   // singular values and their order (CTA 0); then every CTA normalises a
   // share of the kept columns of M in place (X = M / sigma) and writes S
   int* ord = reinterpret_cast<int*>(sv + nc);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "baca.cuh"
 #include "dense.cuh"
@@ -20,6 +21,16 @@ namespace hbaca {
       err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
       return e_;                                                                  \
     }                                                                             \
+  } while (0)
+
+constexpr size_t kJacobiSmemLimit = 220 * 1024;  // dynamic shared memory of one Jacobi CTA
+
+// Bracket one launch with profiling events when the call is profiled.
+#define HB_TIMED(cls, ...)                                   \
+  do {                                                       \
+    if (rc.kt) HB_TRY(rc.kt->begin((cls), rc.st));           \
+    __VA_ARGS__;                                             \
+    if (rc.kt) HB_TRY(rc.kt->end(rc.st));                    \
   } while (0)
 
 template <typename K, typename... Args>
@@ -104,7 +115,7 @@ cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
   int nclusters = std::min(std::min(p.nleaves, ncl), p.max_clusters_scratch);
   p.baca_clusters = nclusters;
   cfg.gridDim = dim3(nclusters * c, 1, 1);
-  HB_TRY(cudaLaunchKernelEx(&cfg, kern, P));
+  HB_TIMED(KC_BACA, HB_TRY(cudaLaunchKernelEx(&cfg, kern, P)));
   ++rc.launches;
   return cudaSuccess;
 }
@@ -161,30 +172,66 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
   const QrJob* qj = reinterpret_cast<const QrJob*>(desc + sg.qrjobs_off);
   const QJob* aj = reinterpret_cast<const QJob*>(desc + sg.qjobs_off);
 
-  pack_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D);
-  HB_TRY(cudaGetLastError());
+  HB_TIMED(KC_PACK, pack_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   const int cq = pick_cluster(sg.nqr, sg.rows_max, rc.sms, 64);
   const size_t qr_smem = (size_t)(3 * (2 + 2 * sg.kcap) + 4) * sizeof(T);
-  HB_TRY(launch_cluster(qr_kernel<T>, sg.nqr * cq, cq, qr_smem, rc.st, D, qj));
-  core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D);
-  HB_TRY(cudaGetLastError());
+  HB_TIMED(KC_QR, HB_TRY(launch_cluster(qr_kernel<T>, sg.nqr * cq, cq, qr_smem, rc.st, D, qj)));
+  HB_TIMED(KC_CORE, core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   const size_t qc_smem = (size_t)sg.kcap * 9 + 2 * sizeof(T) + 32 * 12 + 64 + 16;
   HB_TRY(cudaFuncSetAttribute(qrcp_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qc_smem));
-  qrcp_core_kernel<T><<<nt, kDenseThreads, qc_smem, rc.st>>>(D);
-  HB_TRY(cudaGetLastError());
-  const int cj = pick_cluster(nt, sg.kcap, rc.sms, 16);
-  const size_t j_smem = 16 + (size_t)sg.kcap * 12 + 64;
-  HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_smem, rc.st, D, 40));
-  finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D);
-  HB_TRY(cudaGetLastError());
+  HB_TIMED(KC_QRCP, qrcp_core_kernel<T><<<nt, kDenseThreads, qc_smem, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+  if (rc.sizes_known) {
+    // the cores' sizes are known: group the tasks by the cluster size that
+    // gives each warp about one pair per round, with exactly the shared memory
+    // the group's largest core needs (columns in distributed shared memory
+    // when they fit 16 CTAs; otherwise the sweeps run in global memory)
+    std::vector<TaskDims> dh(nt);
+    HB_TRY(cudaMemcpyAsync(dh.data(), ws + sg.dims_off, (size_t)nt * sizeof(TaskDims), cudaMemcpyDeviceToHost, rc.st));
+    HB_TRY(cudaStreamSynchronize(rc.st));
+    const size_t j_hdr = ((16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15) + kJSlotBytes;
+    std::vector<std::vector<int32_t>> groups(5);  // cluster 1, 2, 4, 8, 16
+    std::vector<size_t> need(5, 0);
+    const std::vector<SvdTask>& th = *sg.tasks_h;
+    for (int i = 0; i < nt; ++i) {
+      const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
+      const int nc = std::min(dh[i].kra, ncm), mr = ncm;
+      int g = 0;
+      while (g < 4 && (1 << (g + 1)) * kDenseThreads / 32 <= (nc + 1) / 2) ++g;
+      auto share = [&](int gg) { return (size_t)((nc + (1 << gg) - 1) >> gg) * (size_t)(mr + nc) * sizeof(T); };
+      while (g < 4 && share(g) + j_hdr > kJacobiSmemLimit) ++g;
+      groups[g].push_back(i);
+      const size_t sh = share(g) + j_hdr <= kJacobiSmemLimit ? share(g) : 0;
+      need[g] = std::max(need[g], sh);
+    }
+    size_t off = 0;
+    for (int g = 0; g < 5; ++g) {
+      if (groups[g].empty()) continue;
+      int32_t* lst = reinterpret_cast<int32_t*>(ws + p.jlist.off) + off;
+      HB_TRY(cudaMemcpyAsync(lst, groups[g].data(), groups[g].size() * 4, cudaMemcpyHostToDevice, rc.st));
+      const int cg_ = 1 << g;
+      HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, (int)groups[g].size() * cg_, cg_, j_hdr + need[g],
+                                                rc.st, D, 40, (int)j_hdr, (int64_t)need[g], (const int32_t*)lst)));
+      off += groups[g].size();
+    }
+  } else {
+    const int cj = pick_cluster(nt, sg.kcap, rc.sms, 16);
+    // header (flags, singular values, order, pair slots) then, up to the
+    // shared-memory limit, room for a task's columns of X and W (used when
+    // they fit)
+    const size_t j_hdr = ((16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15) + kJSlotBytes;
+    const size_t j_cap = ((size_t)sg.kcap + cj - 1) / cj * 2 * (size_t)sg.kcap * sizeof(T);
+    const size_t j_dsm = std::min(j_cap, (size_t)kJacobiSmemLimit - j_hdr);
+    HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, 40, (int)j_hdr,
+                                              (int64_t)j_dsm, (const int32_t*)nullptr)));
+  }
+  HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   rc.launches += 2;
   const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
   const size_t qa_smem = 3 * qa_cols * sizeof(T) + 64;
-  HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj));
+  HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj)));
   rc.launches += 5;
   if (sg.kind != TASK_LEAF) {
-    blockprod_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D);
-    HB_TRY(cudaGetLastError());
+    HB_TIMED(KC_BLOCKPROD, blockprod_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
     ++rc.launches;
   }
   return cudaSuccess;
@@ -203,12 +250,12 @@ cudaError_t run_stages(Plan& p, RunCtx& rc, std::string& err) {
   if (rc.ev[2] && (p.stages.empty() || p.stages.back().kind == TASK_LEAF)) HB_TRY(cudaEventRecord(rc.ev[2], rc.st));
   if (p.tape) {
     char* ws = rc.ws;
-    copyroot_kernel<T><<<dim3(64, p.nblocks), 256, 0, rc.st>>>(
-        reinterpret_cast<const BlockRef*>(ws + p.desc_region.off + p.refs_off),
-        reinterpret_cast<int32_t*>(ws + p.ranks_off), reinterpret_cast<const T*>(ws + p.full_u.off),
-        reinterpret_cast<const double*>(ws + p.full_s.off), reinterpret_cast<const T*>(ws + p.full_v.off),
-        p.root_tape_first, p.user_ref_first);
-    HB_TRY(cudaGetLastError());
+    HB_TIMED(KC_COPYROOT, copyroot_kernel<T><<<dim3(64, p.nblocks), 256, 0, rc.st>>>(
+                              reinterpret_cast<const BlockRef*>(ws + p.desc_region.off + p.refs_off),
+                              reinterpret_cast<int32_t*>(ws + p.ranks_off), reinterpret_cast<const T*>(ws + p.full_u.off),
+                              reinterpret_cast<const double*>(ws + p.full_s.off),
+                              reinterpret_cast<const T*>(ws + p.full_v.off), p.root_tape_first, p.user_ref_first);
+             HB_TRY(cudaGetLastError()));
     ++rc.launches;
   }
   return cudaSuccess;

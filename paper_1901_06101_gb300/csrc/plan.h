@@ -78,6 +78,7 @@ struct Plan {
   Region status, queue, uar, var, cscr, rscr, gscr, tape_int, tape_dbl;
   Region full_u, full_s, full_v, half_u, half_s, half_v;
   Region qr, tau, core, ord;
+  Region jlist;                   // task index lists of the Jacobi launches of one stage
   int64_t cscr_stride = 0, rscr_stride = 0, gscr_stride = 0;
   int max_clusters_scratch = 0;
   // global ref index of node (a, c) of block b: full store at level l, half store at level l

@@ -4,10 +4,45 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "plan.h"
 
 namespace hbaca {
+
+// Kernel classes timed under HBACA_FLAG_PROFILE (hbaca_kernel_times).
+enum KernelClass {
+  KC_BACA = 0, KC_PACK, KC_QR, KC_CORE, KC_QRCP, KC_JACOBI, KC_FINISH, KC_QAPPLY, KC_BLOCKPROD, KC_COPYROOT,
+  KC_COUNT
+};
+
+// Event pairs around every launch of a profiled call; events are created on
+// first use and reused by later calls of the same context.
+struct KernelTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, size_t>> marks;  // (class, index of the start event; the stop is next)
+  size_t used = 0;
+  void reset() { marks.clear(); used = 0; }
+  cudaError_t record(cudaStream_t st) {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      pool.push_back(e);
+    }
+    return cudaEventRecord(pool[used++], st);
+  }
+  cudaError_t begin(int cls, cudaStream_t st) {
+    marks.emplace_back(cls, used);
+    return record(st);
+  }
+  cudaError_t end(cudaStream_t st) { return record(st); }
+  ~KernelTimer() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct RunCtx {
   char* ws;
   cudaStream_t st;
@@ -15,6 +50,8 @@ struct RunCtx {
   const hbaca_result* res;
   int launches = 0;  // kernels launched by the call
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // profile: after BACA, after leaf stage, end
+  KernelTimer* kt = nullptr;                                   // profile: per-launch events
+  bool sizes_known = false;  // the call may synchronise between stages to size launches by the actual ranks
 };
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);

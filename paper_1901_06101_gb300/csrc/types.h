@@ -92,7 +92,8 @@ struct TaskDims {
   int32_t s;       // truncated rank
   int32_t sweeps;  // Jacobi sweeps run
   int32_t nout;    // singular triplets written to the output (s, or all of them when taped)
-  int32_t pad[2];
+  int32_t rotations;  // Jacobi rotations applied (all sweeps, all CTAs of the task)
+  int32_t pad;
 };
 
 struct QrJob {
