@@ -474,8 +474,8 @@ __device__ __forceinline__ void rotate_pair_t(T* a, T* b, int len, double cs, do
   }
 }
 
-// Inner products of a pair posted by its warp, and the rotation computed for
-// it by one lane of warp 0 (all pairs of a CTA's batch at once).
+// Inner products of a pair posted by its warp, turned into the pair's
+// rotation by one thread of the CTA.
 template <typename T>
 struct JPair {
   double al, be;
@@ -484,15 +484,15 @@ struct JPair {
   T sp, cp;
   int ok, pad;
 };
-constexpr int kJSlotBytes = 1024;  // room for 8 JPair<cplx>
+constexpr int kJSlotMax = 96;  // bytes reserved per pair slot (>= sizeof(JPair<cplx>))
 
 // The sweeps of one task.  kDsm: column j of X and of the accumulated rotation
 // W live in the shared memory of CTA j mod c of the cluster, slot j / c
 // ([X(0..mr-1), W(0..nc-1)], stride ldc); otherwise X and W are in global
-// memory (column j at M + j ld, Y + j ld).  A round's pairs are taken in
-// batches of one pair per warp of the cluster: the warps form their pairs'
-// inner products, one warp turns them into rotations (a lane per pair), then
-// every warp rotates its pair.
+// memory (column j at M + j ld, Y + j ld).  A round's pairs are dealt to the
+// warps of the cluster; each CTA (1) forms the inner products of all its
+// pairs, (2) turns them into rotations, one thread per pair, (3) rotates its
+// pairs' columns; one cluster barrier ends the round.
 template <typename T, bool kDsm>
 __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
                               T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
@@ -507,9 +507,15 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     else return Y + (int64_t)j * ld;
   };
   const int npairs = K / 2;
-  const int per_batch = c * nw;
-  const int nbatch = (npairs + per_batch - 1) / per_batch;
+  const int stride = c * nw;                             // pairs dealt per pass over the cluster's warps
+  const int per_warp = (npairs + stride - 1) / stride;   // passes (pairs per warp) per round
   const bool regs = mr <= 32 * kJacRegs;
+  auto pair_of = [&](int rd, int pi, int& a, int& b) {
+    // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
+    if (pi == 0) { a = rd; b = K - 1; }
+    else { a = (rd + pi) % (K - 1); b = (rd - pi + K - 1) % (K - 1); }
+    if (a > b) { int tmp = a; a = b; b = tmp; }
+  };
   unsigned fb = 0;
   for (; sweep < max_sweeps && K > 1; ++sweep) {
     const double tau2 = 0.01 * eps * eps * cmax;
@@ -517,36 +523,30 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; }
     __syncthreads();
     for (int rd = 0; rd < K - 1; ++rd) {
-      for (int bt = 0; bt < nbatch; ++bt) {
-        // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
-        const int pi = bt * per_batch + q * nw + warp;
+      // (1) inner products of this warp's pairs
+      for (int j = 0; j < per_warp; ++j) {
+        const int pi = j * stride + q * nw + warp;
         int a = 0, b = 0;
         bool act = pi < npairs;
         if (act) {
-          if (pi == 0) { a = rd; b = K - 1; }
-          else { a = (rd + pi) % (K - 1); b = (rd - pi + K - 1) % (K - 1); }
-          if (a > b) { int tmp = a; a = b; b = tmp; }
+          pair_of(rd, pi, a, b);
           act = b < nc;  // else a padding column
         }
-        T* ca = act ? colX(a) : nullptr;
-        T* cb = act ? colX(b) : nullptr;
-        T ra[kJacRegs], rb[kJacRegs];
         double al = 0.0, be = 0.0;
         T ga = Traits<T>::zero();
         if (act) {
+          const T* ca = colX(a);
+          const T* cb = colX(b);
           if (regs) {
 #pragma unroll
             for (int u = 0; u < kJacRegs; ++u) {
               const int i = lane + 32 * u;
-              ra[u] = i < mr ? jld<T, kDsm>(ca + i) : Traits<T>::zero();
-              rb[u] = i < mr ? jld<T, kDsm>(cb + i) : Traits<T>::zero();
-            }
-#pragma unroll
-            for (int u = 0; u < kJacRegs; ++u) {
               if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
-                al += abs2(ra[u]);
-                be += abs2(rb[u]);
-                ga = cmac(ga, ra[u], rb[u]);
+                const T xa = i < mr ? jld<T, kDsm>(ca + i) : Traits<T>::zero();
+                const T xb = i < mr ? jld<T, kDsm>(cb + i) : Traits<T>::zero();
+                al += abs2(xa);
+                be += abs2(xb);
+                ga = cmac(ga, xa, xb);
               }
             }
           } else {
@@ -563,48 +563,43 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
           wmax = fmax(wmax, fmax(al, be));
         }
         if (lane == 0) {
-          slots[warp].al = al;
-          slots[warp].be = be;
-          slots[warp].ga = ga;
-          slots[warp].ok = act ? 1 : 0;
+          JPair<T>& sl = slots[j * nw + warp];
+          sl.al = al;
+          sl.be = be;
+          sl.ga = ga;
+          sl.ok = act ? 1 : 0;
         }
-        __syncthreads();
-        if (warp == 0 && lane < nw) {
-          JPair<T>& sp = slots[lane];
-          if (sp.ok) {
-            double cs, sn;
-            T ph;
-            if (jacobi_rotation(sp.al, sp.be, sp.ga, tol, negl, fro2, cs, sn, ph)) {
-              sp.cs = cs;
-              sp.sn = sn;
-              sp.sp = scale(ph, sn);
-              sp.cp = scale(ph, cs);
-            } else {
-              sp.ok = 0;
-            }
-          }
+      }
+      __syncthreads();
+      // (2) rotations, one thread per pair
+      for (int sidx = tid; sidx < per_warp * nw; sidx += blockDim.x) {
+        JPair<T>& sl = slots[sidx];
+        if (!sl.ok) continue;
+        double cs, sn;
+        T ph;
+        if (jacobi_rotation(sl.al, sl.be, sl.ga, tol, negl, fro2, cs, sn, ph)) {
+          sl.cs = cs;
+          sl.sn = sn;
+          sl.sp = scale(ph, sn);
+          sl.cp = scale(ph, cs);
+        } else {
+          sl.ok = 0;
         }
-        __syncthreads();
-        if (act && slots[warp].ok) {
-          const double cs = slots[warp].cs, sn = slots[warp].sn;
-          const T spv = slots[warp].sp, cpv = slots[warp].cp;
-          if (lane == 0 && fmax(al, be) >= tau2) flag[fb & 1] = 1;
-          ++nrot;
-          if (regs) {
-#pragma unroll
-            for (int u = 0; u < kJacRegs; ++u) {
-              const int i = lane + 32 * u;
-              if (i < mr) {
-                rot_elem(ra[u], rb[u], cs, sn, spv, cpv);
-                ca[i] = ra[u];
-                cb[i] = rb[u];
-              }
-            }
-          } else {
-            rotate_pair_t<T, kDsm>(ca, cb, mr, cs, sn, spv, cpv, lane);
-          }
-          rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
-        }
+      }
+      __syncthreads();
+      // (3) rotate this warp's pairs
+      for (int j = 0; j < per_warp; ++j) {
+        const JPair<T>& sl = slots[j * nw + warp];
+        if (!sl.ok) continue;  // warp-uniform
+        const int pi = j * stride + q * nw + warp;
+        int a, b;
+        pair_of(rd, pi, a, b);
+        const double cs = sl.cs, sn = sl.sn;
+        const T spv = sl.sp, cpv = sl.cp;
+        if (lane == 0 && fmax(sl.al, sl.be) >= tau2) flag[fb & 1] = 1;
+        ++nrot;
+        rotate_pair_t<T, kDsm>(colX(a), colX(b), mr, cs, sn, spv, cpv, lane);
+        rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
       }
       __syncthreads();
       cl.sync();
@@ -629,7 +624,7 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
 
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DenseParams<T> P, int max_sweeps,
-                                                                   int hdr_bytes, int64_t dsm_bytes,
+                                                                   int hdr_bytes, int slot_off, int64_t dsm_bytes,
                                                                    const int32_t* task_list) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
@@ -705,7 +700,7 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   int nrot = 0;  // rotations applied by this warp
   if (tid == 0) { flag[0] = 0; flag[1] = 0; }
   cl.sync();
-  JPair<T>* slots = reinterpret_cast<JPair<T>*>(smem_raw + hdr_bytes - kJSlotBytes);
+  JPair<T>* slots = reinterpret_cast<JPair<T>*>(smem_raw + slot_off);
   if (use_dsm)
     jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
                            slots, sweep, nrot);

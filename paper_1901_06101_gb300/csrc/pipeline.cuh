@@ -188,7 +188,13 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
     std::vector<TaskDims> dh(nt);
     HB_TRY(cudaMemcpyAsync(dh.data(), ws + sg.dims_off, (size_t)nt * sizeof(TaskDims), cudaMemcpyDeviceToHost, rc.st));
     HB_TRY(cudaStreamSynchronize(rc.st));
-    const size_t j_hdr = ((16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15) + kJSlotBytes;
+    const size_t j_base = (16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15;
+    // pair slots: (pairs of a round per CTA, rounded up to whole passes over its warps)
+    auto j_hdr_of = [&](int cc) {
+      const size_t pairs = ((size_t)sg.kcap + 1) / 2;
+      const size_t per_cta = (pairs + (size_t)cc * 8 - 1) / ((size_t)cc * 8) * 8;
+      return j_base + per_cta * kJSlotMax;
+    };
     std::vector<std::vector<int32_t>> groups(5);  // cluster 1, 2, 4, 8, 16
     std::vector<size_t> need(5, 0);
     const std::vector<SvdTask>& th = *sg.tasks_h;
@@ -198,9 +204,9 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
       int g = 0;
       while (g < 4 && (1 << (g + 1)) * kDenseThreads / 32 <= (nc + 1) / 2) ++g;
       auto share = [&](int gg) { return (size_t)((nc + (1 << gg) - 1) >> gg) * (size_t)(mr + nc) * sizeof(T); };
-      while (g < 4 && share(g) + j_hdr > kJacobiSmemLimit) ++g;
+      while (g < 4 && share(g) + j_hdr_of(1 << g) > kJacobiSmemLimit) ++g;
       groups[g].push_back(i);
-      const size_t sh = share(g) + j_hdr <= kJacobiSmemLimit ? share(g) : 0;
+      const size_t sh = share(g) + j_hdr_of(1 << g) <= kJacobiSmemLimit ? share(g) : 0;
       need[g] = std::max(need[g], sh);
     }
     size_t off = 0;
@@ -209,8 +215,10 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
       int32_t* lst = reinterpret_cast<int32_t*>(ws + p.jlist.off) + off;
       HB_TRY(cudaMemcpyAsync(lst, groups[g].data(), groups[g].size() * 4, cudaMemcpyHostToDevice, rc.st));
       const int cg_ = 1 << g;
+      const size_t j_hdr = j_hdr_of(cg_);
       HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, (int)groups[g].size() * cg_, cg_, j_hdr + need[g],
-                                                rc.st, D, 40, (int)j_hdr, (int64_t)need[g], (const int32_t*)lst)));
+                                                rc.st, D, 40, (int)j_hdr, (int)j_base, (int64_t)need[g],
+                                                (const int32_t*)lst)));
       off += groups[g].size();
     }
   } else {
@@ -218,11 +226,12 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
     // header (flags, singular values, order, pair slots) then, up to the
     // shared-memory limit, room for a task's columns of X and W (used when
     // they fit)
-    const size_t j_hdr = ((16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15) + kJSlotBytes;
+    const size_t j_base = (16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15;
+    const size_t j_hdr = j_base + (((size_t)sg.kcap + 1) / 2 + (size_t)cj * 8 - 1) / ((size_t)cj * 8) * 8 * kJSlotMax;
     const size_t j_cap = ((size_t)sg.kcap + cj - 1) / cj * 2 * (size_t)sg.kcap * sizeof(T);
     const size_t j_dsm = std::min(j_cap, (size_t)kJacobiSmemLimit - j_hdr);
     HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, 40, (int)j_hdr,
-                                              (int64_t)j_dsm, (const int32_t*)nullptr)));
+                                              (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr)));
   }
   HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   rc.launches += 2;
