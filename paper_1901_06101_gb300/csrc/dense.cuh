@@ -226,20 +226,42 @@ __global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> 
     __syncthreads();
     const T ctau = coef[0], sc = coef[1];
     const T csc = conj_(sc);
-    // w_l = a_jl + conj(sc) dot_l ; A(i, l) -= conj(tau) * (x_i sc) * w_l ; head row: A(j, l) -= conj(tau) w_l
-    for (int l = 1; l < ncol; ++l) {
+    // w_l = a_jl + conj(sc) dot_l ; f_l = conj(tau) w_l (into the dot slots)
+    for (int l = 1 + tid; l < ncol; l += blockDim.x) {
       const T w = mac(tot[2 + t.kcap + (l - 1)], csc, tot[2 + (l - 1)]);
-      const T f = mul(ctau, w);
-      T* coll = A + (int64_t)(j + l) * lda;
-      const T* colj = A + (int64_t)j * lda;
-      for (int i = i0 + tid; i < rb; i += blockDim.x) coll[i] = msub(coll[i], mul(colj[i], sc), f);
-      if (tid == 0 && j >= ra && j < rb) coll[j] = sub(coll[j], f);
+      tot[2 + (l - 1)] = mul(ctau, w);
     }
     __syncthreads();
+    // A(i, l) -= (x_i sc) f_l: one thread per row, four trailing columns per
+    // step so that their loads are in flight together; the tail of column j
+    // becomes the reflector x sc
     {
+      const T* fv = tot + 1;  // f_l at fv[l]
       T* colj = A + (int64_t)j * lda;
-      for (int i = i0 + tid; i < rb; i += blockDim.x) colj[i] = mul(colj[i], sc);
-      if (tid == 0 && j >= ra && j < rb) colj[j] = coef[2];
+      for (int i = i0 + tid; i < rb; i += blockDim.x) {
+        const T xi = mul(colj[i], sc);
+        int l = 1;
+        for (; l + 3 < ncol; l += 4) {
+          T* c0 = A + (int64_t)(j + l) * lda + i;
+          const T v0 = c0[0], v1 = c0[lda], v2 = c0[2 * lda], v3 = c0[3 * lda];
+          c0[0] = msub(v0, xi, fv[l]);
+          c0[lda] = msub(v1, xi, fv[l + 1]);
+          c0[2 * lda] = msub(v2, xi, fv[l + 2]);
+          c0[3 * lda] = msub(v3, xi, fv[l + 3]);
+        }
+        for (; l < ncol; ++l) {
+          T* c0 = A + (int64_t)(j + l) * lda + i;
+          *c0 = msub(*c0, xi, fv[l]);
+        }
+        colj[i] = xi;
+      }
+      if (j >= ra && j < rb) {  // head row: A(j, l) -= f_l
+        for (int l = 1 + tid; l < ncol; l += blockDim.x) {
+          T* h = A + (int64_t)(j + l) * lda + j;
+          *h = sub(*h, fv[l]);
+        }
+        if (tid == 0) colj[j] = coef[2];
+      }
     }
     __syncthreads();
   }
@@ -875,11 +897,21 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
       wv[tc] = mul(tj, sum);
     }
     __syncthreads();
-    for (int tc = 0; tc < s; ++tc) {
-      const T f = wv[tc];
-      for (int i = i0 + tid; i < rb; i += blockDim.x) {
-        const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];
-        D[(int64_t)tc * ldd + i] = msub(D[(int64_t)tc * ldd + i], u, f);
+    // D(i, tc) -= u_i wv_tc: one thread per row, four columns per step
+    for (int i = i0 + tid; i < rb; i += blockDim.x) {
+      const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];
+      int tc = 0;
+      for (; tc + 3 < s; tc += 4) {
+        T* d0 = D + (int64_t)tc * ldd + i;
+        const T v0 = d0[0], v1 = d0[ldd], v2 = d0[2 * ldd], v3 = d0[3 * ldd];
+        d0[0] = msub(v0, u, wv[tc]);
+        d0[ldd] = msub(v1, u, wv[tc + 1]);
+        d0[2 * ldd] = msub(v2, u, wv[tc + 2]);
+        d0[3 * ldd] = msub(v3, u, wv[tc + 3]);
+      }
+      for (; tc < s; ++tc) {
+        T* d0 = D + (int64_t)tc * ldd + i;
+        *d0 = msub(*d0, u, wv[tc]);
       }
     }
     __syncthreads();
