@@ -79,9 +79,9 @@ struct GenRowsTask {
 
 // One reverse BACA iteration of one leaf: from R_k (dI x n, row-major), the
 // block J_k, the LRID positions jbar (first dk kept) and Zbar = Vbar_k R_k^T
-// (dk x dI, column-major), form W = R_k(:, J_k(jbar)), its pseudo-inverse
-// Z = W^+ (dk x dI, column-major, written), the adjoint
-//   Wbar = (I - W Z) Zbar^T (W^T W)^-1 - Z^T Zbar Z^T,
+// (dk x dI, column-major), form W = R_k(:, J_k(jbar)) = Q T, its
+// pseudo-inverse Z = W^+ = T^-1 Q^T (dk x dI, column-major, written), the adjoint
+//   Wbar = (I - Q Q^T) Zbar^T (W^T W)^-1 - Z^T Zbar Z^T,
 // added to Acols at rows I_k of columns r0 .. r0+dk-1, and slotcol[r0 + t] =
 // J_k(jbar(t)).
 struct LeafStepTask {
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(32) leafstep_kernel(const LeafStepTask* tasks)
   const int dI = T.dI, dk = T.dk;
   double* W0 = lsm;                   // W (dI x dk); later ZZ = Zbar Z^T (dk x dk)
   double* Hq = W0 + kMaxD * kLd;      // Householder work, then Q (dI x dk); later F2 (dI x dk)
-  double* Tm = Hq + kMaxD * kLd;      // R, then T^-1; later ZF = Z Zbar^T (dk x dk)
+  double* Tm = Hq + kMaxD * kLd;      // R, then T^-1; later Q^T Zbar^T (dk x dk)
   double* Zs = Tm + kMaxD * kLd;      // Z (dk x dI)
   double* Zb = Zs + kMaxD * kLd;      // Zbar (dk x dI)
   double* F1 = Zb + kMaxD * kLd;      // scratch, then G (dk x dk)
@@ -376,24 +376,32 @@ __global__ void __launch_bounds__(32) leafstep_kernel(const LeafStepTask* tasks)
       F1[lane * kLd + a] = v;
     }
   __syncwarp();
-  // ZF(a, b) = sum_i Z(a, i) Zbar(b, i), lane = b, into Tm
-  if (lane < dk)
-    for (int a = 0; a < dk; ++a) {
-      double v = 0.0;
-      for (int i = 0; i < dI; ++i) v = fma(Zs[i * kLd + a], Zb[i * kLd + lane], v);
-      F3[lane * kLd + a] = v;
-    }
-  __syncwarp();
-  for (int c = 0; c < dk; ++c)
-    if (lane < dk) Tm[c * kLd + lane] = F3[c * kLd + lane];
-  __syncwarp();
-  // F2(i, b) = Zbar(b, i) - sum_a W(i, a) ZF(a, b), lane = i, into Hq
-  if (lane < dI)
-    for (int b = 0; b < dk; ++b) {
-      double v = Zb[lane * kLd + b];
-      for (int a = 0; a < dk; ++a) v -= W0[a * kLd + lane] * Tm[b * kLd + a];
-      F3[b * kLd + lane] = v;
-    }
+  // F2 = (I - W W^+) Zbar^T = (I - Q Q^T) Zbar^T (dI x dk), into Hq.  The
+  // projector is formed from the orthonormal Q (not as I - W Z, whose
+  // rounding error ~ cond(W) eps would be amplified by (W^T W)^-1); for a
+  // square W it is exactly zero.
+  if (dI > dk) {
+    // QZ(a, b) = sum_i Q(i, a) Zbar(b, i), lane = b, into Tm
+    if (lane < dk)
+      for (int a = 0; a < dk; ++a) {
+        double v = 0.0;
+        for (int i = 0; i < dI; ++i) v = fma(Hq[a * kLd + i], Zb[i * kLd + lane], v);
+        F3[lane * kLd + a] = v;
+      }
+    __syncwarp();
+    for (int c = 0; c < dk; ++c)
+      if (lane < dk) Tm[c * kLd + lane] = F3[c * kLd + lane];
+    __syncwarp();
+    // F2(i, b) = Zbar(b, i) - sum_a Q(i, a) QZ(a, b), lane = i
+    if (lane < dI)
+      for (int b = 0; b < dk; ++b) {
+        double v = Zb[lane * kLd + b];
+        for (int a = 0; a < dk; ++a) v -= Hq[a * kLd + lane] * Tm[b * kLd + a];
+        F3[b * kLd + lane] = v;
+      }
+  } else {
+    for (int b = 0; b < dk; ++b) F3[b * kLd + lane] = 0.0;
+  }
   __syncwarp();
   for (int c = 0; c < dk; ++c) Hq[c * kLd + lane] = F3[c * kLd + lane];
   __syncwarp();
