@@ -105,6 +105,15 @@ typedef struct hbaca_gen {
                                   only the eps-rank kept ones), for hbaca_apply_backward.
                                   The kept results are the same as without the flag; the
                                   workspace is larger (no store is reused across levels) */
+#define HBACA_FLAG_GRAPH 8u    /* capture the call into a CUDA graph and replay it: the first
+                                  call with a given plan, caller buffers, workspace and
+                                  options runs normally (sizing its launches by the actual
+                                  ranks) and then captures itself; later identical calls on
+                                  the same context only launch the graph (one graph is kept
+                                  per context).  The workspace must not be used by other
+                                  calls between replays.  New data in the same buffers is
+                                  allowed: results are exact, only the launch shapes were
+                                  chosen for the first call's ranks. */
 
 /* Options of one compression (Alg. 3 inputs n_b, d, eps). */
 typedef struct hbaca_opts {
@@ -220,6 +229,18 @@ hbaca_status hbaca_apply_backward(hbaca_ctx* ctx, const hbaca_gen* gen, const hb
                                   const void* workspace, const void* X, int64_t nrhs, int64_t ldx, const void* dY,
                                   int64_t lddy, double* d_h, double* d_x, double* d_y, void* dX, int64_t lddx,
                                   void* bwd_workspace, size_t bwd_bytes, void* stream);
+
+/* Autotuner of the batched (or single, nblocks = 1) call: times the
+   persistent leaf BACA launch (Alg. 2 over all leaves) with clusters of 1, 2,
+   4, 8 and 16 CTAs per leaf (every size whose plan fits `workspace_bytes`)
+   and returns the fastest in *best_cluster and its device time in *best_ms.
+   The cluster size does not change any result (every CTA of a cluster takes
+   the same pivot decisions); set opts.cluster to the returned value.  Uses
+   `workspace` as scratch and synchronises `stream`.  No counterpart in the
+   paper. */
+hbaca_status hbaca_autotune_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                    void* workspace, size_t workspace_bytes, void* stream, int32_t* best_cluster,
+                                    double* best_ms);
 
 /* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
    by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index

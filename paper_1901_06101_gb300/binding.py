@@ -17,6 +17,7 @@ F64, C128 = 0, 1
 FLAG_ASYNC = 1
 FLAG_PROFILE = 2
 FLAG_TAPE = 4
+FLAG_GRAPH = 8
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
           5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE"}
 STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}
@@ -78,6 +79,9 @@ SIGNATURES = [
                                              ctypes.c_int64, ctypes.POINTER(LeafTrace), ctypes.c_void_p]),
     ("hbaca_debug_backward_json", ctypes.c_int64, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                                    ctypes.c_int64, ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("hbaca_autotune_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Gen), ctypes.POINTER(Opts),
+                                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int32)]),
     ("hbaca_apply_workspace_size", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
@@ -470,6 +474,20 @@ class Batch:
                                            self.res, ctypes.c_void_p(self.ws.data_ptr()),
                                            ctypes.c_void_p(stream)))
         return self
+
+    def autotune(self, stream=None):
+        """hbaca_autotune_batched on this batch's workspace: sets opts.cluster
+        to the fastest leaf cluster size and returns (cluster, ms)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        c = ctypes.c_int32(0)
+        ms = ctypes.c_double(0.0)
+        check(lib().hbaca_autotune_batched(self.ctx.ptr, len(self.specs), self.gens, ctypes.byref(self.opts),
+                                           ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                           ctypes.c_void_p(stream), ctypes.byref(c), ctypes.byref(ms)))
+        self.opts.cluster = c.value
+        return c.value, ms.value
 
     def ranks(self):
         return [int(self.res[i].rank) for i in range(len(self.specs))]

@@ -20,6 +20,12 @@ struct hbaca_ctx {
   bool have_times;
   int launches;
   hbaca::KernelTimer kt;
+  // HBACA_FLAG_GRAPH: the last captured call, its plan and what identifies it
+  // (the raw call arguments)
+  cudaGraphExec_t gexec;
+  std::vector<char> gkey;
+  hbaca::Plan gplan;
+  cudaStream_t cap_stream;  // captures run on this stream (the legacy default stream cannot be captured)
 };
 
 namespace {
@@ -76,7 +82,7 @@ hbaca_status hbaca_create(hbaca_ctx** ctx) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (major * 10 + minor != 103)
     return fail(HBACA_CUDA, "libhbaca is built for sm_103a (GB300); device is sm_" + std::to_string(major * 10 + minor));
-  *ctx = new (std::nothrow) hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0, {}};
+  *ctx = new (std::nothrow) hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0, {}, nullptr, {}, {}, nullptr};
   if (!*ctx) return fail(HBACA_INVALID_ARG, "out of host memory");
   for (int i = 0; i < 4; ++i) {
     e = cudaEventCreate(&(*ctx)->ev[i]);
@@ -87,9 +93,12 @@ hbaca_status hbaca_create(hbaca_ctx** ctx) {
 }
 
 hbaca_status hbaca_destroy(hbaca_ctx* ctx) {
-  if (ctx)
+  if (ctx) {
     for (int i = 0; i < 4; ++i)
       if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  }
   delete ctx;
   return HBACA_OK;
 }
@@ -116,40 +125,110 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
     if (outs[b].ldu < gens[b].m || outs[b].ldv < gens[b].n)
       return fail(HBACA_INVALID_ARG, "result needs ldu >= m and ldv >= n");
   }
-  hbaca::Plan p;
-  std::string err;
-  if (!hbaca::make_plan(gens, nblocks, *opts, ctx->sms, p, err)) return fail(HBACA_INVALID_ARG, err);
-  for (int b = 0; b < nblocks; ++b) hbaca::bind_user_result(p, b, outs[b]);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
-  hbaca::RunCtx rc{ws, st, ctx->sms, &outs[0], 0};
-  rc.sizes_known = (opts->flags & HBACA_FLAG_ASYNC) == 0;
-  const bool prof = (opts->flags & HBACA_FLAG_PROFILE) != 0;
+  const bool graph = (opts->flags & HBACA_FLAG_GRAPH) != 0;
+  std::vector<char> key;
+  if (graph) {  // a captured call is identified by its raw arguments
+    auto add = [&](const void* ptr, size_t bytes) {
+      const char* c = reinterpret_cast<const char*>(ptr);
+      key.insert(key.end(), c, c + bytes);
+    };
+    add(&nblocks, sizeof(nblocks));
+    add(gens, sizeof(hbaca_gen) * (size_t)nblocks);
+    add(opts, sizeof(hbaca_opts));
+    for (int b = 0; b < nblocks; ++b) {
+      add(&outs[b].U, sizeof(void*));
+      add(&outs[b].ldu, sizeof(int64_t));
+      add(&outs[b].S, sizeof(void*));
+      add(&outs[b].V, sizeof(void*));
+      add(&outs[b].ldv, sizeof(int64_t));
+    }
+    add(&workspace, sizeof(workspace));
+  }
+  const bool replay = graph && ctx->gexec && key == ctx->gkey;
+  hbaca::Plan fresh;
+  std::string err;
+  if (!replay) {
+    if (!hbaca::make_plan(gens, nblocks, *opts, ctx->sms, fresh, err)) return fail(HBACA_INVALID_ARG, err);
+    for (int b = 0; b < nblocks; ++b) hbaca::bind_user_result(fresh, b, outs[b]);
+  }
+  hbaca::Plan& p = replay ? ctx->gplan : fresh;
+  cudaError_t e = cudaSuccess;
   ctx->have_times = false;
-  if (prof) {
-    for (int i = 0; i < 4; ++i) rc.ev[i] = ctx->ev[i];
-    ctx->kt.reset();
-    rc.kt = &ctx->kt;
-    cudaError_t pe = cudaEventRecord(ctx->ev[0], st);
-    if (pe != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(pe));
-  }
-  // status word and leaf work counter live in separate 256-byte regions
-  cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.desc_region.off, p.desc.data(), p.desc.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.ranks_off, 0, (size_t)p.nslots * 4, st);
-  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("workspace set-up: ") + cudaGetErrorString(e));
-  e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
-  if (e != cudaSuccess) return fail(HBACA_CUDA, err.empty() ? cudaGetErrorString(e) : err);
-  ctx->launches = rc.launches;
-  if (p.tape) {  // mark the workspace as holding a complete tape of this call
-    e = cudaMemsetAsync(ws + p.status.off + kTapeMarkOffset, kTapeMarkByte, 4, st);
-    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("tape mark: ") + cudaGetErrorString(e));
-  }
-  if (prof) {
-    e = cudaEventRecord(ctx->ev[3], st);
-    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
-    ctx->have_times = true;
+  if (replay) {
+    e = cudaGraphLaunch(ctx->gexec, st);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    ctx->launches = 0;
+  } else {
+    hbaca::RunCtx rc{ws, st, ctx->sms, &outs[0], 0};
+    rc.sizes_known = (opts->flags & HBACA_FLAG_ASYNC) == 0;
+    std::vector<hbaca::JacobiLaunch> recipe;
+    if (graph) rc.record = &recipe;
+    const bool prof = (opts->flags & HBACA_FLAG_PROFILE) != 0 && !graph;
+    if (prof) {
+      for (int i = 0; i < 4; ++i) rc.ev[i] = ctx->ev[i];
+      ctx->kt.reset();
+      rc.kt = &ctx->kt;
+      cudaError_t pe = cudaEventRecord(ctx->ev[0], st);
+      if (pe != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(pe));
+    }
+    // status word and leaf work counter live in separate 256-byte regions
+    auto reset = [&](cudaStream_t sx) {
+      cudaError_t r = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, sx);
+      if (r == cudaSuccess) r = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, sx);
+      if (r == cudaSuccess) r = cudaMemsetAsync(ws + p.ranks_off, 0, (size_t)p.nslots * 4, sx);
+      return r;
+    };
+    e = reset(st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.desc_region.off, p.desc.data(), p.desc.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("workspace set-up: ") + cudaGetErrorString(e));
+    e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, err.empty() ? cudaGetErrorString(e) : err);
+    ctx->launches = rc.launches;
+    if (p.tape) {  // mark the workspace as holding a complete tape of this call
+      e = cudaMemsetAsync(ws + p.status.off + kTapeMarkOffset, kTapeMarkByte, 4, st);
+      if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("tape mark: ") + cudaGetErrorString(e));
+    }
+    if (prof) {
+      e = cudaEventRecord(ctx->ev[3], st);
+      if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+      ctx->have_times = true;
+    }
+    if (graph) {
+      // capture the same call with the recorded launch shapes: resets, the
+      // persistent leaf kernel, every stage; no host synchronisation inside
+      if (!ctx->cap_stream) {
+        e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("capture stream: ") + cudaGetErrorString(e));
+      }
+      cudaStream_t cs = ctx->cap_stream;
+      hbaca::RunCtx rg{ws, cs, ctx->sms, &outs[0], 0};
+      rg.replay = &recipe;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        std::string gerr;
+        cudaError_t ce = reset(cs);
+        if (ce == cudaSuccess) ce = p.cplx ? hbaca::run_c128(p, rg, gerr) : hbaca::run_f64(p, rg, gerr);
+        if (ce == cudaSuccess && p.tape) ce = cudaMemsetAsync(ws + p.status.off + kTapeMarkOffset, kTapeMarkByte, 4, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (ce != cudaSuccess) e = ce;
+      }
+      cudaGraphExec_t ex = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HBACA_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      }
+      if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = ex;
+      ctx->gkey.swap(key);
+      ctx->gplan = fresh;  // a copy: this call still reads its ranks through `p`
+      // the stages' host task tables point into the plan's own storage
+      for (size_t i = 0; i < ctx->gplan.stages.size(); ++i) ctx->gplan.stages[i].tasks_h = &ctx->gplan.task_storage[i];
+    }
   }
   const int32_t* d_ranks = reinterpret_cast<const int32_t*>(ws + p.ranks_off) + p.user_ref_first;
   for (int b = 0; b < nblocks; ++b) {
@@ -190,6 +269,61 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
                                                  : "device-side failure";
     return fail(hs, what);
   }
+  tls_err.clear();
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_autotune_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                    void* workspace, size_t workspace_bytes, void* stream, int32_t* best_cluster,
+                                    double* best_ms) {
+  if (!ctx || !gens || !opts || !workspace || !best_cluster || nblocks < 1) return fail(HBACA_INVALID_ARG, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return fail(HBACA_WORKSPACE, "workspace must be 256-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* ws = reinterpret_cast<char*>(workspace);
+  cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1];
+  int best = 0;
+  double bms = 0.0;
+  std::string last;
+  for (int c = 1; c <= 16; c *= 2) {
+    hbaca_opts o = *opts;
+    o.cluster = c;
+    o.flags &= ~(HBACA_FLAG_GRAPH | HBACA_FLAG_PROFILE);
+    hbaca::Plan p;
+    std::string err;
+    if (!hbaca::make_plan(gens, nblocks, o, ctx->sms, p, err) || p.total > workspace_bytes) {
+      last = err.empty() ? "workspace too small for cluster " + std::to_string(c) : err;
+      continue;
+    }
+    double ms = -1.0;
+    for (int rep = 0; rep < 2; ++rep) {  // the second run is timed (the first warms up)
+      hbaca::RunCtx rc{ws, st, ctx->sms, nullptr, 0};
+      rc.baca_only = true;
+      cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ws + p.desc_region.off, p.desc.data(), p.desc.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = p.cplx ? hbaca::run_c128(p, rc, err) : hbaca::run_f64(p, rc, err);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        last = err.empty() ? cudaGetErrorString(e) : err;
+        ms = -1.0;
+        break;
+      }
+      ms = t;
+    }
+    if (ms >= 0.0 && (best == 0 || ms < bms)) {
+      best = c;
+      bms = ms;
+    }
+  }
+  if (best == 0) return fail(HBACA_INVALID_ARG, "no cluster size could run: " + last);
+  *best_cluster = best;
+  if (best_ms) *best_ms = bms;
+  ctx->have_times = false;
   tls_err.clear();
   return HBACA_OK;
 }

@@ -28,6 +28,7 @@ cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err) {
       return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  if (rc.baca_only) return cudaSuccess;
   return run_stages<cplx>(p, rc, err);
 }
 

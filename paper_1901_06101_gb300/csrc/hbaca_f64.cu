@@ -33,6 +33,7 @@ cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err) {
       return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  if (rc.baca_only) return cudaSuccess;
   return run_stages<double>(p, rc, err);
 }
 

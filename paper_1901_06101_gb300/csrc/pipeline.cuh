@@ -121,7 +121,7 @@ cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
 }
 
 template <typename T>
-cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
+cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string& err) {
   char* ws = rc.ws;
   char* desc = ws + p.desc_region.off;
   DenseParams<T> D;
@@ -180,7 +180,16 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
   const size_t qc_smem = (size_t)sg.kcap * 9 + 2 * sizeof(T) + 32 * 12 + 64 + 16;
   HB_TRY(cudaFuncSetAttribute(qrcp_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qc_smem));
   HB_TIMED(KC_QRCP, qrcp_core_kernel<T><<<nt, kDenseThreads, qc_smem, rc.st>>>(D); HB_TRY(cudaGetLastError()));
-  if (rc.sizes_known) {
+  if (rc.replay) {
+    // captured call: the launch shapes a synchronous call chose (task lists
+    // already in the workspace); kernels still check every task's sizes
+    for (const JacobiLaunch& jl : *rc.replay) {
+      if (jl.stage != si) continue;
+      const int32_t* lst = reinterpret_cast<const int32_t*>(ws + p.jlist.off) + jl.list_off;
+      HB_TRY(launch_cluster(jacobi_kernel<T>, jl.count * jl.cluster, jl.cluster, jl.hdr + jl.dsm, rc.st, D, 40,
+                            (int)jl.hdr, (int)jl.base, (int64_t)jl.dsm, lst));
+    }
+  } else if (rc.sizes_known) {
     // the cores' sizes are known: group the tasks by the cluster size that
     // gives each warp about one pair per round, with exactly the shared memory
     // the group's largest core needs (columns in distributed shared memory
@@ -209,7 +218,7 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
       const size_t sh = share(g) + j_hdr_of(1 << g) <= kJacobiSmemLimit ? share(g) : 0;
       need[g] = std::max(need[g], sh);
     }
-    size_t off = 0;
+    size_t off = sg.jlist_off;
     for (int g = 0; g < 5; ++g) {
       if (groups[g].empty()) continue;
       int32_t* lst = reinterpret_cast<int32_t*>(ws + p.jlist.off) + off;
@@ -219,6 +228,7 @@ cudaError_t run_stage(Plan& p, const Stage& sg, RunCtx& rc, std::string& err) {
       HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, (int)groups[g].size() * cg_, cg_, j_hdr + need[g],
                                                 rc.st, D, 40, (int)j_hdr, (int)j_base, (int64_t)need[g],
                                                 (const int32_t*)lst)));
+      if (rc.record) rc.record->push_back(JacobiLaunch{si, cg_, (int)groups[g].size(), j_hdr, j_base, need[g], off});
       off += groups[g].size();
     }
   } else {
@@ -253,7 +263,7 @@ cudaError_t run_stages(Plan& p, RunCtx& rc, std::string& err) {
     const Stage& sg = p.stages[i];
     if (rc.ev[2] && sg.kind != TASK_LEAF && (i == 0 || p.stages[i - 1].kind == TASK_LEAF))
       HB_TRY(cudaEventRecord(rc.ev[2], rc.st));  // leaf re-compression done
-    cudaError_t e = run_stage<T>(p, sg, rc, err);
+    cudaError_t e = run_stage<T>(p, (int)i, sg, rc, err);
     if (e != cudaSuccess) return e;
   }
   if (rc.ev[2] && (p.stages.empty() || p.stages.back().kind == TASK_LEAF)) HB_TRY(cudaEventRecord(rc.ev[2], rc.st));

@@ -485,9 +485,12 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
   p.core = Lo.take(core_elems * p.esz);
   p.ord = Lo.take(ord_elems * 4);
   {
-    size_t mx = 1;
-    for (const Stage& st : p.stages) mx = std::max<size_t>(mx, (size_t)st.ntasks);
-    p.jlist = Lo.take(mx * 4);
+    size_t tot = 1;
+    for (Stage& st : p.stages) {
+      st.jlist_off = tot - 1;
+      tot += (size_t)st.ntasks;
+    }
+    p.jlist = Lo.take(tot * 4);
   }
   p.total = Lo.cur;
   return true;

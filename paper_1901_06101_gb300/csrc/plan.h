@@ -41,6 +41,7 @@ struct Stage {
   int kcap = 0;
   int rows_max = 0;
   int in_store = -1, out_store = -1;  // block-store arenas: 0 = full, 1 = half
+  size_t jlist_off = 0;                // element offset of this stage's Jacobi task lists in jlist
 };
 
 struct Plan {
@@ -78,7 +79,7 @@ struct Plan {
   Region status, queue, uar, var, cscr, rscr, gscr, tape_int, tape_dbl;
   Region full_u, full_s, full_v, half_u, half_s, half_v;
   Region qr, tau, core, ord;
-  Region jlist;                   // task index lists of the Jacobi launches of one stage
+  Region jlist;                   // task index lists of the Jacobi launches (one slot per stage)
   int64_t cscr_stride = 0, rscr_stride = 0, gscr_stride = 0;
   int max_clusters_scratch = 0;
   // global ref index of node (a, c) of block b: full store at level l, half store at level l

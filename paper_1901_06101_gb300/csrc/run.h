@@ -43,6 +43,13 @@ struct KernelTimer {
   }
 };
 
+// Launch shape of one Jacobi launch of a stage, as sized by a synchronous call
+// (replayed when the call is captured into a CUDA graph).
+struct JacobiLaunch {
+  int stage, cluster, count;
+  size_t hdr, base, dsm, list_off;
+};
+
 struct RunCtx {
   char* ws;
   cudaStream_t st;
@@ -52,6 +59,9 @@ struct RunCtx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // profile: after BACA, after leaf stage, end
   KernelTimer* kt = nullptr;                                   // profile: per-launch events
   bool sizes_known = false;  // the call may synchronise between stages to size launches by the actual ranks
+  std::vector<JacobiLaunch>* record = nullptr;       // sized launches are appended here
+  const std::vector<JacobiLaunch>* replay = nullptr;  // capture: launch these shapes, no host sync
+  bool baca_only = false;                             // autotuning: the leaf BACA launch alone
 };
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);

@@ -114,3 +114,52 @@ def test_batched_rejects_mixed_kinds(ctx):
     opts = B.make_opts(1e-8, 8, 0)
     with pytest.raises(B.HbacaError):
         B.compress_batched(ctx, specs, opts)
+
+
+def _same_results(a, b):
+    for ra, rb in zip(a.results(), b.results()):
+        assert ra.rank == rb.rank
+        assert torch.equal(ra.S, rb.S) and torch.equal(ra.U, rb.U) and torch.equal(ra.V, rb.V)
+
+
+def test_graph_replay_bit_identical_and_follows_new_data(ctx):
+    """HBACA_FLAG_GRAPH: the first call runs and captures itself, later calls
+    replay the graph; every replay equals a plain call bit for bit, also after
+    the points change in place (same buffers, new data)."""
+    blocks = inputs.batched_blocks(seed=11, nblocks=24, lo=64, hi=600)
+    specs = _specs(blocks)
+    plain = B.make_opts(1e-8, 8, -256, seed=0, rank_cap=256, leaf_rank_cap=256)
+    gopts = B.make_opts(1e-8, 8, -256, seed=0, rank_cap=256, leaf_rank_cap=256, flags=B.FLAG_GRAPH)
+    gctx = B.Context()
+    ref = B.Batch(ctx, specs, plain).run()
+    gb = B.Batch(gctx, specs, gopts)
+    for _ in range(3):
+        gb.run()
+        torch.cuda.synchronize()
+        _same_results(ref, gb)
+    for s in specs:  # new points in the same device buffers
+        s.keep[0].mul_(1.05)
+        s.keep[1].add_(0.02)
+    ref2 = B.Batch(ctx, specs, plain).run()
+    gb.run()
+    torch.cuda.synchronize()
+    _same_results(ref2, gb)
+
+
+def test_autotune_returns_a_cluster_size_with_valid_results(ctx):
+    blocks = inputs.batched_blocks(seed=12, nblocks=16, lo=64, hi=600)
+    specs = _specs(blocks)
+    opts = B.make_opts(1e-8, 8, -256, seed=0, rank_cap=256, leaf_rank_cap=256)
+    bt = B.Batch(ctx, specs, opts)
+    c, ms = bt.autotune()
+    assert c in (1, 2, 4, 8, 16) and ms > 0
+    bt.run()
+    torch.cuda.synchronize()
+    for (x, y, h), res in zip(blocks, bt.results()):
+        ogen = og.Gaussian(x, y, h)
+        A = ogen(np.arange(ogen.m), np.arange(ogen.n))
+        U, S, V = res.U.cpu().numpy(), res.S.cpu().numpy(), res.V.cpu().numpy()
+        err = np.linalg.norm(A - (U * S) @ V) / np.linalg.norm(A)
+        sv = np.linalg.svd(A, compute_uv=False)
+        e_opt = np.linalg.norm(sv[ol.eps_rank(sv, 1e-8):]) / np.linalg.norm(sv)
+        assert err <= 2 * max(1e-8, e_opt), (err, e_opt)
