@@ -230,6 +230,21 @@ hbaca_status hbaca_apply_backward(hbaca_ctx* ctx, const hbaca_gen* gen, const hb
                                   int64_t lddy, double* d_h, double* d_x, double* d_y, void* dX, int64_t lddx,
                                   void* bwd_workspace, size_t bwd_bytes, void* stream);
 
+/* Reverse pass over the blocks of one taped hbaca_compress_batched call
+   (GAUSSIAN, F64): per block b the same as hbaca_apply_backward with X[b]
+   (n_b x nrhs, ld n_b), dY[b] (m_b x nrhs, ld m_b), dX[b] (n_b x nrhs, ld n_b;
+   dX or dX[b] may be NULL), d_x[b] (m_b x dim), d_y[b] (n_b x dim) and d_h[b]
+   (d_h: a device array of nblocks doubles; any of d_h, d_x, d_y may be NULL).
+   X, dY, dX, d_x, d_y are HOST arrays of device pointers; gens, results are the
+   forward's host arrays.  The size query reads the forward's ranks. */
+size_t hbaca_backward_workspace_size_batched(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                             const void* workspace, int64_t nrhs, void* stream);
+hbaca_status hbaca_apply_backward_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens,
+                                          const hbaca_opts* opts, const hbaca_result* results, const void* workspace,
+                                          const void* const* X, int64_t nrhs, const void* const* dY, double* d_h,
+                                          double* const* d_x, double* const* d_y, void* const* dX,
+                                          void* bwd_workspace, size_t bwd_bytes, void* stream);
+
 /* Autotuner of the batched (or single, nblocks = 1) call: times the
    persistent leaf BACA launch (Alg. 2 over all leaves) with clusters of 1, 2,
    4, 8 and 16 CTAs per leaf (every size whose plan fits `workspace_bytes`)

@@ -84,6 +84,16 @@ SIGNATURES = [
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_kernel_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int32)]),
+    ("hbaca_backward_workspace_size_batched", ctypes.c_size_t, [ctypes.c_int32, ctypes.POINTER(Gen),
+                                                                ctypes.POINTER(Opts), ctypes.c_void_p, ctypes.c_int64,
+                                                                ctypes.c_void_p]),
+    ("hbaca_apply_backward_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Gen),
+                                                    ctypes.POINTER(Opts), ctypes.POINTER(Result), ctypes.c_void_p,
+                                                    ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                                    ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                                    ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                                    ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_size_t,
+                                                    ctypes.c_void_p]),
     ("hbaca_apply_workspace_size", ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64]),
     ("hbaca_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Result), ctypes.c_void_p,
                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -367,6 +377,36 @@ def apply_backward(ctx, spec, opts, comp, X, dY, stream=None, want_dX=True, keep
     if keep_workspace:
         return dh[0], dx, dy, (dXc.t() if want_dX else None), bws
     return dh[0], dx, dy, (dXc.t() if want_dX else None)
+
+
+def apply_backward_batched(batch, Xs, dYs, stream=None, want_dX=True):
+    """hbaca_apply_backward_batched for a Batch compressed with FLAG_TAPE:
+    Xs[b] (n_b, nrhs), dYs[b] (m_b, nrhs).  Returns (d_h (nblocks,), [d_x_b],
+    [d_y_b], [dX_b])."""
+    import torch
+    nb = len(batch.specs)
+    Xc = [_colmajor(X, s.n)[0] for X, s in zip(Xs, batch.specs)]
+    dYc = [_colmajor(dY, s.m)[0] for dY, s in zip(dYs, batch.specs)]
+    nrhs = Xc[0].shape[0]
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = ctypes.c_void_p(stream)
+    nbytes = lib().hbaca_backward_workspace_size_batched(nb, batch.gens, ctypes.byref(batch.opts),
+                                                         ctypes.c_void_p(batch.ws.data_ptr()), nrhs, st)
+    if nbytes == 0:
+        raise HbacaError(1, lib().hbaca_last_error().decode())
+    bws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dh = torch.empty(nb, dtype=torch.float64, device="cuda")
+    dx = [torch.empty((s.m, s.gen.dim), dtype=torch.float64, device="cuda") for s in batch.specs]
+    dy = [torch.empty((s.n, s.gen.dim), dtype=torch.float64, device="cuda") for s in batch.specs]
+    dX = [torch.empty((nrhs, s.n), dtype=torch.float64, device="cuda") for s in batch.specs] if want_dX else None
+    ptrs = lambda ts: (ctypes.c_void_p * nb)(*[t.data_ptr() for t in ts])
+    check(lib().hbaca_apply_backward_batched(batch.ctx.ptr, nb, batch.gens, ctypes.byref(batch.opts), batch.res,
+                                             ctypes.c_void_p(batch.ws.data_ptr()), ptrs(Xc), nrhs, ptrs(dYc),
+                                             ctypes.c_void_p(dh.data_ptr()), ptrs(dx), ptrs(dy),
+                                             ptrs(dX) if want_dX else None, ctypes.c_void_p(bws.data_ptr()), nbytes,
+                                             st))
+    return dh, dx, dy, ([t.t() for t in dX] if want_dX else None)
 
 
 def _autograd_function():

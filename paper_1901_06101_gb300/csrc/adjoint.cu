@@ -125,7 +125,7 @@ CopyTask copy_task(int64_t rows, int64_t cols, const double* src, int64_t s_ri, 
   return CopyTask{rows, cols, src, s_ri, s_cj, dst, d_ri, d_cj};
 }
 
-cudaError_t run_program(const Program& pg, char* dev_blob, const GaussAdj& G, cudaStream_t st, int& launches) {
+cudaError_t run_program(const Program& pg, char* dev_blob, cudaStream_t st, int& launches) {
   cudaError_t e = cudaSuccess;
   if (!pg.blob.empty()) e = cudaMemcpyAsync(dev_blob, pg.blob.data(), pg.blob.size(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
@@ -144,18 +144,18 @@ cudaError_t run_program(const Program& pg, char* dev_blob, const GaussAdj& G, cu
         gap_kernel<<<dim3((unsigned)s.grid, s.ntasks), 256, 0, st>>>(reinterpret_cast<const GapTask*>(tp));
         break;
       case ST_GENROWS:
-        genrows_kernel<<<dim3((unsigned)s.grid, s.ntasks), 256, 0, st>>>(reinterpret_cast<const GenRowsTask*>(tp), G);
+        genrows_kernel<<<dim3((unsigned)s.grid, s.ntasks), 256, 0, st>>>(reinterpret_cast<const GenRowsTask*>(tp));
         break;
       case ST_LEAFSTEP:
         leafstep_kernel<<<s.ntasks, 32, kLeafStepSmem, st>>>(reinterpret_cast<const LeafStepTask*>(tp));
         break;
       case ST_ADJCOLS:
         genadj_cols_kernel<<<dim3((unsigned)s.grid, s.ntasks), kAdjThreads, 0, st>>>(
-            reinterpret_cast<const GenAdjTask*>(tp), G);
+            reinterpret_cast<const GenAdjTask*>(tp));
         break;
       case ST_ADJROWS:
         genadj_rows_kernel<<<dim3((unsigned)s.grid, s.ntasks), kAdjThreads, 0, st>>>(
-            reinterpret_cast<const GenAdjTask*>(tp), G);
+            reinterpret_cast<const GenAdjTask*>(tp));
         break;
     }
     e = cudaGetLastError();
@@ -247,7 +247,7 @@ struct NodeRec {
 };
 
 struct LeafRec {
-  int leaf;
+  int leaf, block;
   int64_t m, n, row0, col0;
   int rB;                    // BACA rank
   const double* UB;          // m x rB (ld m)
@@ -271,9 +271,8 @@ struct Backward {
   size_t total = 0;
 };
 
-// Caller arrays of one backward call (device pointers).
-struct BwdArgs {
-  int64_t nrhs;
+// Caller arrays of one block of a backward call (device pointers).
+struct BlockArgs {
   const double* X;
   int64_t ldx;
   const double* dY;
@@ -286,6 +285,14 @@ struct BwdArgs {
   int rank;
   double* dX;       // may be null
   int64_t lddx;
+  double* d_x;      // gradient outputs (may be null)
+  double* d_y;
+  double* d_h;
+};
+
+struct BwdArgs {
+  int64_t nrhs;
+  std::vector<BlockArgs> blk;
 };
 
 // Lay out the backward workspace at base address `bws` and program every
@@ -332,15 +339,15 @@ bool build_backward(const Plan& p, const char* ws, const TapeSizes& ts, const Bw
       bw.nodes.push_back(nd);
     }
   }
-  // ---- the root of block 0 receives (dY, X)
-  {
-    const int rn = node_of_ref[p.root_tape_first];
+  // ---- the root of every block receives (dY, X)
+  for (int b = 0; b < p.nblocks; ++b) {
+    const int rn = node_of_ref[p.root_tape_first + b];
     if (rn < 0) { err = "no root node"; return false; }
     Adj a;
-    a.P = ar.dY;
-    a.ldp = ar.lddy;
-    a.Q = ar.X;
-    a.ldq = ar.ldx;
+    a.P = ar.blk[b].dY;
+    a.ldp = ar.blk[b].lddy;
+    a.Q = ar.blk[b].X;
+    a.ldq = ar.blk[b].ldx;
     a.rho = (int)nrhs;
     a.set = true;
     bw.nodes[rn].in = a;
@@ -352,6 +359,7 @@ bool build_backward(const Plan& p, const char* ws, const TapeSizes& ts, const Bw
     LeafRec& lr = bw.leaves[l];
     const LeafDesc& Ld = leafd[l];
     lr.leaf = l;
+    lr.block = Ld.block;
     lr.m = Ld.m;
     lr.n = Ld.n;
     lr.row0 = Ld.row0;
@@ -413,8 +421,23 @@ bool build_backward(const Plan& p, const char* ws, const TapeSizes& ts, const Bw
     lr.slotcol = L.take((size_t)rB * 4);
     lr.rowidx = L.take((size_t)std::max(lr.nrow, 1) * 4);
   }
-  const size_t t2 = L.take((size_t)std::max(ar.rank, 1) * nrhs * 8);  // U^T dY for dX
+  std::vector<size_t> t2(p.nblocks);  // U^T dY for dX, per block
+  for (int b = 0; b < p.nblocks; ++b) t2[b] = L.take((size_t)std::max(ar.blk[b].rank, 1) * nrhs * 8);
   bw.zero_bytes = L.cur;
+  // the entry generator of a block and where its gradients go
+  auto gauss_of = [&](int b) {
+    GaussAdj G;
+    const hbaca_gen& g = p.gens[b];
+    G.x = g.x;
+    G.y = g.y;
+    G.dim = g.dim;
+    G.h = g.h;
+    G.c = -1.0 / (2.0 * g.h * g.h);
+    G.dx = ar.blk[b].d_x;
+    G.dy = ar.blk[b].d_y;
+    G.dh = ar.blk[b].d_h;
+    return G;
+  };
 
   Program& pg = bw.pg;
 
@@ -533,7 +556,7 @@ bool build_backward(const Plan& p, const char* ws, const TapeSizes& ts, const Bw
         GemmTask t = gemm_task(dI, (int)n, r0, -1.0, lr.UB, 1, m, lr.VB, n, 1, Rk, n, 1, true);
         t.amap = it.I;
         gR.push_back(t);
-        gen.push_back(GenRowsTask{dI, (int)n, it.I, Rk, lr.row0, lr.col0});
+        gen.push_back(GenRowsTask{dI, (int)n, it.I, Rk, lr.row0, lr.col0, gauss_of(lr.block)});
         // Zbar = Vbar(r0:r0+dk, :) R_k^T  (dk x dI)
         gZ.push_back(gemm_task(dk, dI, (int)n, 1.0, Vb + (size_t)r0 * n, n, 1, Rk, 1, n, D(lr.Zbar), 1, dk, true));
         // Acols(:, r0:r0+dk) = Ubar(:, r0:r0+dk), then the LRID step adds Wbar at rows I_k
@@ -604,6 +627,7 @@ bool build_backward(const Plan& p, const char* ws, const TapeSizes& ts, const Bw
       t.slotcol = I32(lr.slotcol);
       t.Arows = D(lr.Arows);
       t.rowidx = I32(lr.rowidx);
+      t.G = gauss_of(lr.block);
       tc.push_back(t);
       tr.push_back(t);
       gm = std::max<int64_t>(gm, (lr.m + kAdjThreads - 1) / kAdjThreads);
@@ -613,14 +637,21 @@ bool build_backward(const Plan& p, const char* ws, const TapeSizes& ts, const Bw
     pg.add(ST_ADJROWS, tr, gn);
   }
 
-  // ---- dX = V^T diag(S) (U^T dY)
-  if (ar.dX && ar.rank > 0) {
-    const int r = ar.rank;
-    const int64_t m = p.gens[0].m, n = p.gens[0].n;
-    pg.gemm({gemm_task(r, (int)nrhs, (int)m, 1.0, ar.U, ar.ldu, 1, ar.dY, 1, ar.lddy, D(t2), 1, r, false)});
-    GemmTask t = gemm_task((int)n, (int)nrhs, r, 1.0, ar.V, 1, ar.ldv, D(t2), 1, r, ar.dX, 1, ar.lddx, false);
-    t.akscale = ar.S;
-    pg.gemm({t});
+  // ---- dX = V^T diag(S) (U^T dY), per block
+  {
+    std::vector<GemmTask> a, b2;
+    for (int b = 0; b < p.nblocks; ++b) {
+      const BlockArgs& ba = ar.blk[b];
+      if (!ba.dX || ba.rank <= 0) continue;
+      const int r = ba.rank;
+      const int64_t m = p.gens[b].m, n = p.gens[b].n;
+      a.push_back(gemm_task(r, (int)nrhs, (int)m, 1.0, ba.U, ba.ldu, 1, ba.dY, 1, ba.lddy, D(t2[b]), 1, r, false));
+      GemmTask t = gemm_task((int)n, (int)nrhs, r, 1.0, ba.V, 1, ba.ldv, D(t2[b]), 1, r, ba.dX, 1, ba.lddx, false);
+      t.akscale = ba.S;
+      b2.push_back(t);
+    }
+    pg.gemm(a);
+    pg.gemm(b2);
   }
   bw.blob_off = align256(bw.zero_bytes);
   bw.total = bw.blob_off + align256(pg.blob.size());
@@ -635,9 +666,11 @@ using namespace hbaca;
 namespace {
 
 // Plan of the forward and the sizes it left in its workspace.
-bool load_forward(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs, void* stream,
-                  Plan& p, TapeSizes& ts, int& sms, std::string& err) {
-  if (!check_real_gauss(gen, err)) return false;
+bool load_forward(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
+                  void* stream, Plan& p, TapeSizes& ts, int& sms, std::string& err) {
+  if (!gens || nblocks < 1) { err = "gens is NULL or nblocks < 1"; return false; }
+  for (int b = 0; b < nblocks; ++b)
+    if (!check_real_gauss(gens + b, err)) return false;
   if (!opts || !workspace) { err = "opts or workspace is NULL"; return false; }
   if (nrhs < 1) { err = "nrhs must be >= 1"; return false; }
   if (!(opts->flags & HBACA_FLAG_TAPE)) { err = "opts must carry HBACA_FLAG_TAPE (the flags of the forward call)"; return false; }
@@ -645,13 +678,109 @@ bool load_forward(const hbaca_gen* gen, const hbaca_opts* opts, const void* work
   sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaGetLastError();
-  if (!make_plan(gen, 1, *opts, sms, p, err)) return false;
+  if (!make_plan(gens, nblocks, *opts, sms, p, err)) return false;
   return read_sizes(p, reinterpret_cast<const char*>(workspace), reinterpret_cast<cudaStream_t>(stream), ts, err);
 }
 
-int root_rank(const Plan& p, const TapeSizes& ts) {
+int root_rank(const Plan& p, const TapeSizes& ts, int b) {
   const BlockRef* refs = reinterpret_cast<const BlockRef*>(p.desc.data() + p.refs_off);
-  return ts.ranks[refs[p.root_tape_first].rank_slot];
+  return ts.ranks[refs[p.root_tape_first + b].rank_slot];
+}
+
+// Arguments with placeholder pointers: the backward's layout does not depend
+// on the caller's arrays, only on the sizes.
+BwdArgs placeholder_args(const Plan& p, const TapeSizes& ts, int64_t nrhs) {
+  static const double kDummy[1] = {0.0};
+  BwdArgs ar;
+  ar.nrhs = nrhs;
+  for (int b = 0; b < p.nblocks; ++b) {
+    const int64_t m = p.gens[b].m, n = p.gens[b].n;
+    ar.blk.push_back(BlockArgs{kDummy, n, kDummy, m, kDummy, m, kDummy, kDummy, n, root_rank(p, ts, b),
+                               const_cast<double*>(kDummy), n, nullptr, nullptr, nullptr});
+  }
+  return ar;
+}
+
+size_t backward_size(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts, const void* workspace,
+                     int64_t nrhs, void* stream) {
+  Plan p;
+  TapeSizes ts;
+  int sms = 152;
+  std::string err;
+  if (!load_forward(nblocks, gens, opts, workspace, nrhs, stream, p, ts, sms, err)) {
+    record_error(HBACA_INVALID_ARG, err);
+    return 0;
+  }
+  const BwdArgs ar = placeholder_args(p, ts, nrhs);
+  Backward bw;
+  bw.pg.sms = sms;
+  char* base = reinterpret_cast<char*>(static_cast<uintptr_t>(4096));
+  if (!build_backward(p, reinterpret_cast<const char*>(workspace), ts, ar, base, bw, err)) {
+    record_error(HBACA_INVALID_ARG, err);
+    return 0;
+  }
+  record_error(HBACA_OK, "");
+  return bw.total;
+}
+
+// The reverse pass over the blocks of one forward call; `ar.blk` holds the
+// caller's arrays of every block.
+hbaca_status backward(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts, const void* workspace,
+                      BwdArgs& ar, void* bwd_workspace, size_t bwd_bytes, void* stream) {
+  if (!bwd_workspace) return record_error(HBACA_INVALID_ARG, "NULL backward workspace");
+  if (reinterpret_cast<uintptr_t>(bwd_workspace) & 255u)
+    return record_error(HBACA_WORKSPACE, "backward workspace must be 256-byte aligned");
+  Plan p;
+  TapeSizes ts;
+  int sms = 152;
+  std::string err;
+  if (!load_forward(nblocks, gens, opts, workspace, ar.nrhs, stream, p, ts, sms, err))
+    return record_error(HBACA_INVALID_ARG, err);
+  for (int b = 0; b < nblocks; ++b) {
+    const BlockArgs& ba = ar.blk[b];
+    if (!ba.X || !ba.dY) return record_error(HBACA_INVALID_ARG, "NULL X or dY");
+    if (ba.ldx < gens[b].n || ba.lddy < gens[b].m || (ba.dX && ba.lddx < gens[b].n))
+      return record_error(HBACA_INVALID_ARG, "leading dimensions too small");
+    if (ba.rank != root_rank(p, ts, b))
+      return record_error(HBACA_INVALID_ARG, "result rank differs from the tape's root rank");
+  }
+  char* bws = reinterpret_cast<char*>(bwd_workspace);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Backward bw;
+  bw.pg.sms = sms;
+  if (!build_backward(p, reinterpret_cast<const char*>(workspace), ts, ar, bws, bw, err))
+    return record_error(HBACA_INVALID_ARG, err);
+  if (bw.total > bwd_bytes)
+    return record_error(HBACA_WORKSPACE, "backward workspace too small (hbaca_backward_workspace_size gives the size)");
+  // zero the buffers and the outputs, upload the row indices, run
+  cudaError_t e = cudaMemsetAsync(bws, 0, bw.zero_bytes, st);
+  for (int b = 0; b < nblocks && e == cudaSuccess; ++b) {
+    const BlockArgs& ba = ar.blk[b];
+    if (ba.dX)
+      for (int64_t c = 0; c < ar.nrhs && e == cudaSuccess; ++c)
+        e = cudaMemsetAsync(ba.dX + c * ba.lddx, 0, (size_t)gens[b].n * 8, st);
+    if (e == cudaSuccess && ba.d_x) e = cudaMemsetAsync(ba.d_x, 0, (size_t)gens[b].m * gens[b].dim * 8, st);
+    if (e == cudaSuccess && ba.d_y) e = cudaMemsetAsync(ba.d_y, 0, (size_t)gens[b].n * gens[b].dim * 8, st);
+    if (e == cudaSuccess && ba.d_h) e = cudaMemsetAsync(ba.d_h, 0, 8, st);
+  }
+  for (size_t l = 0; l < bw.leaves.size() && e == cudaSuccess; ++l) {
+    const LeafRec& lr = bw.leaves[l];
+    if (!lr.rowidx_h.empty())
+      e = cudaMemcpyAsync(bws + lr.rowidx, lr.rowidx_h.data(), lr.rowidx_h.size() * 4, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return record_error(HBACA_CUDA, std::string("backward set-up: ") + cudaGetErrorString(e));
+  int launches = 0;
+  e = run_program(bw.pg, bws + bw.blob_off, st, launches);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return record_error(HBACA_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+  return record_error(HBACA_OK, "");
+}
+
+BlockArgs block_args(const hbaca_result& r, const void* X, int64_t ldx, const void* dY, int64_t lddy, void* dX,
+                     int64_t lddx, double* d_x, double* d_y, double* d_h) {
+  return BlockArgs{reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(dY), lddy,
+                   reinterpret_cast<const double*>(r.U), r.ldu, r.S, reinterpret_cast<const double*>(r.V), r.ldv,
+                   (int)r.rank, reinterpret_cast<double*>(dX), lddx, d_x, d_y, d_h};
 }
 
 }  // namespace
@@ -694,9 +823,8 @@ hbaca_status hbaca_apply(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_resul
   }
   if (tbytes + pg.blob.size() > hbaca_apply_workspace_size(std::max(r, 1), nrhs))
     return record_error(HBACA_WORKSPACE, "apply workspace too small");
-  GaussAdj G{};
   int launches = 0;
-  cudaError_t e = run_program(pg, ws + tbytes, G, st, launches);
+  cudaError_t e = run_program(pg, ws + tbytes, st, launches);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return record_error(HBACA_CUDA, std::string("apply: ") + cudaGetErrorString(e));
   return record_error(HBACA_OK, "");
@@ -704,82 +832,37 @@ hbaca_status hbaca_apply(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_resul
 
 size_t hbaca_backward_workspace_size(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
                                      void* stream) {
-  Plan p;
-  TapeSizes ts;
-  int sms = 152;
-  std::string err;
-  if (!load_forward(gen, opts, workspace, nrhs, stream, p, ts, sms, err)) {
-    record_error(HBACA_INVALID_ARG, err);
-    return 0;
-  }
-  // the layout does not depend on the caller's arrays: lay out against placeholders
-  static const double kDummy[1] = {0.0};
-  BwdArgs ar{nrhs, kDummy, gen->n, kDummy, gen->m, kDummy, gen->m, kDummy, kDummy, gen->n, root_rank(p, ts),
-             const_cast<double*>(kDummy), gen->n};
-  Backward bw;
-  bw.pg.sms = sms;
-  char* base = reinterpret_cast<char*>(static_cast<uintptr_t>(4096));
-  if (!build_backward(p, reinterpret_cast<const char*>(workspace), ts, ar, base, bw, err)) {
-    record_error(HBACA_INVALID_ARG, err);
-    return 0;
-  }
-  record_error(HBACA_OK, "");
-  return bw.total;
+  return backward_size(1, gen, opts, workspace, nrhs, stream);
+}
+
+size_t hbaca_backward_workspace_size_batched(int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
+                                             const void* workspace, int64_t nrhs, void* stream) {
+  return backward_size(nblocks, gens, opts, workspace, nrhs, stream);
 }
 
 hbaca_status hbaca_apply_backward(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts, const hbaca_result* res,
                                   const void* workspace, const void* X, int64_t nrhs, int64_t ldx, const void* dY,
                                   int64_t lddy, double* d_h, double* d_x, double* d_y, void* dX, int64_t lddx,
                                   void* bwd_workspace, size_t bwd_bytes, void* stream) {
-  if (!ctx || !res || !X || !dY || !bwd_workspace) return record_error(HBACA_INVALID_ARG, "NULL argument");
-  if (reinterpret_cast<uintptr_t>(bwd_workspace) & 255u)
-    return record_error(HBACA_WORKSPACE, "backward workspace must be 256-byte aligned");
-  Plan p;
-  TapeSizes ts;
-  int sms = 152;
-  std::string err;
-  if (!load_forward(gen, opts, workspace, nrhs, stream, p, ts, sms, err)) return record_error(HBACA_INVALID_ARG, err);
-  if (ldx < gen->n || lddy < gen->m || (dX && lddx < gen->n)) return record_error(HBACA_INVALID_ARG, "leading dimensions too small");
-  if (res->rank != root_rank(p, ts)) return record_error(HBACA_INVALID_ARG, "result rank differs from the tape's root rank");
-  char* bws = reinterpret_cast<char*>(bwd_workspace);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  BwdArgs ar{nrhs, reinterpret_cast<const double*>(X), ldx, reinterpret_cast<const double*>(dY), lddy,
-             reinterpret_cast<const double*>(res->U), res->ldu, res->S, reinterpret_cast<const double*>(res->V), res->ldv,
-             res->rank, reinterpret_cast<double*>(dX), lddx};
-  Backward bw;
-  bw.pg.sms = sms;
-  if (!build_backward(p, reinterpret_cast<const char*>(workspace), ts, ar, bws, bw, err))
-    return record_error(HBACA_INVALID_ARG, err);
-  if (bw.total > bwd_bytes)
-    return record_error(HBACA_WORKSPACE, "backward workspace too small (hbaca_backward_workspace_size gives the size)");
-  // zero the buffers and the outputs, upload the row indices, run
-  cudaError_t e = cudaMemsetAsync(bws, 0, bw.zero_bytes, st);
-  if (e == cudaSuccess && dX)
-    for (int64_t c = 0; c < nrhs && e == cudaSuccess; ++c)
-      e = cudaMemsetAsync(reinterpret_cast<double*>(dX) + c * lddx, 0, (size_t)gen->n * 8, st);
-  if (e == cudaSuccess && d_x) e = cudaMemsetAsync(d_x, 0, (size_t)gen->m * gen->dim * 8, st);
-  if (e == cudaSuccess && d_y) e = cudaMemsetAsync(d_y, 0, (size_t)gen->n * gen->dim * 8, st);
-  if (e == cudaSuccess && d_h) e = cudaMemsetAsync(d_h, 0, 8, st);
-  for (size_t l = 0; l < bw.leaves.size() && e == cudaSuccess; ++l) {
-    const LeafRec& lr = bw.leaves[l];
-    if (!lr.rowidx_h.empty())
-      e = cudaMemcpyAsync(bws + lr.rowidx, lr.rowidx_h.data(), lr.rowidx_h.size() * 4, cudaMemcpyHostToDevice, st);
-  }
-  if (e != cudaSuccess) return record_error(HBACA_CUDA, std::string("backward set-up: ") + cudaGetErrorString(e));
-  GaussAdj G;
-  G.x = gen->x;
-  G.y = gen->y;
-  G.dim = gen->dim;
-  G.h = gen->h;
-  G.c = -1.0 / (2.0 * gen->h * gen->h);
-  G.dx = d_x;
-  G.dy = d_y;
-  G.dh = d_h;
-  int launches = 0;
-  e = run_program(bw.pg, bws + bw.blob_off, G, st, launches);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return record_error(HBACA_CUDA, std::string("backward: ") + cudaGetErrorString(e));
-  return record_error(HBACA_OK, "");
+  if (!ctx || !res || !X || !dY || !gen) return record_error(HBACA_INVALID_ARG, "NULL argument");
+  BwdArgs ar;
+  ar.nrhs = nrhs;
+  ar.blk.push_back(block_args(*res, X, ldx, dY, lddy, dX, lddx, d_x, d_y, d_h));
+  return backward(1, gen, opts, workspace, ar, bwd_workspace, bwd_bytes, stream);
+}
+
+hbaca_status hbaca_apply_backward_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens,
+                                          const hbaca_opts* opts, const hbaca_result* results, const void* workspace,
+                                          const void* const* X, int64_t nrhs, const void* const* dY, double* d_h,
+                                          double* const* d_x, double* const* d_y, void* const* dX,
+                                          void* bwd_workspace, size_t bwd_bytes, void* stream) {
+  if (!ctx || !gens || !results || !X || !dY || nblocks < 1) return record_error(HBACA_INVALID_ARG, "NULL argument");
+  BwdArgs ar;
+  ar.nrhs = nrhs;
+  for (int b = 0; b < nblocks; ++b)
+    ar.blk.push_back(block_args(results[b], X[b], gens[b].n, dY[b], gens[b].m, dX ? dX[b] : nullptr, gens[b].n,
+                                d_x ? d_x[b] : nullptr, d_y ? d_y[b] : nullptr, d_h ? d_h + b : nullptr));
+  return backward(nblocks, gens, opts, workspace, ar, bwd_workspace, bwd_bytes, stream);
 }
 
 int64_t hbaca_debug_backward_json(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
@@ -788,13 +871,11 @@ int64_t hbaca_debug_backward_json(const hbaca_gen* gen, const hbaca_opts* opts, 
   TapeSizes ts;
   int sms = 152;
   std::string err;
-  if (!load_forward(gen, opts, workspace, nrhs, stream, p, ts, sms, err)) {
+  if (!load_forward(1, gen, opts, workspace, nrhs, stream, p, ts, sms, err)) {
     record_error(HBACA_INVALID_ARG, err);
     return -1;
   }
-  static const double kDummy[1] = {0.0};
-  BwdArgs ar{nrhs, kDummy, gen->n, kDummy, gen->m, kDummy, gen->m, kDummy, kDummy, gen->n, root_rank(p, ts),
-             const_cast<double*>(kDummy), gen->n};
+  const BwdArgs ar = placeholder_args(p, ts, nrhs);
   Backward bw;
   bw.pg.sms = sms;
   char* base = reinterpret_cast<char*>(static_cast<uintptr_t>(4096));

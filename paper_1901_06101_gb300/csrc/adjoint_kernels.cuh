@@ -69,12 +69,26 @@ struct GapTask {
   double* E2;
 };
 
+// Gaussian entry generator of one block (points, dimension, c = -1 / (2 h^2),
+// h) and where its gradients go.
+struct GaussAdj {
+  const double* x;
+  const double* y;
+  int dim;
+  double c;
+  double h;
+  double* dx;  // m x dim (may be null)
+  double* dy;  // n x dim (may be null)
+  double* dh;  // 1 (may be null)
+};
+
 // Gaussian entries of rows I(0..rows-1) of a leaf added to R (rows x n, row-major).
 struct GenRowsTask {
   int32_t rows, n;
   const int32_t* I;  // leaf-local row indices
   double* R;
   int64_t row0, col0;  // leaf offsets in the matrix
+  GaussAdj G;          // the leaf's block
 };
 
 // One reverse BACA iteration of one leaf: from R_k (dI x n, row-major), the
@@ -108,18 +122,9 @@ struct GenAdjTask {
   const int32_t* slotcol;
   const double* Arows;
   const int32_t* rowidx;
+  GaussAdj G;  // the leaf's block: entry generator and gradient outputs
 };
 
-struct GaussAdj {
-  const double* x;
-  const double* y;
-  int dim;
-  double c;
-  double h;
-  double* dx;  // m x dim (may be null)
-  double* dy;  // n x dim (may be null)
-  double* dh;  // 1 (may be null)
-};
 
 // ------------------------------------------------------------------ GEMM
 __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const GemmTask* tasks, int ntasks) {
@@ -251,8 +256,9 @@ __device__ __forceinline__ double gauss_entry(const GaussAdj& G, int64_t i, int6
   return exp(G.c * d2);
 }
 
-__global__ void genrows_kernel(const GenRowsTask* tasks, const GaussAdj G) {
+__global__ void genrows_kernel(const GenRowsTask* tasks) {
   const GenRowsTask T = tasks[blockIdx.y];
+  const GaussAdj G = T.G;
   const int64_t tot = (int64_t)T.rows * T.n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / T.n), j = (int)(e % T.n);
@@ -445,8 +451,9 @@ __device__ __forceinline__ double block_sum_adj(double v, double* red) {
 }
 
 // grid (chunks of rows, task): thread = leaf row i; loops over the kept columns
-__global__ void __launch_bounds__(kAdjThreads) genadj_cols_kernel(const GenAdjTask* tasks, const GaussAdj G) {
+__global__ void __launch_bounds__(kAdjThreads) genadj_cols_kernel(const GenAdjTask* tasks) {
   const GenAdjTask T = tasks[blockIdx.y];
+  const GaussAdj G = T.G;
   __shared__ double ys[kAdjSlots][kMaxDim];
   __shared__ double dys[kAdjSlots][kMaxDim];
   __shared__ double red[32];
@@ -501,8 +508,9 @@ __global__ void __launch_bounds__(kAdjThreads) genadj_cols_kernel(const GenAdjTa
 }
 
 // grid (chunks of columns, task): thread = leaf column j; loops over the residual rows
-__global__ void __launch_bounds__(kAdjThreads) genadj_rows_kernel(const GenAdjTask* tasks, const GaussAdj G) {
+__global__ void __launch_bounds__(kAdjThreads) genadj_rows_kernel(const GenAdjTask* tasks) {
   const GenAdjTask T = tasks[blockIdx.y];
+  const GaussAdj G = T.G;
   __shared__ double xs[kAdjSlots][kMaxDim];
   __shared__ double dxs[kAdjSlots][kMaxDim];
   __shared__ double red[32];

@@ -14,6 +14,7 @@ from oracle import generators as og
 from oracle import hbaca as oh
 from paper_1901_06101_gb300 import binding as B
 from paper_1901_06101_gb300 import inputs
+from tests.test_gpu_batched import levels_for
 
 pytestmark = pytest.mark.gpu
 
@@ -178,3 +179,51 @@ def test_cfg5_full_size_gradient_against_dense_autograd(ctx):
     assert float(torch.linalg.norm(dy - gy)) <= 1e-5 * float(torch.linalg.norm(gy))
     refX = A.detach().T @ Y
     assert float(torch.linalg.norm(dX - refX)) <= 1e-6 * float(torch.linalg.norm(refX))
+
+
+def test_batched_backward_matches_dense_autograd_per_block(ctx):
+    """One batched reverse pass over uneven Gaussian blocks (each with its own
+    tree depth): every block's dL/dh, dL/dx, dL/dy against autograd through
+    that block's dense kernel matrix (O(eps) apart), and dX exactly."""
+    eps, nrhs = 1e-10, 3
+    blocks = inputs.batched_blocks(seed=21, nblocks=6, lo=200, hi=700)
+    specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
+    opts = B.make_opts(eps, 8, -256, seed=0, rank_cap=256, leaf_rank_cap=256, flags=B.FLAG_TAPE)
+    bt = B.Batch(ctx, specs, opts).run()
+    torch.cuda.synchronize()
+    Xs = [torch.from_numpy(inputs.rhs(300 + b, s.n, nrhs)).cuda() for b, s in enumerate(specs)]
+    res = bt.results()
+    Ys = [(r.U * r.S[None, :]) @ (r.V @ X) for r, X in zip(res, Xs)]
+    dh, dx, dy, dX = B.apply_backward_batched(bt, Xs, Ys)
+    for b, ((x, y, h), r, X, Y) in enumerate(zip(blocks, res, Xs, Ys)):
+        Ah = (r.U * r.S[None, :]) @ r.V
+        assert float(torch.linalg.norm(dX[b] - Ah.T @ Y)) <= 1e-12 * float(torch.linalg.norm(Ah.T @ Y))
+        ht = torch.tensor(h, dtype=torch.float64, requires_grad=True)
+        xt = torch.tensor(x, requires_grad=True)
+        yt = torch.tensor(y, requires_grad=True)
+        A = torch.exp(-torch.cdist(xt, yt) ** 2 / (2 * ht ** 2))
+        loss = 0.5 * torch.sum((A @ X.cpu()) ** 2)
+        gh, gx, gy = torch.autograd.grad(loss, (ht, xt, yt))
+        # O(eps) apart; on the smoothest blocks (h ~ 5) the point gradients are
+        # sums of nearly cancelling terms and the two agree to ~2e-6
+        assert abs(float(dh[b]) - float(gh)) <= 1e-5 * abs(float(gh)) + 1e-12, (b, float(dh[b]), float(gh))
+        assert float(torch.linalg.norm(dx[b].cpu() - gx)) <= 1e-5 * float(torch.linalg.norm(gx)) + 1e-12, b
+        assert float(torch.linalg.norm(dy[b].cpu() - gy)) <= 1e-5 * float(torch.linalg.norm(gy)) + 1e-12, b
+    # the reference proper for the smoothest block: central differences of the
+    # oracle H-BACA with this block's pivots (batch index b) and ranks frozen
+    b = max(range(len(blocks)), key=lambda i: blocks[i][2])
+    x, y, h = blocks[b]
+    L = levels_for(x.shape[0], y.shape[0], 256)
+    nb = 1 << L
+    traces = {leaf: B.read_leaf_trace_batched(specs, opts, bt.ws, b, leaf) for leaf in range(nb * nb)}
+    Xn = Xs[b].cpu().numpy()
+
+    def oloss(hh, ranks=None):
+        r = oh.hbaca(og.Gaussian(x, y, hh), L, 8, eps, seed=0, batch_index=b, forced=traces, ranks=ranks)
+        Yo = ((r["U"] * r["s"][None, :]) @ r["V"]) @ Xn
+        return 0.5 * float(np.sum(Yo * Yo)), r
+
+    _, r0 = oloss(h)
+    dl = 1e-6 * h
+    fd = (oloss(h + dl, r0["ranks"])[0] - oloss(h - dl, r0["ranks"])[0]) / (2 * dl)
+    assert abs(float(dh[b]) - fd) <= 1e-6 * abs(fd), (float(dh[b]), fd)
