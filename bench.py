@@ -52,11 +52,21 @@ WORKLOADS = {
     "grad16384": dict(workload="gaussian_f64_16384_d16_L3_eps1e-8_nrhs64_grad", kernel="gaussian",
                       m=16384, n=16384, h=0.7, d=16, levels=3, eps=1e-8, seed=0, nrhs=64,
                       rank_cap=512, leaf_rank_cap=384),
+    # the differentiated workload batched: 256 Gaussian blocks, m, n
+    # log-uniform in [256, 2048], h = 0.7, eps = 1e-8, d = 16, leaves of at most
+    # 256 rows and columns, 64 right-hand sides per block
+    "gradbatch256": dict(workload="gaussian_f64_256_blocks_256-2048_d16_leaf256_eps1e-8_nrhs64_grad",
+                         kernel="gaussian", nblocks=256, h=0.7, d=16, levels=-256, eps=1e-8, seed=5, nrhs=64,
+                         rank_cap=256, leaf_rank_cap=256),
     "batched4096": dict(workload="gaussian_f64_4096_blocks_64-2048_d8_leaf512_eps1e-8", kernel="gaussian",
                         nblocks=4096, d=8, levels=-512, eps=1e-8, seed=3, rank_cap=256, leaf_rank_cap=256),
 }
 WORKLOAD = WORKLOADS["helmholtz20000"]
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max SM clock
+# DRAM bytes (read + write) per launch of the current kernels on the default
+# workload, averaged over one compression's launches (ncu dram__bytes_read.sum
+# + dram__bytes_write.sum); None where no capture of the current kernel exists
+TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 18.89e6}}
 
 
 def parse():
@@ -349,8 +359,9 @@ def run_ours(args, rank, world):
     for kname, fl in work.items():
         kms, kl = ktimes[kname]
         ach = fl / (kms / 1e3) / 1e12
+        traffic = TRAFFIC_PER_LAUNCH.get(args.workload, {}).get(kname)
         roofs[kname] = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "flops_per_launch": fl / max(kl, 1),
+                        "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "flops_per_launch": fl / max(kl, 1),
                         "ms_per_launch": kms / max(kl, 1), "launches": kl, "peak_note": peak_note}
     roof = roofs.get(dominant, roofs["jacobi_kernel"])
     roof = dict(roof, dominant_kernel=dominant)
@@ -412,6 +423,59 @@ def run_grad(args):
             "config": dict(cfg, l2="flushed between timed calls (512 MiB write)", parallelism="1 GPU"),
             "forward_ms": f, "backward_ms": b, "forward_untaped_compress_ms": float(np.mean(fwd_plain)),
             "rank": comp.rank, "dL_dh": dh, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
+def run_gradbatch(args):
+    """One step = batched taped compression + apply per block (forward) and one
+    batched reverse pass (backward); reports both times and their ratio."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+
+    cfg = WORKLOAD
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    blocks = inputs.grad_blocks(seed=cfg["seed"], nblocks=cfg["nblocks"], h=cfg["h"])
+    ctx = B.Context()
+    specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
+    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
+    bt = B.Batch(ctx, specs, opts)
+    Xs = [torch.from_numpy(inputs.rhs(cfg["seed"] + 1 + b, s.n, cfg["nrhs"])).to(dev) for b, s in enumerate(specs)]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def forward():
+        bt.run()
+        return [B.apply(ctx, s, c, X) for s, c, X in zip(specs, bt.results(), Xs)]
+
+    fwd, bwd = [], []
+    with ClockSampler(dev.index) as clk:
+        for it in range(args.warmup + args.steps):
+            tf, Ys = timed(forward)
+            tb, _ = timed(lambda: B.apply_backward_batched(bt, Xs, Ys, want_dX=True))
+            if it >= args.warmup:
+                fwd.append(tf)
+                bwd.append(tb)
+    f, b = float(np.mean(fwd)), float(np.mean(bwd))
+    ranks = bt.ranks()
+    line = {"metric": METRIC, "value": b / f, "unit": "backward ms / forward ms", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f + b, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, l2="flushed between timed calls (512 MiB write)", parallelism="1 GPU"),
+            "forward_ms": f, "backward_ms": b, "ranks": {"max": max(ranks), "mean": float(np.mean(ranks))},
+            "clocks": clk.summary()}
     print(json.dumps(line))
 
 
@@ -521,6 +585,11 @@ def main():
         if args.impl == "reference" or world > 1:
             raise SystemExit("the gradient workload is a single-GPU forward/backward comparison")
         run_grad(args)
+        return
+    if args.workload == "gradbatch256":
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("the gradient workload is a single-GPU forward/backward comparison")
+        run_gradbatch(args)
         return
     if args.workload == "batched4096":
         if args.impl == "reference" or world > 1:

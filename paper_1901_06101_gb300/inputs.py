@@ -119,6 +119,22 @@ def batched_blocks(seed=3, nblocks=4096, lo=64, hi=2048):
     return out
 
 
+def grad_blocks(seed=5, nblocks=256, lo=256, hi=2048, h=0.7):
+    """List of (x, y, h) Gaussian-kernel blocks shaped like the differentiated
+    workload: x uniform in [0,1]^3, y uniform in [2,3]x[0,1]^2, sizes
+    log-uniform in [lo, hi], one width h."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nblocks):
+        m = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        x = rng.uniform(0.0, 1.0, (m, 3))
+        y = rng.uniform(0.0, 1.0, (n, 3))
+        y[:, 0] += 2.0
+        out.append((x, y, float(h)))
+    return out
+
+
 def lowrank(seed, m, n, r, complex_=False):
     rng = np.random.default_rng(seed)
     U = rng.standard_normal((m, r))
