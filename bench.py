@@ -96,14 +96,14 @@ def leaf_spans(n, L):
     return spans
 
 
-def jacobi_accounting(ws, plan, complex_):
+def jacobi_accounting(ws, plan, complex_, accumulates=False):
     """Algorithmic FP64 flops of the Jacobi SVD launches of one compression,
     from the per-task records the kernel leaves (sizes, sweeps, rotations):
     every sweep forms the three inner products of each of the nc (nc - 1) / 2
     column pairs over the mr rows of the core, and every applied rotation
-    updates both columns of the core (mr rows) and of the accumulated
-    rotation (nc rows).  Per element: inner products 16 flops (complex) / 6
-    (real), rotation 18 / 7."""
+    updates both columns of the core (mr rows), and of the accumulated
+    rotation (nc rows) when the call is taped (``accumulates``).  Per element:
+    inner products 16 flops (complex) / 6 (real), rotation 18 / 7."""
     import torch
     fd, fr = (16.0, 18.0) if complex_ else (6.0, 7.0)
     total = 0.0
@@ -116,7 +116,7 @@ def jacobi_accounting(ws, plan, complex_):
             if nc < 2:
                 continue
             nsw = min(int(sweeps) + 1, 40)
-            total += nsw * nc * (nc - 1) / 2 * mr * fd + float(rot) * (mr + nc) * fr
+            total += nsw * nc * (nc - 1) / 2 * mr * fd + float(rot) * (mr + (nc if accumulates else 0)) * fr
     return total
 
 

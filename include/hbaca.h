@@ -103,7 +103,9 @@ typedef struct hbaca_gen {
 #define HBACA_FLAG_TAPE 4u     /* keep, in the workspace, every intermediate block of the
                                   merge tree with ALL singular triplets of its core (not
                                   only the eps-rank kept ones), for hbaca_apply_backward.
-                                  The kept results are the same as without the flag; the
+                                  The kept results agree with an untaped call to rounding
+                                  (a taped call accumulates the Jacobi rotations, an
+                                  untaped one recovers the kept right vectors); the
                                   workspace is larger (no store is reused across levels) */
 #define HBACA_FLAG_GRAPH 8u    /* capture the call into a CUDA graph and replay it: the first
                                   call with a given plan, caller buffers, workspace and
@@ -124,9 +126,9 @@ typedef struct hbaca_opts {
                              and columns (limited by 2^L <= min(m, n)) */
   uint64_t seed;          /* seed of the random initial column blocks J_1 */
   int64_t rank_cap;       /* column capacity of U / rows of V (output and every
-                             merged block); 0 = min(m, n, 1024) */
+                             merged block), <= 1024; 0 = min(m, n, 1024) */
   int64_t leaf_rank_cap;  /* capacity of a leaf's BACA factors before
-                             re-compression; 0 = min(m_leaf, n_leaf, 1024) */
+                             re-compression, <= 1024; 0 = min(m_leaf, n_leaf, 1024) */
   uint32_t flags;         /* HBACA_FLAG_* */
   int32_t cluster;        /* CTAs per leaf (1, 2, 4, 8, 16); 0 = choose automatically */
 } hbaca_opts;

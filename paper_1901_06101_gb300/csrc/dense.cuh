@@ -518,7 +518,8 @@ constexpr int kJSlotMax = 96;  // bytes reserved per pair slot (>= sizeof(JPair<
 template <typename T, bool kDsm>
 __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
                               T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
-                              int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot) {
+                              int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot,
+                              bool acc_w) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   auto colX = [&](int j) -> T* {
     if constexpr (kDsm) return cl.map_shared_rank(dsm, j % c) + (int64_t)(j / c) * ldc;
@@ -621,7 +622,7 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
         if (lane == 0 && fmax(sl.al, sl.be) >= tau2) flag[fb & 1] = 1;
         ++nrot;
         rotate_pair_t<T, kDsm>(colX(a), colX(b), mr, cs, sn, spv, cpv, lane);
-        rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
+        if (acc_w) rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
       }
       __syncthreads();
       cl.sync();
@@ -679,15 +680,20 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   const int64_t ldc = (int64_t)mr + nc;
   T* dsm = reinterpret_cast<T*>(smem_raw + hdr_bytes);
   const bool use_dsm = (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
+  // the rotations are accumulated (W) only for a taped output, which keeps
+  // every triplet; otherwise the kept right vectors of X are recovered from
+  // X^H z_i = sigma_i w_i after the sweeps (wsolve_kernel)
+  const bool acc_w = P.out_blocks[t.out].full_slot >= 0;
   if (use_dsm) {  // own columns: X from global memory, W = I
     for (int l = warp; l < per; l += nw) {
       const int j = l * c + q;
       if (j >= nc) continue;
       T* dst = dsm + (int64_t)l * ldc;
       for (int i = lane; i < mr; i += 32) dst[i] = M[(int64_t)j * ld + i];
-      for (int i = lane; i < nc; i += 32) dst[mr + i] = from_re<T>(i == j ? 1.0 : 0.0);
+      if (acc_w)
+        for (int i = lane; i < nc; i += 32) dst[mr + i] = from_re<T>(i == j ? 1.0 : 0.0);
     }
-  } else {  // Y = I
+  } else if (acc_w) {  // Y = I
     const int j0 = q * per, j1 = min(nc, j0 + per);
     for (int j = j0; j < j1; ++j)
       for (int i = tid; i < nc; i += blockDim.x) Y[(int64_t)j * ld + i] = from_re<T>(i == j ? 1.0 : 0.0);
@@ -725,17 +731,18 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   JPair<T>* slots = reinterpret_cast<JPair<T>*>(smem_raw + slot_off);
   if (use_dsm)
     jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
-                           slots, sweep, nrot);
+                           slots, sweep, nrot, acc_w);
   else
     jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
-                            cmx, slots, sweep, nrot);
+                            cmx, slots, sweep, nrot, acc_w);
   if (use_dsm) {  // the sweeps' result back to global memory for the epilogue and finish_kernel
     for (int l = warp; l < per; l += nw) {
       const int j = l * c + q;
       if (j >= nc) continue;
       const T* src = dsm + (int64_t)l * ldc;
       for (int i = lane; i < mr; i += 32) M[(int64_t)j * ld + i] = src[i];
-      for (int i = lane; i < nc; i += 32) Y[(int64_t)j * ld + i] = src[mr + i];
+      if (acc_w)
+        for (int i = lane; i < nc; i += 32) Y[(int64_t)j * ld + i] = src[mr + i];
     }
   }
   cl.sync();
@@ -793,6 +800,82 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
     }
   }
   cl.sync();
+}
+
+// ------------------------------------------------------------------ right vectors of X
+// For an output that keeps only its eps-rank triplets the sweeps do not
+// accumulate W; its kept columns come from the SVD relation X^H z_i = sigma_i
+// w_i with X = R2^H, i.e. w_i = R2 z_i / sigma_i (R2 upper trapezoidal, the
+// pivoted QR of the core left in place: pivoted column c at physical column
+// perm[c]), written to W's column ord[tc] as the
+// accumulated rotation would have been.  The error of w_i is about
+// eps_mach sigma_1 / sigma_i (at most eps_mach / eps for kept triplets); one
+// modified Gram-Schmidt pass over the s columns restores orthonormality.
+// One CTA per task.
+constexpr int kMaxWsolveCols = 1024;  // kept triplets of one output (rank caps are <= 1024)
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads) wsolve_kernel(const DenseParams<T> P) {
+  const int ti = blockIdx.x;
+  const SvdTask t = P.tasks[ti];
+  const BlockRef ob = P.out_blocks[t.out];
+  if (ob.full_slot >= 0) return;  // taped: W was accumulated
+  const TaskDims dm = P.dims[ti];
+  const int s = min(dm.nout, kMaxWsolveCols);
+  const int ncm = t.kind == TASK_LEAF ? dm.krb : dm.k;
+  const int p = min(dm.kra, ncm);
+  if (s <= 0 || p <= 0) return;
+  const int ld = t.kcap;
+  const T* R2 = P.core + t.m_off;   // R2(r, c) at R2[perm[c] ld + r], r <= c (columns not moved)
+  const int32_t* perm = P.ord + t.ord_off + t.kcap;
+  const T* Z = P.core + t.x_off;    // z_j (normalised for the kept j) at Z[j ld + i], i < ncm
+  T* W = P.core + t.y_off;
+  const int32_t* ord = P.ord + t.ord_off;
+  const double* sg = out_s(P, ob);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // w_tc(r) = sum_{c >= r} R2(r, c) z_ord(c) / sigma_tc; a thread per (tc, r)
+  for (int tc = warp; tc < s; tc += nw) {
+    const int j = ord[tc];
+    const double inv = sg[tc] > 0.0 ? 1.0 / sg[tc] : 0.0;
+    const T* z = Z + (int64_t)j * ld;
+    T* w = W + (int64_t)j * ld;
+    for (int r = lane; r < p; r += 32) {
+      T acc = Traits<T>::zero();
+      for (int c = r; c < ncm; ++c) acc = mac(acc, R2[(int64_t)perm[c] * ld + r], ldcg(z + c));
+      w[r] = scale(acc, inv);
+    }
+  }
+  __syncthreads();
+  // one classical Gram-Schmidt pass in the sorted order (the columns are
+  // orthonormal up to ~eps_mach / eps, so one pass suffices)
+  __shared__ double red[kDenseThreads / 32];
+  __shared__ T dd[kMaxWsolveCols];
+  for (int tc = 0; tc < s; ++tc) {
+    T* wt = W + (int64_t)ord[tc] * ld;
+    for (int u = warp; u < tc; u += nw) {  // d_u = w_u^H w_tc
+      const T* wu = W + (int64_t)ord[u] * ld;
+      T part = Traits<T>::zero();
+      for (int r = lane; r < p; r += 32) part = cmac(part, wu[r], wt[r]);
+      part = warp_sum(part);
+      if (lane == 0) dd[u] = part;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int r = tid; r < p; r += blockDim.x) {  // w_tc -= sum_u w_u d_u
+      T v = wt[r];
+      for (int u = 0; u < tc; ++u) v = msub(v, W[(int64_t)ord[u] * ld + r], dd[u]);
+      wt[r] = v;
+      part += abs2(v);
+    }
+    part = warp_sum(part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    double nrm = 0.0;
+    for (int q2 = 0; q2 < nw; ++q2) nrm += red[q2];
+    const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+    for (int r = tid; r < p; r += blockDim.x) wt[r] = scale(wt[r], inv);
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ finish

@@ -243,6 +243,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, 40, (int)j_hdr,
                                               (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr)));
   }
+  if (!p.tape) HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   rc.launches += 2;
   const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;

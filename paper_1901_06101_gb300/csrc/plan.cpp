@@ -120,6 +120,7 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
     return false;
   }
   if (o.rank_cap < 0 || o.leaf_rank_cap < 0) { err = "rank caps must be >= 0"; return false; }
+  if (o.rank_cap > 1024 || o.leaf_rank_cap > 1024) { err = "rank caps must be <= 1024"; return false; }
   if (sms <= 0) sms = 152;
   p.gens.assign(gens, gens + nblocks);
   p.opts = o;
