@@ -151,20 +151,69 @@ __global__ void pack_kernel(const DenseParams<T> P) {
   }
 }
 
+// ------------------------------------------------------------------ cluster groups
+// A matrix with few companions in its stage is spread over G clusters (a
+// cooperative launch keeps every CTA of the grid resident).  After each
+// cluster has combined its CTAs' partial sums through DSMEM, its leader CTA
+// publishes them in a global slot (double-buffered by step parity), counts
+// itself in on the matrix's arrival counter and waits until all G clusters
+// have arrived at that step; every CTA then sums the G slots in cluster
+// order, so all CTAs of all clusters hold bit-identical totals.  The wait is
+// bounded by kXWaitNs of wall time: on expiry the status word records
+// DS_TIMEOUT and the clusters leave the column loop together.
+constexpr unsigned long long kXWaitNs = 4000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One thread, after a __syncthreads that follows the CTA's slot writes.
+__device__ __forceinline__ int xgroup_arrive_wait(unsigned* cnt, unsigned target, int* status) {
+  __threadfence();
+  atomicAdd(cnt, 1u);
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+    if (v >= target) return 1;
+    if (global_ns() - t0 > kXWaitNs) {
+      set_status(status, DS_TIMEOUT);
+      return 0;
+    }
+    __nanosleep(100);
+  }
+}
+
+// Inter-cluster arguments: G clusters per matrix, slot stride xplen elements.
+template <typename T>
+struct XGroup {
+  int G;
+  int xplen;
+  T* xpart;       // [cluster of the grid][2][xplen]
+  unsigned* xcnt; // [matrix of the launch]
+};
+
 // ------------------------------------------------------------------ QR
 // Householder QR (LAPACK geqr2 convention) of a rows x k column-major matrix,
 // in place: R in the upper triangle (diagonal = beta), reflector tails below,
-// tau[j].  One cluster per matrix; CTA q owns a contiguous slice of rows.
+// tau[j].  G clusters per matrix (one unless the stage has few matrices);
+// CTA q of cluster g owns the contiguous slice g c + q of the rows.
 // Per column: one pass forms the partial squared tail norm, the partial
 // inner products of the tail with every trailing column and the head row;
-// one cluster barrier; every CTA combines the partials in rank order.
+// one cluster barrier; every CTA combines the partials in rank order (then
+// across the G clusters through global memory).
 
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> P, const QrJob* jobs) {
+__global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> P, const QrJob* jobs, const XGroup<T> X) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int xok;
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
-  const int job = blockIdx.x / c;
+  const int G = X.G;
+  const int cid = blockIdx.x / c;
+  const int job = cid / G, g = cid - job * G;
   const QrJob jb = jobs[job];
   const SvdTask t = P.tasks[jb.task];
   const TaskDims dm = P.dims[jb.task];
@@ -175,8 +224,9 @@ __global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> 
   T* tau = P.tau + t.tau_off + (jb.which ? t.kcap : 0);
   const int kk = min(rows, k);
   if (kk <= 0) return;
-  const int chunk = (rows + c - 1) / c;
-  const int ra = min(rows, q * chunk), rb = min(rows, ra + chunk);
+  const int np = G * c, pi = g * c + q;
+  const int chunk = (rows + np - 1) / np;
+  const int ra = min(rows, pi * chunk), rb = min(rows, ra + chunk);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   // partial buffer (double-buffered): [0] sig2 (re), [1] alpha, [2 + l] dot_l, [2 + kcap + l] head row value
   const int plen = 2 + 2 * t.kcap;
@@ -213,6 +263,26 @@ __global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> 
       tot[idx] = s;
     }
     __syncthreads();
+    if (G > 1) {
+      auto slot_idx = [&](int e) {
+        return e < ncol ? (e == 0 ? 0 : 2 + (e - 1)) : (e == ncol ? 1 : 2 + t.kcap + (e - ncol - 1));
+      };
+      if (q == 0) {
+        T* xs = X.xpart + ((size_t)cid * 2 + (j & 1)) * X.xplen;
+        for (int e = tid; e < 2 * ncol; e += blockDim.x) xs[slot_idx(e)] = tot[slot_idx(e)];
+        __syncthreads();
+        if (tid == 0) xok = xgroup_arrive_wait(X.xcnt + job, (unsigned)(j + 1) * G, P.status);
+      }
+      cl.sync();
+      if (*cl.map_shared_rank(&xok, 0) == 0) break;
+      for (int e = tid; e < 2 * ncol; e += blockDim.x) {
+        const int idx = slot_idx(e);
+        T s = Traits<T>::zero();
+        for (int gg = 0; gg < G; ++gg) s = add(s, ldcg(X.xpart + ((size_t)(job * G + gg) * 2 + (j & 1)) * X.xplen + idx));
+        tot[idx] = s;
+      }
+      __syncthreads();
+    }
     if (tid == 0) {
       double beta;
       T tu, sc;
@@ -221,7 +291,7 @@ __global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> 
       coef[1] = sc;
       coef[2] = from_re<T>(beta);
       coef[3] = tu;
-      if (q == 0) tau[j] = tu;
+      if (pi == 0) tau[j] = tu;
     }
     __syncthreads();
     const T ctau = coef[0], sc = coef[1];
@@ -932,11 +1002,15 @@ __global__ void finish_kernel(const DenseParams<T> P) {
 // combined through DSMEM) and a rank-1 update of this CTA's rows.
 
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams<T> P, const QJob* jobs) {
+__global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams<T> P, const QJob* jobs, const XGroup<T> X) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int xok;
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
-  const QJob jb = jobs[blockIdx.x / c];
+  const int G = X.G;
+  const int cid = blockIdx.x / c;
+  const int job = cid / G, g = cid - job * G;
+  const QJob jb = jobs[job];
   const SvdTask t = P.tasks[jb.task];
   const TaskDims dm = P.dims[jb.task];
   const int s = dm.nout;  // columns written (the kept s, or all when taped)
@@ -950,8 +1024,9 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   T* D = jb.to_v ? out_v(P, ob) : out_u(P, ob);
   const int64_t ldd = jb.to_v ? ob.ldv : ob.ldu;
   if (s <= 0) return;
-  const int chunk = (rows + c - 1) / c;
-  const int ra = min(rows, q * chunk), rb = min(rows, ra + chunk);
+  const int np = G * c;
+  const int chunk = (rows + np - 1) / np;
+  const int ra = min(rows, (g * c + q) * chunk), rb = min(rows, ra + chunk);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   T* part = reinterpret_cast<T*>(smem_raw);  // 2 x s partials
   T* wv = part + 2 * s;                       // s combined
@@ -977,9 +1052,25 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
     for (int tc = tid; tc < s; tc += blockDim.x) {
       T sum = Traits<T>::zero();
       for (int r = 0; r < c; ++r) sum = add(sum, cl.map_shared_rank(part + (j & 1) * s, r)[tc]);
-      wv[tc] = mul(tj, sum);
+      wv[tc] = G > 1 ? sum : mul(tj, sum);
     }
     __syncthreads();
+    if (G > 1) {
+      if (q == 0) {
+        T* xs = X.xpart + ((size_t)cid * 2 + (j & 1)) * X.xplen;
+        for (int tc = tid; tc < s; tc += blockDim.x) xs[tc] = wv[tc];
+        __syncthreads();
+        if (tid == 0) xok = xgroup_arrive_wait(X.xcnt + job, (unsigned)(kk - j) * G, P.status);
+      }
+      cl.sync();
+      if (*cl.map_shared_rank(&xok, 0) == 0) break;
+      for (int tc = tid; tc < s; tc += blockDim.x) {
+        T sum = Traits<T>::zero();
+        for (int gg = 0; gg < G; ++gg) sum = add(sum, ldcg(X.xpart + ((size_t)(job * G + gg) * 2 + (j & 1)) * X.xplen + tc));
+        wv[tc] = mul(tj, sum);
+      }
+      __syncthreads();
+    }
     // D(i, tc) -= u_i wv_tc: one thread per row, four columns per step
     for (int i = i0 + tid; i < rb; i += blockDim.x) {
       const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];

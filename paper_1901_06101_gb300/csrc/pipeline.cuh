@@ -33,33 +33,79 @@ constexpr size_t kJacobiSmemLimit = 220 * 1024;  // dynamic shared memory of one
     if (rc.kt) HB_TRY(rc.kt->end(rc.st));                    \
   } while (0)
 
-template <typename K, typename... Args>
-cudaError_t launch_cluster(K kern, int grid, int cluster, size_t smem, cudaStream_t st, Args... args) {
+template <typename K>
+cudaError_t cluster_config(K kern, int grid, int cluster, size_t smem, cudaStream_t st, bool coop,
+                           cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
-  cudaLaunchConfig_t cfg = {};
+  cfg = cudaLaunchConfig_t{};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kDenseThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = coop ? 2 : 1;
+  return cudaSuccess;
+}
+
+// coop: all CTAs of the grid resident at once (kernels whose clusters wait
+// on one another)
+template <typename K, typename... Args>
+cudaError_t launch_cluster_x(K kern, int grid, int cluster, size_t smem, cudaStream_t st, bool coop, Args... args) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  cudaError_t e = cluster_config(kern, grid, cluster, smem, st, coop, cfg, attr);
+  if (e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename K, typename... Args>
+cudaError_t launch_cluster(K kern, int grid, int cluster, size_t smem, cudaStream_t st, Args... args) {
+  return launch_cluster_x(kern, grid, cluster, smem, st, false, args...);
+}
+
+// Clusters of `cluster` CTAs with `smem` bytes that can be resident at once.
+template <typename K>
+int resident_clusters(K kern, int cluster, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  if (cluster_config(kern, cluster, cluster, smem, st, false, cfg, attr) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 inline int pick_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
   int c = 1;
   while (c < 16 && (int64_t)jobs * c < 2 * sms && rows / (2 * c) >= min_rows_per_cta) c *= 2;
   return c;
+}
+
+// Clusters per matrix when a stage has too few matrices to fill the machine
+// with one 16-CTA cluster each: 8-CTA clusters, as many per matrix as the
+// SMs (and the exchange slots) allow; 1 when that is not more than 16 CTAs.
+inline int pick_groups(int jobs, int rows, int sms, int resident, int min_rows_per_cta) {
+  int G = 1;
+  while (jobs * (G + 1) <= kXSlots && jobs * (G + 1) * 8 <= sms && jobs * (G + 1) <= resident &&
+         rows / ((G + 1) * 8) >= min_rows_per_cta)
+    ++G;
+  return G * 8 > 16 ? G : 1;
 }
 
 template <typename Gen>
@@ -173,9 +219,23 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   const QJob* aj = reinterpret_cast<const QJob*>(desc + sg.qjobs_off);
 
   HB_TIMED(KC_PACK, pack_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
-  const int cq = pick_cluster(sg.nqr, sg.rows_max, rc.sms, 64);
+  int cq = pick_cluster(sg.nqr, sg.rows_max, rc.sms, 64);
   const size_t qr_smem = (size_t)(3 * (2 + 2 * sg.kcap) + 4) * sizeof(T);
-  HB_TIMED(KC_QR, HB_TRY(launch_cluster(qr_kernel<T>, sg.nqr * cq, cq, qr_smem, rc.st, D, qj)));
+  const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
+  const size_t qa_smem = 3 * qa_cols * sizeof(T) + 64;
+  XGroup<T> X{1, p.xplen, reinterpret_cast<T*>(ws + p.xpart.off), reinterpret_cast<unsigned*>(ws + p.xcnt.off)};
+  if (cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
+    const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
+                             resident_clusters(qapply_kernel<T>, 8, qa_smem, rc.st));
+    const int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
+    if (G > 1) {
+      cq = 8;
+      X.G = G;
+    }
+  }
+  const bool coop = X.G > 1;
+  if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
+  HB_TIMED(KC_QR, HB_TRY(launch_cluster_x(qr_kernel<T>, sg.nqr * X.G * cq, cq, qr_smem, rc.st, coop, D, qj, X)));
   HB_TIMED(KC_CORE, core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   const size_t qc_smem = (size_t)sg.kcap * 9 + 2 * sizeof(T) + 32 * 12 + 64 + 16;
   HB_TRY(cudaFuncSetAttribute(qrcp_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qc_smem));
@@ -246,9 +306,8 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   if (!p.tape) HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   rc.launches += 2;
-  const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
-  const size_t qa_smem = 3 * qa_cols * sizeof(T) + 64;
-  HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster(qapply_kernel<T>, sg.nq * cq, cq, qa_smem, rc.st, D, aj)));
+  if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
+  HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
   rc.launches += 5;
   if (sg.kind != TASK_LEAF) {
     HB_TIMED(KC_BLOCKPROD, blockprod_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));

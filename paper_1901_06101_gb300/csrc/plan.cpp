@@ -493,6 +493,13 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
     }
     p.jlist = Lo.take(tot * 4);
   }
+  {
+    int kx = (int)p.rank_cap_max;
+    for (const Stage& st : p.stages) kx = std::max(kx, st.kcap);
+    p.xplen = 2 + 2 * kx;
+    p.xpart = Lo.take((size_t)kXSlots * 2 * (size_t)p.xplen * p.esz);
+    p.xcnt = Lo.take((size_t)kXSlots * 4);
+  }
   p.total = Lo.cur;
   return true;
 }

@@ -80,6 +80,8 @@ struct Plan {
   Region full_u, full_s, full_v, half_u, half_s, half_v;
   Region qr, tau, core, ord;
   Region jlist;                   // task index lists of the Jacobi launches (one slot per stage)
+  Region xpart, xcnt;             // inter-cluster partial sums (kXSlots x 2 x xplen) and arrival counters
+  int xplen = 0;
   int64_t cscr_stride = 0, rscr_stride = 0, gscr_stride = 0;
   int max_clusters_scratch = 0;
   // global ref index of node (a, c) of block b: full store at level l, half store at level l

@@ -96,6 +96,10 @@ struct TaskDims {
   int32_t pad;
 };
 
+// Cluster slots of the inter-cluster partial-sum exchange of one QR or
+// Q-application launch (matrices x clusters per matrix).
+constexpr int kXSlots = 32;
+
 struct QrJob {
   int32_t task;
   int32_t which;  // 0: operand A, 1: operand B
