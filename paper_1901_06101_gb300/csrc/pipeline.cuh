@@ -264,26 +264,27 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       const size_t per_cta = (pairs + (size_t)cc * 8 - 1) / ((size_t)cc * 8) * 8;
       return j_base + per_cta * kJSlotMax;
     };
-    std::vector<std::vector<int32_t>> groups(5);  // cluster 1, 2, 4, 8, 16
-    std::vector<size_t> need(5, 0);
+    // cluster size c = 1..16: the round's pairs in one pass over the cluster's warps
+    std::vector<std::vector<int32_t>> groups(17);
+    std::vector<size_t> need(17, 0);
     const std::vector<SvdTask>& th = *sg.tasks_h;
+    const int wpc = kDenseThreads / 32;
     for (int i = 0; i < nt; ++i) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int nc = std::min(dh[i].kra, ncm), mr = ncm;
-      int g = 0;
-      while (g < 4 && (1 << (g + 1)) * kDenseThreads / 32 <= (nc + 1) / 2) ++g;
-      auto share = [&](int gg) { return (size_t)((nc + (1 << gg) - 1) >> gg) * (size_t)(mr + nc) * sizeof(T); };
-      while (g < 4 && share(g) + j_hdr_of(1 << g) > kJacobiSmemLimit) ++g;
+      int g = std::min(16, std::max(1, ((nc + 1) / 2 + wpc - 1) / wpc));
+      auto share = [&](int cc) { return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + nc) * sizeof(T); };
+      while (g < 16 && share(g) + j_hdr_of(g) > kJacobiSmemLimit) ++g;
       groups[g].push_back(i);
-      const size_t sh = share(g) + j_hdr_of(1 << g) <= kJacobiSmemLimit ? share(g) : 0;
+      const size_t sh = share(g) + j_hdr_of(g) <= kJacobiSmemLimit ? share(g) : 0;
       need[g] = std::max(need[g], sh);
     }
     size_t off = sg.jlist_off;
-    for (int g = 0; g < 5; ++g) {
+    for (int g = 1; g <= 16; ++g) {
       if (groups[g].empty()) continue;
       int32_t* lst = reinterpret_cast<int32_t*>(ws + p.jlist.off) + off;
       HB_TRY(cudaMemcpyAsync(lst, groups[g].data(), groups[g].size() * 4, cudaMemcpyHostToDevice, rc.st));
-      const int cg_ = 1 << g;
+      const int cg_ = g;
       const size_t j_hdr = j_hdr_of(cg_);
       HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, (int)groups[g].size() * cg_, cg_, j_hdr + need[g],
                                                 rc.st, D, 40, (int)j_hdr, (int)j_base, (int64_t)need[g],
