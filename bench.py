@@ -69,6 +69,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA 
 TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 13.76e6}}
 
 
+EXTRA_FLAGS = 0  # option flags added to every call (--single-cluster)
+
+
+def mk_opts(*a, flags=0, **kw):
+    from paper_1901_06101_gb300 import binding as B
+    return B.make_opts(*a, flags=flags | EXTRA_FLAGS, **kw)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -80,6 +88,8 @@ def parse():
     ap.add_argument("--workload", default="helmholtz20000", choices=sorted(WORKLOADS))
     ap.add_argument("--nblocks", type=int, default=None, help="batched workload: first N blocks only")
     ap.add_argument("--no-loop", action="store_true", help="batched workload: skip the per-block loop")
+    ap.add_argument("--single-cluster", action="store_true",
+                    help="one cluster per matrix in QR / Q application (for profilers that serialise launches)")
     return ap.parse_args()
 
 
@@ -255,7 +265,7 @@ def run_ours(args, rank, world):
     x, y = inputs.sphere_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
     ctx = B.Context()
     spec = B.helmholtz(x, y, cfg["k"])
-    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
                        leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE)
     ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
     cap = cfg["rank_cap"]
@@ -322,7 +332,7 @@ def run_ours(args, rank, world):
     Uh = torch.empty((cap, cfg["m"]), dtype=torch.complex128).pin_memory()
     Sh = torch.empty(cap, dtype=torch.float64).pin_memory()
     Vh = torch.empty((cap, cfg["n"]), dtype=torch.complex128).pin_memory()
-    opts_e2e = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cap,
+    opts_e2e = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cap,
                            leaf_rank_cap=cfg["leaf_rank_cap"])
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize(dev)
@@ -385,9 +395,9 @@ def run_grad(args):
     X = torch.from_numpy(inputs.rhs(cfg["seed"] + 1, cfg["n"], cfg["nrhs"])).to(dev)
     ctx = B.Context()
     spec = B.gaussian(x, y, cfg["h"])
-    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
                        leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
-    plain = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+    plain = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
                         leaf_rank_cap=cfg["leaf_rank_cap"])
     ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
     wsp = torch.empty(B.workspace_size(spec.gen, plain), dtype=torch.uint8, device=dev)
@@ -439,7 +449,7 @@ def run_gradbatch(args):
     blocks = inputs.grad_blocks(seed=cfg["seed"], nblocks=cfg["nblocks"], h=cfg["h"])
     ctx = B.Context()
     specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
-    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
                        leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
     bt = B.Batch(ctx, specs, opts)
     Xs = [torch.from_numpy(inputs.rhs(cfg["seed"] + 1 + b, s.n, cfg["nrhs"])).to(dev) for b, s in enumerate(specs)]
@@ -498,11 +508,11 @@ def run_batched(args):
     entries = float(sum(x.shape[0] * y.shape[0] for (x, y, _) in blocks))
     # the batched arm: leaf cluster size from the autotuner, the call captured
     # into a CUDA graph on its first (warm-up) run and replayed afterwards
-    opts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
                        leaf_rank_cap=cfg["leaf_rank_cap"])
     batch = B.Batch(ctx, specs, opts)
     tuned_cluster, tuned_ms = batch.autotune()
-    batch.opts.flags = B.FLAG_GRAPH
+    batch.opts.flags = B.FLAG_GRAPH | EXTRA_FLAGS
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 1)):
@@ -523,13 +533,13 @@ def run_batched(args):
     ms = float(np.mean(step_ms))
     # phase split and launch count from one profiled (uncaptured) call
     pctx = B.Context()
-    pb = B.Batch(pctx, specs, B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+    pb = B.Batch(pctx, specs, mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
                                           leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE,
                                           cluster=tuned_cluster), ws=batch.ws)
     pb.run()
     (tb, tr, tm, tt), launches = B.phase_times(pctx)
     # the plain loop: one compress per block, shared workspace and outputs
-    lopts = B.make_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+    lopts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
                         leaf_rank_cap=cfg["leaf_rank_cap"])
     wsz = max(B.workspace_size(s.gen, lopts) for s in specs)
     lws = torch.empty(wsz, dtype=torch.uint8, device=dev)
@@ -576,9 +586,11 @@ def run_batched(args):
 
 
 def main():
-    global WORKLOAD
+    global WORKLOAD, EXTRA_FLAGS
     args = parse()
     WORKLOAD = WORKLOADS[args.workload]
+    if args.single_cluster:
+        EXTRA_FLAGS = 16  # HBACA_FLAG_SINGLE_CLUSTER
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.workload == "grad16384":

@@ -116,6 +116,14 @@ typedef struct hbaca_gen {
                                   calls between replays.  New data in the same buffers is
                                   allowed: results are exact, only the launch shapes were
                                   chosen for the first call's ranks. */
+#define HBACA_FLAG_SINGLE_CLUSTER 16u  /* one thread-block cluster per matrix in the QR and Q
+                                  application of every merge stage.  By default a stage
+                                  with few matrices spreads each over several clusters
+                                  that exchange partial sums through global memory and
+                                  wait for one another (a cooperative launch keeps them
+                                  resident; waits are bounded, HBACA_TIMEOUT on expiry).
+                                  This flag is for tools that serialise or re-launch
+                                  kernels (profilers), which cannot keep them resident. */
 
 /* Options of one compression (Alg. 3 inputs n_b, d, eps). */
 typedef struct hbaca_opts {

@@ -18,6 +18,7 @@ FLAG_ASYNC = 1
 FLAG_PROFILE = 2
 FLAG_TAPE = 4
 FLAG_GRAPH = 8
+FLAG_SINGLE_CLUSTER = 16
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
           5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE"}
 STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}

@@ -162,6 +162,7 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
     ctx->launches = 0;
   } else {
     hbaca::RunCtx rc{ws, st, ctx->sms, &outs[0], 0};
+    rc.xgroups = (opts->flags & HBACA_FLAG_SINGLE_CLUSTER) == 0;
     rc.sizes_known = (opts->flags & HBACA_FLAG_ASYNC) == 0;
     std::vector<hbaca::JacobiLaunch> recipe;
     if (graph) rc.record = &recipe;
@@ -204,6 +205,7 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
       }
       cudaStream_t cs = ctx->cap_stream;
       hbaca::RunCtx rg{ws, cs, ctx->sms, &outs[0], 0};
+      rg.xgroups = (opts->flags & HBACA_FLAG_SINGLE_CLUSTER) == 0;
       rg.replay = &recipe;
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
@@ -297,6 +299,7 @@ hbaca_status hbaca_autotune_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca
     double ms = -1.0;
     for (int rep = 0; rep < 2; ++rep) {  // the second run is timed (the first warms up)
       hbaca::RunCtx rc{ws, st, ctx->sms, nullptr, 0};
+      rc.xgroups = (opts->flags & HBACA_FLAG_SINGLE_CLUSTER) == 0;
       rc.baca_only = true;
       cudaError_t e = cudaMemsetAsync(ws + p.status.off, 0, p.status.bytes, st);
       if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.queue.off, 0, p.queue.bytes, st);

@@ -303,6 +303,7 @@ enum DevStatus : int {
   DS_RANK_CAPACITY = 2,
   DS_TIMEOUT = 4,
   DS_NUMERICAL = 6,
+  DS_LAUNCH = 8,  // a kernel found a launch shape other than the planned one
 };
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
 

@@ -29,6 +29,9 @@ namespace cg = cooperative_groups;
 namespace hbaca {
 
 constexpr int kDenseThreads = 256;
+// one CTA per task with a serial column loop (pivoted QR of the core): the
+// widest block hides more of the latency of the per-column reductions
+constexpr int kWideThreads = 1024;
 
 
 
@@ -186,10 +189,13 @@ __device__ __forceinline__ int xgroup_arrive_wait(unsigned* cnt, unsigned target
   }
 }
 
-// Inter-cluster arguments: G clusters per matrix, slot stride xplen elements.
+// Launch shape (cluster size csize, njobs matrices, G clusters per matrix)
+// and the inter-cluster exchange (slot stride xplen elements).
 template <typename T>
 struct XGroup {
   int G;
+  int csize;
+  int njobs;
   int xplen;
   T* xpart;       // [cluster of the grid][2][xplen]
   unsigned* xcnt; // [matrix of the launch]
@@ -214,6 +220,10 @@ __global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> 
   const int G = X.G;
   const int cid = blockIdx.x / c;
   const int job = cid / G, g = cid - job * G;
+  if (c != X.csize || job >= X.njobs) {  // not the planned launch shape: touch nothing
+    if (threadIdx.x == 0) set_status(P.status, DS_LAUNCH);
+    return;
+  }
   const QrJob jb = jobs[job];
   const SvdTask t = P.tasks[jb.task];
   const TaskDims dm = P.dims[jb.task];
@@ -403,7 +413,7 @@ __device__ __forceinline__ double block_sum_dense(double v, double* scratch) {
 // reflector tails; perm (nc ints) lists the pivot order followed by the
 // unchosen columns; X = R2^H is written to the x_off region.  One CTA per task.
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads) qrcp_core_kernel(const DenseParams<T> P) {
+__global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DenseParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ti = blockIdx.x;
   const SvdTask t = P.tasks[ti];
@@ -918,7 +928,7 @@ __global__ void __launch_bounds__(kDenseThreads) wsolve_kernel(const DenseParams
   __syncthreads();
   // one classical Gram-Schmidt pass in the sorted order (the columns are
   // orthonormal up to ~eps_mach / eps, so one pass suffices)
-  __shared__ double red[kDenseThreads / 32];
+  __shared__ double red[32];
   __shared__ T dd[kMaxWsolveCols];
   for (int tc = 0; tc < s; ++tc) {
     T* wt = W + (int64_t)ord[tc] * ld;
@@ -1010,6 +1020,10 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   const int G = X.G;
   const int cid = blockIdx.x / c;
   const int job = cid / G, g = cid - job * G;
+  if (c != X.csize || job >= X.njobs) {  // not the planned launch shape: touch nothing
+    if (threadIdx.x == 0) set_status(P.status, DS_LAUNCH);
+    return;
+  }
   const QJob jb = jobs[job];
   const SvdTask t = P.tasks[jb.task];
   const TaskDims dm = P.dims[jb.task];

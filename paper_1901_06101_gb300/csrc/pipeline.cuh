@@ -223,14 +223,16 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   const size_t qr_smem = (size_t)(3 * (2 + 2 * sg.kcap) + 4) * sizeof(T);
   const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
   const size_t qa_smem = 3 * qa_cols * sizeof(T) + 64;
-  XGroup<T> X{1, p.xplen, reinterpret_cast<T*>(ws + p.xpart.off), reinterpret_cast<unsigned*>(ws + p.xcnt.off)};
-  if (cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
+  XGroup<T> X{1, cq, sg.nqr, p.xplen, reinterpret_cast<T*>(ws + p.xpart.off),
+              reinterpret_cast<unsigned*>(ws + p.xcnt.off)};
+  if (rc.xgroups && cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
     const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
                              resident_clusters(qapply_kernel<T>, 8, qa_smem, rc.st));
     const int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
     if (G > 1) {
       cq = 8;
       X.G = G;
+      X.csize = cq;
     }
   }
   const bool coop = X.G > 1;
@@ -239,7 +241,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   HB_TIMED(KC_CORE, core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   const size_t qc_smem = (size_t)sg.kcap * 9 + 2 * sizeof(T) + 32 * 12 + 64 + 16;
   HB_TRY(cudaFuncSetAttribute(qrcp_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qc_smem));
-  HB_TIMED(KC_QRCP, qrcp_core_kernel<T><<<nt, kDenseThreads, qc_smem, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+  HB_TIMED(KC_QRCP, qrcp_core_kernel<T><<<nt, kWideThreads, qc_smem, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   if (rc.replay) {
     // captured call: the launch shapes a synchronous call chose (task lists
     // already in the workspace); kernels still check every task's sizes
@@ -264,20 +266,46 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       const size_t per_cta = (pairs + (size_t)cc * 8 - 1) / ((size_t)cc * 8) * 8;
       return j_base + per_cta * kJSlotMax;
     };
-    // cluster size c = 1..16: the round's pairs in one pass over the cluster's warps
+    // cluster size c = 1..16.  Preferred: the round's pairs in one pass over
+    // the cluster's warps, when every cluster of that group can be resident at
+    // once; otherwise the largest power of two with at least one pair per warp
+    // (a stage with many cores is bound by the FP64 rate, not by the rounds).
     std::vector<std::vector<int32_t>> groups(17);
     std::vector<size_t> need(17, 0);
     const std::vector<SvdTask>& th = *sg.tasks_h;
     const int wpc = kDenseThreads / 32;
-    for (int i = 0; i < nt; ++i) {
+    std::vector<int> c_one(nt), c_pow(nt);
+    auto share_of = [&](int i, int cc) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int nc = std::min(dh[i].kra, ncm), mr = ncm;
-      int g = std::min(16, std::max(1, ((nc + 1) / 2 + wpc - 1) / wpc));
-      auto share = [&](int cc) { return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + nc) * sizeof(T); };
-      while (g < 16 && share(g) + j_hdr_of(g) > kJacobiSmemLimit) ++g;
-      groups[g].push_back(i);
-      const size_t sh = share(g) + j_hdr_of(g) <= kJacobiSmemLimit ? share(g) : 0;
-      need[g] = std::max(need[g], sh);
+      return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + nc) * sizeof(T);
+    };
+    auto fit = [&](int i, int cc) {
+      while (cc < 16 && share_of(i, cc) + j_hdr_of(cc) > kJacobiSmemLimit) ++cc;
+      return cc;
+    };
+    auto add_task = [&](int i, int cc) {
+      groups[cc].push_back(i);
+      const size_t sh = share_of(i, cc) + j_hdr_of(cc) <= kJacobiSmemLimit ? share_of(i, cc) : 0;
+      need[cc] = std::max(need[cc], sh);
+    };
+    for (int i = 0; i < nt; ++i) {
+      const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
+      const int pairs = (std::min(dh[i].kra, ncm) + 1) / 2;
+      int g = 0;
+      while (g < 4 && (1 << (g + 1)) * wpc <= pairs) ++g;
+      c_pow[i] = fit(i, 1 << g);
+      c_one[i] = fit(i, std::min(16, std::max(1, (pairs + wpc - 1) / wpc)));
+      add_task(i, c_one[i]);
+    }
+    for (int cc = 1; cc <= 16; ++cc) {
+      if (groups[cc].empty()) continue;
+      const int res = resident_clusters(jacobi_kernel<T>, cc, j_hdr_of(cc) + need[cc], rc.st);
+      if ((int)groups[cc].size() <= res) continue;
+      std::vector<int32_t> moved;
+      moved.swap(groups[cc]);
+      need[cc] = 0;
+      for (int32_t i : moved) add_task(i, c_pow[i]);
     }
     size_t off = sg.jlist_off;
     for (int g = 1; g <= 16; ++g) {
@@ -307,6 +335,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   if (!p.tape) HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
   rc.launches += 2;
+  X.njobs = sg.nq;
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
   HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
   rc.launches += 5;

@@ -62,6 +62,7 @@ struct RunCtx {
   std::vector<JacobiLaunch>* record = nullptr;       // sized launches are appended here
   const std::vector<JacobiLaunch>* replay = nullptr;  // capture: launch these shapes, no host sync
   bool baca_only = false;                             // autotuning: the leaf BACA launch alone
+  bool xgroups = true;  // QR / Q application may spread a matrix over several clusters
 };
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);

@@ -253,3 +253,24 @@ def test_cfg3_sparse_50000_sampled_leaves(ctx):
     res, compared, div, tr = run_and_compare(ctx, spec, og_, 5, 32, 1e-8, seed=2, rank_cap=1024, leaf_cap=512,
                                              check_all_leaves=False)
     print("cfg3: rank %d, max leaf BACA rank %d" % (res.rank, res.res.leaf_rank_max))
+
+
+def test_single_cluster_flag_agrees_with_cluster_groups(ctx):
+    """The root stage of a 2000^2 problem with 2 levels spreads its QR and Q
+    application over several clusters; with HBACA_FLAG_SINGLE_CLUSTER it
+    uses one.  Both are the same Householder factorisation summed in another
+    order: ranks equal, singular values and the product equal to rounding."""
+    x, y = inputs.gaussian_pair(seed=0, m=2000, n=2000)
+    spec = B.gaussian(x, y, 1.0)
+    outs = []
+    for flags in (0, B.FLAG_SINGLE_CLUSTER):
+        opts = B.make_opts(1e-6, 8, 2, seed=0, rank_cap=128, leaf_rank_cap=256, flags=flags)
+        res = B.compress(ctx, spec, opts)
+        torch.cuda.synchronize()
+        outs.append((res.rank, res.U.cpu().numpy(), res.S.cpu().numpy(), res.V.cpu().numpy()))
+    (r0, U0, S0, V0), (r1, U1, S1, V1) = outs
+    assert r0 == r1
+    np.testing.assert_allclose(S0, S1, rtol=0, atol=1e-12 * S0[0])
+    A0 = (U0 * S0[None, :]) @ V0
+    A1 = (U1 * S1[None, :]) @ V1
+    assert np.linalg.norm(A0 - A1) <= 1e-11 * np.linalg.norm(A0)
