@@ -541,6 +541,7 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, doub
 }
 
 constexpr int kJacRegs = 8;  // columns of up to 256 rows are held in registers
+constexpr int kJacKeep = 5;  // columns of up to 160 rows stay in registers from (1) to (3)
 
 // Loads of the Jacobi sweeps: columns in another CTA's shared memory are read
 // with plain (distributed shared memory) loads, columns in global memory
@@ -584,7 +585,7 @@ struct JPair {
   T ga;
   double cs, sn;
   T sp, cp;
-  int ok, pad;
+  int ok, a, b, pad;  // a, b: the pair's columns
 };
 constexpr int kJSlotMax = 96;  // bytes reserved per pair slot (>= sizeof(JPair<cplx>))
 
@@ -599,20 +600,19 @@ template <typename T, bool kDsm>
 __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
                               T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
                               int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot,
-                              bool acc_w) {
+                              bool acc_w, T* const* ctab) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  auto colX = [&](int j) -> T* {
-    if constexpr (kDsm) return cl.map_shared_rank(dsm, j % c) + (int64_t)(j / c) * ldc;
-    else return M + (int64_t)j * ld;
-  };
+  // column addresses from the table (no division by the cluster size per access)
+  auto colX = [&](int j) -> T* { return ctab[j]; };
   auto colW = [&](int j) -> T* {
-    if constexpr (kDsm) return colX(j) + mr;
+    if constexpr (kDsm) return ctab[j] + mr;
     else return Y + (int64_t)j * ld;
   };
   const int npairs = K / 2;
   const int stride = c * nw;                             // pairs dealt per pass over the cluster's warps
   const int per_warp = (npairs + stride - 1) / stride;   // passes (pairs per warp) per round
   const bool regs = mr <= 32 * kJacRegs;
+  const bool keep = mr <= 32 * kJacKeep;
   auto pair_of = [&](int rd, int pi, int& a, int& b) {
     // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
     if (pi == 0) { a = rd; b = K - 1; }
@@ -626,7 +626,9 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; }
     __syncthreads();
     for (int rd = 0; rd < K - 1; ++rd) {
-      // (1) inner products of this warp's pairs
+      // (1) inner products of this warp's pairs; the first pass keeps its
+      // two columns in registers for (3)
+      T ka[kJacKeep], kb[kJacKeep];
       for (int j = 0; j < per_warp; ++j) {
         const int pi = j * stride + q * nw + warp;
         int a = 0, b = 0;
@@ -650,6 +652,10 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
                 al += abs2(xa);
                 be += abs2(xb);
                 ga = cmac(ga, xa, xb);
+                if (u < kJacKeep && j == 0) {
+                  ka[u < kJacKeep ? u : 0] = xa;
+                  kb[u < kJacKeep ? u : 0] = xb;
+                }
               }
             }
           } else {
@@ -671,6 +677,8 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
           sl.be = be;
           sl.ga = ga;
           sl.ok = act ? 1 : 0;
+          sl.a = a;
+          sl.b = b;
         }
       }
       __syncthreads();
@@ -694,17 +702,28 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
       for (int j = 0; j < per_warp; ++j) {
         const JPair<T>& sl = slots[j * nw + warp];
         if (!sl.ok) continue;  // warp-uniform
-        const int pi = j * stride + q * nw + warp;
-        int a, b;
-        pair_of(rd, pi, a, b);
+        const int a = sl.a, b = sl.b;
         const double cs = sl.cs, sn = sl.sn;
         const T spv = sl.sp, cpv = sl.cp;
         if (lane == 0 && fmax(sl.al, sl.be) >= tau2) flag[fb & 1] = 1;
         ++nrot;
-        rotate_pair_t<T, kDsm>(colX(a), colX(b), mr, cs, sn, spv, cpv, lane);
+        T* ca = colX(a);
+        T* cb = colX(b);
+        if (keep && j == 0) {
+#pragma unroll
+          for (int u = 0; u < kJacKeep; ++u) {
+            const int i = lane + 32 * u;
+            if (32 * u < mr && i < mr) {
+              rot_elem(ka[u], kb[u], cs, sn, spv, cpv);
+              ca[i] = ka[u];
+              cb[i] = kb[u];
+            }
+          }
+        } else {
+          rotate_pair_t<T, kDsm>(ca, cb, mr, cs, sn, spv, cpv, lane);
+        }
         if (acc_w) rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
       }
-      __syncthreads();
       cl.sync();
     }
     // the largest column norm^2 of this sweep, over the cluster (for the next tau)
@@ -809,12 +828,19 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   if (tid == 0) { flag[0] = 0; flag[1] = 0; }
   cl.sync();
   JPair<T>* slots = reinterpret_cast<JPair<T>*>(smem_raw + slot_off);
+  // column addresses of X for the sweeps, in the singular-value area (free
+  // until the epilogue): column j in CTA j mod c (DSMEM) or in global memory
+  T** ctab = reinterpret_cast<T**>(sv);
+  for (int j = tid; j < nc; j += blockDim.x)
+    ctab[j] = use_dsm ? cl.map_shared_rank(dsm, j % c) + (int64_t)(j / c) * ldc : M + (int64_t)j * ld;
+  __syncthreads();
   if (use_dsm)
     jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
-                           slots, sweep, nrot, acc_w);
+                           slots, sweep, nrot, acc_w, ctab);
   else
     jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
-                            cmx, slots, sweep, nrot, acc_w);
+                            cmx, slots, sweep, nrot, acc_w, ctab);
+  __syncthreads();
   if (use_dsm) {  // the sweeps' result back to global memory for the epilogue and finish_kernel
     for (int l = warp; l < per; l += nw) {
       const int j = l * c + q;
