@@ -66,7 +66,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA 
 # DRAM bytes (read + write) per launch of the current kernels on the default
 # workload, averaged over one compression's launches (ncu dram__bytes_read.sum
 # + dram__bytes_write.sum); None where no capture of the current kernel exists
-TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 13.76e6}}
+TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 13.78e6}}
 
 
 EXTRA_FLAGS = 0  # option flags added to every call (--single-cluster)
@@ -128,6 +128,22 @@ def jacobi_accounting(ws, plan, complex_, accumulates=False):
             nsw = min(int(sweeps) + 1, 40)
             total += nsw * nc * (nc - 1) / 2 * mr * fd + float(rot) * (mr + (nc if accumulates else 0)) * fr
     return total
+
+
+def jacobi_stage_stats(ws, plan):
+    """Per stage of one compression: tasks, mean core columns and the mean and
+    largest number of Jacobi sweeps (from the per-task records)."""
+    import torch
+    out = []
+    for st in plan["stages"]:
+        nt = st["ntasks"]
+        d = ws[st["dims"]: st["dims"] + 32 * nt].view(torch.int32).view(nt, 8).cpu().numpy()
+        ncm = d[:, 2] if st["kind"] == 0 else d[:, 0]
+        nc = np.minimum(d[:, 1], ncm)
+        sw = np.minimum(d[:, 4] + 1, 40)
+        out.append({"tasks": int(nt), "cols": round(float(nc.mean()), 1), "sweeps_mean": round(float(sw.mean()), 2),
+                    "sweeps_max": int(sw.max())})
+    return out
 
 
 def leaf_accounting(traces, leaf_sizes, d, complex_):
@@ -359,7 +375,9 @@ def run_ours(args, rank, world):
     res = B.compress(ctx, spec, opts, ws=ws, out=out)
     torch.cuda.synchronize(dev)
     ktimes = B.kernel_times(ctx)
-    jac_flops = jacobi_accounting(ws, B.plan_json(spec, opts), True)
+    plan = B.plan_json(spec, opts)
+    jac_flops = jacobi_accounting(ws, plan, True)
+    jac_stages = jacobi_stage_stats(ws, plan)
     probe = B.fp64_probe()
     peak_note = ("FP64 peak derived from 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz; live probe DFMA %.3f, "
                  "DMMA %.3f TFLOP/s" % probe)
@@ -377,6 +395,7 @@ def run_ours(args, rank, world):
     roof = dict(roof, dominant_kernel=dominant)
     return dict(value=value, ms=ms_max, entries=entries, flops=flops, rank=rank, phases=phases, roof=roof,
                 roof_baca=roofs["baca_leaf_kernel"], kernel_ms={k: v[0] for k, v in ktimes.items()},
+                jacobi_stages=jac_stages,
                 launches=launches, clocks=clk.summary(), wall=wall, e2e=dict(value=e2e_value, unit="entries/s",
                 h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, seconds_per_step=e2e_s), x=x, y=y)
 
@@ -648,7 +667,7 @@ def main():
             "roofline": r["roof"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
             "clocks": r["clocks"], "phases_ms": r["phases"], "rank": r["rank"],
             "roofline_leaf_baca": r["roof_baca"], "kernel_ms": r["kernel_ms"],
-            "entries_per_step": r["entries"]}
+            "jacobi_stages": r["jacobi_stages"], "entries_per_step": r["entries"]}
     print(json.dumps(line))
 
 
