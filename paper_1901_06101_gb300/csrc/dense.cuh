@@ -411,33 +411,54 @@ __device__ __forceinline__ double block_sum_dense(double v, double* scratch) {
 // graded matrix X = R2^H (nc x p), which converges in a few sweeps.
 // M (mr x nc) is overwritten by R2 (column perm[t] holds R2(0..t, t)) and the
 // reflector tails; perm (nc ints) lists the pivot order followed by the
-// unchosen columns; X = R2^H is written to the x_off region.  One CTA per task.
+// unchosen columns; X = R2^H is written to the x_off region.  One cluster per
+// task, column j owned by CTA j mod c: per step every CTA forms the norms of
+// its columns and a local argmax, the cluster argmax is taken in rank order
+// through DSMEM (ties to the smaller index, identical in every CTA), the
+// owner of the pivot column builds the reflector, every CTA copies it to
+// shared memory after a cluster barrier and updates its own columns.
+struct QcArg {
+  long long b;
+  int i, pad;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DenseParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ti = blockIdx.x;
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
+  const int ti = blockIdx.x / c;
+  if (ti >= P.ntasks) return;  // uniform per cluster
   const SvdTask t = P.tasks[ti];
   const TaskDims dm = P.dims[ti];
   const int mr = dm.kra;
   const int nc = t.kind == TASK_LEAF ? dm.krb : dm.k;
   const int ld = t.kcap;
-  if (mr <= 0 || nc <= 0) return;
+  if (mr <= 0 || nc <= 0) return;  // uniform per cluster
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   T* M = P.core + t.m_off;
   T* X = P.core + t.x_off;
   T* tau = P.tau + t.tau_off + 2 * t.kcap;
   int32_t* perm = P.ord + t.ord_off + t.kcap;
-  double* nrm = reinterpret_cast<double*>(smem_raw);            // nc
-  T* coef = reinterpret_cast<T*>(nrm + nc + (nc & 1));           // [0] conj(tau)
-  long long* wb = reinterpret_cast<long long*>(coef + 2);        // 32
+  // shared memory: [rv: kcap T][coef: 2 T][slots: 2 QcArg][nrm: kcap double]
+  //                [wb: 32 ll][wi: 32 int][sh: 4 int][sperm: kcap int][chosen: kcap bytes]
+  T* rv = reinterpret_cast<T*>(smem_raw);                        // reflector u (rows st..mr-1)
+  T* coef = rv + t.kcap;                                         // [0] conj(tau), [1] beta (re)
+  QcArg* aslot = reinterpret_cast<QcArg*>(coef + 2);             // argmax slots (step parity)
+  double* nrm = reinterpret_cast<double*>(aslot + 2);            // this CTA's column norms
+  long long* wb = reinterpret_cast<long long*>(nrm + t.kcap);    // 32
   int* wi = reinterpret_cast<int*>(wb + 32);                     // 32
   int* sh = wi + 32;                                             // [0] pivot
-  uint8_t* chosen = reinterpret_cast<uint8_t*>(sh + 4);          // nc
+  int* sperm = sh + 4;                                           // pivot order (every CTA)
+  uint8_t* chosen = reinterpret_cast<uint8_t*>(sperm + t.kcap);  // nc
   for (int j = tid; j < nc; j += blockDim.x) chosen[j] = 0;
   __syncthreads();
   const int p = min(mr, nc);
+  const int own = (nc - q + c - 1) / c;  // columns q, q + c, ...
   for (int st = 0; st < p; ++st) {
-    for (int j = warp; j < nc; j += nw) {
+    // norms of this CTA's unchosen columns, local argmax
+    for (int l = warp; l < own; l += nw) {
+      const int j = q + l * c;
       if (chosen[j]) continue;
       double a = 0.0;
       for (int i = st + lane; i < mr; i += 32) a += abs2(M[(int64_t)j * ld + i]);
@@ -447,8 +468,10 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
     __syncthreads();
     long long bb = -1;
     int bi = INT_MAX;
-    for (int j = tid; j < nc; j += blockDim.x)
+    for (int l = tid; l < own; l += blockDim.x) {
+      const int j = q + l * c;
       if (!chosen[j]) argmax_merge(bb, bi, nbits(nrm[j]), j);
+    }
     warp_argmax(bb, bi);
     if (lane == 0) { wb[warp] = bb; wi[warp] = bi; }
     __syncthreads();
@@ -456,53 +479,75 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
       bb = lane < nw ? wb[lane] : -1;
       bi = lane < nw ? wi[lane] : INT_MAX;
       warp_argmax(bb, bi);
-      if (lane == 0) { sh[0] = bi; perm[st] = bi; chosen[bi] = 1; }
+      if (lane == 0) { aslot[st & 1].b = bb; aslot[st & 1].i = bi; }
+    }
+    cl.sync();
+    if (tid == 0) {  // cluster argmax in rank order
+      long long gb = -1;
+      int gi = INT_MAX;
+      for (int r = 0; r < c; ++r) {
+        const QcArg* rs = cl.map_shared_rank(aslot + (st & 1), r);
+        argmax_merge(gb, gi, rs->b, rs->i);
+      }
+      sh[0] = gi;
+      chosen[gi] = 1;
+      sperm[st] = gi;
     }
     __syncthreads();
-    T* col = M + (int64_t)sh[0] * ld;
-    if (warp == 0) {
+    const int pc = sh[0];
+    T* col = M + (int64_t)pc * ld;
+    const int owner = pc % c;
+    if (q == owner && warp == 0) {
+      const T alpha = col[st];  // read by every lane before lane 0 overwrites it
       double sig2 = 0.0;
       for (int i = st + 1 + lane; i < mr; i += 32) sig2 += abs2(col[i]);
       sig2 = warp_sum(sig2);
+      double beta;
+      T tu, sc;
+      householder(alpha, sig2, beta, tu, sc);  // every lane: the same value
+      for (int i = st + 1 + lane; i < mr; i += 32) col[i] = mul(col[i], sc);
       if (lane == 0) {
-        double beta;
-        T tu, sc;
-        householder(col[st], sig2, beta, tu, sc);
         coef[0] = conj_(tu);
-        coef[1] = sc;
+        coef[1] = from_re<T>(beta);
         tau[st] = tu;
         col[st] = from_re<T>(beta);
       }
-      __syncwarp();
-      const T sc = coef[1];
-      for (int i = st + 1 + lane; i < mr; i += 32) col[i] = mul(col[i], sc);
     }
+    cl.sync();
+    // the reflector u = [1; col(st+1:)] and conj(tau) from the owner
+    for (int i = st + 1 + tid; i < mr; i += blockDim.x) rv[i] = ldcg(col + i);
+    const T ctau = *cl.map_shared_rank(coef, owner);
     __syncthreads();
-    const T ctau = coef[0];
-    for (int j = warp; j < nc; j += nw) {
+    for (int l = warp; l < own; l += nw) {
+      const int j = q + l * c;
       if (chosen[j]) continue;
       T* y = M + (int64_t)j * ld;
       T w = Traits<T>::zero();
-      for (int i = st + 1 + lane; i < mr; i += 32) w = cmac(w, col[i], y[i]);
+      for (int i = st + 1 + lane; i < mr; i += 32) w = cmac(w, rv[i], y[i]);
       w = warp_sum(w);
       w = add(w, y[st]);
       const T f = mul(ctau, w);
       if (lane == 0) y[st] = sub(y[st], f);
-      for (int i = st + 1 + lane; i < mr; i += 32) y[i] = msub(y[i], col[i], f);
+      for (int i = st + 1 + lane; i < mr; i += 32) y[i] = msub(y[i], rv[i], f);
     }
-    __syncthreads();
+    // the owner may overwrite coef only after every CTA has read it
+    cl.sync();
   }
   if (tid == 0) {  // unchosen columns (nc > mr) follow in index order
-    int q = p;
+    int qq = p;
     for (int j = 0; j < nc; ++j)
-      if (!chosen[j]) perm[q++] = j;
+      if (!chosen[j]) sperm[qq++] = j;
   }
   __syncthreads();
-  // X = R2^H: X(j, i) = conj(R2(i, j)) = conj(M(i, perm[j])) for i <= j, i < p
-  for (int e = tid; e < nc * p; e += blockDim.x) {
-    const int j = e % nc, i = e / nc;
-    X[(int64_t)i * ld + j] = i <= j ? conj_(M[(int64_t)perm[j] * ld + i]) : Traits<T>::zero();
+  if (q == 0)
+    for (int j = tid; j < nc; j += blockDim.x) perm[j] = sperm[j];
+  // X = R2^H: X(j, i) = conj(R2(i, j)) = conj(M(i, perm[j])) for i <= j, i < p;
+  // CTA q writes the rows j = q, q + c, ... (columns of other CTAs read through L2)
+  for (int e = tid; e < own * p; e += blockDim.x) {
+    const int j = q + (e % own) * c, i = e / own;
+    X[(int64_t)i * ld + j] = i <= j ? conj_(ldcg(M + (int64_t)sperm[j] * ld + i)) : Traits<T>::zero();
   }
+  cl.sync();
 }
 
 // ------------------------------------------------------------------ Jacobi SVD

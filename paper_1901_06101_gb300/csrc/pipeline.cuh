@@ -35,7 +35,7 @@ constexpr size_t kJacobiSmemLimit = 220 * 1024;  // dynamic shared memory of one
 
 template <typename K>
 cudaError_t cluster_config(K kern, int grid, int cluster, size_t smem, cudaStream_t st, bool coop,
-                           cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
+                           cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int threads = kDenseThreads) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
@@ -44,7 +44,7 @@ cudaError_t cluster_config(K kern, int grid, int cluster, size_t smem, cudaStrea
   }
   cfg = cudaLaunchConfig_t{};
   cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(kDenseThreads, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -239,9 +239,17 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
   HB_TIMED(KC_QR, HB_TRY(launch_cluster_x(qr_kernel<T>, sg.nqr * X.G * cq, cq, qr_smem, rc.st, coop, D, qj, X)));
   HB_TIMED(KC_CORE, core_kernel<T><<<dim3(16, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
-  const size_t qc_smem = (size_t)sg.kcap * 9 + 2 * sizeof(T) + 32 * 12 + 64 + 16;
-  HB_TRY(cudaFuncSetAttribute(qrcp_core_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qc_smem));
-  HB_TIMED(KC_QRCP, qrcp_core_kernel<T><<<nt, kWideThreads, qc_smem, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+  // pivoted QR of the cores: up to 8 CTAs per core while the stage leaves SMs idle
+  const size_t qc_smem = (size_t)sg.kcap * (sizeof(T) + 8 + 4 + 1) + 2 * sizeof(T) + 2 * sizeof(QcArg) + 32 * 12 +
+                         16 + 64;
+  int cqc = 1;
+  while (cqc < 8 && nt * cqc * 2 <= rc.sms) cqc *= 2;
+  {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    HB_TRY(cluster_config(qrcp_core_kernel<T>, nt * cqc, cqc, qc_smem, rc.st, false, cfg, attr, kWideThreads));
+    HB_TIMED(KC_QRCP, HB_TRY(cudaLaunchKernelEx(&cfg, qrcp_core_kernel<T>, D)));
+  }
   if (rc.replay) {
     // captured call: the launch shapes a synchronous call chose (task lists
     // already in the workspace); kernels still check every task's sizes
