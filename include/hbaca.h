@@ -314,8 +314,10 @@ hbaca_status hbaca_phase_times(hbaca_ctx* ctx, double ms[4], int32_t* launches);
    call's stream).  Classes, in order: leaf BACA (Alg. 2), QR-operand
    packing, Householder QR, core product, pivoted QR of the core, Jacobi SVD
    of the core, singular vectors of the core, reflector application,
-   block-diagonal product, root copy (taped calls).  ms[c] is the summed
-   duration, launches[c] the number of launches.  Synchronises on the events. */
+   block-diagonal product, root copy (taped calls).  ms[c] is the time during
+   which at least one launch of class c ran (launches of a class that run
+   concurrently on two streams count once), launches[c] the number of
+   launches.  Synchronises on the events. */
 #define HBACA_KERNEL_CLASSES 10
 hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES], int32_t launches[HBACA_KERNEL_CLASSES]);
 

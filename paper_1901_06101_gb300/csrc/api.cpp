@@ -26,6 +26,9 @@ struct hbaca_ctx {
   std::vector<char> gkey;
   hbaca::Plan gplan;
   cudaStream_t cap_stream;  // captures run on this stream (the legacy default stream cannot be captured)
+  // concurrent Jacobi launch groups of one stage (created on first use)
+  cudaStream_t aux_stream;
+  cudaEvent_t fork_ev, join_ev;
 };
 
 namespace {
@@ -47,6 +50,21 @@ int current_sms() {
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 152; }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); return 152; }
   return sms > 0 ? sms : 152;
+}
+
+// The auxiliary stream and its fork / join events (created once per context).
+cudaError_t ensure_aux(hbaca_ctx* ctx) {
+  cudaError_t e = cudaSuccess;
+  if (!ctx->aux_stream) e = cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->fork_ev) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->join_ev) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+  return e;
+}
+
+void use_aux(hbaca_ctx* ctx, hbaca::RunCtx& rc) {
+  rc.aux = ctx->aux_stream;
+  rc.fork_ev = ctx->fork_ev;
+  rc.join_ev = ctx->join_ev;
 }
 
 hbaca_status map_device_status(int ds) {
@@ -98,6 +116,9 @@ hbaca_status hbaca_destroy(hbaca_ctx* ctx) {
       if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   }
   delete ctx;
   return HBACA_OK;
@@ -164,6 +185,9 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
     hbaca::RunCtx rc{ws, st, ctx->sms, &outs[0], 0};
     rc.xgroups = (opts->flags & HBACA_FLAG_SINGLE_CLUSTER) == 0;
     rc.sizes_known = (opts->flags & HBACA_FLAG_ASYNC) == 0;
+    e = ensure_aux(ctx);
+    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("auxiliary stream: ") + cudaGetErrorString(e));
+    use_aux(ctx, rc);
     std::vector<hbaca::JacobiLaunch> recipe;
     if (graph) rc.record = &recipe;
     const bool prof = (opts->flags & HBACA_FLAG_PROFILE) != 0 && !graph;
@@ -206,6 +230,7 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
       cudaStream_t cs = ctx->cap_stream;
       hbaca::RunCtx rg{ws, cs, ctx->sms, &outs[0], 0};
       rg.xgroups = (opts->flags & HBACA_FLAG_SINGLE_CLUSTER) == 0;
+      use_aux(ctx, rg);
       rg.replay = &recipe;
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
@@ -473,14 +498,34 @@ hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES],
     launches[i] = 0;
   }
   cudaError_t e = cudaEventSynchronize(ctx->ev[3]);
+  // launch intervals on the call's clock (from the start event); launches of
+  // one class that overlap (concurrent streams) count once: the class time is
+  // the length of the union of its intervals
+  std::vector<std::vector<std::pair<float, float>>> iv(HBACA_KERNEL_CLASSES);
   for (const auto& mk : ctx->kt.marks) {
     if (e != cudaSuccess) break;
-    float t = 0.f;
-    e = cudaEventElapsedTime(&t, ctx->kt.pool[mk.second], ctx->kt.pool[mk.second + 1]);
-    if (mk.first >= 0 && mk.first < HBACA_KERNEL_CLASSES) {
-      ms[mk.first] += t;
+    float t0 = 0.f, t1 = 0.f;
+    e = cudaEventElapsedTime(&t0, ctx->ev[0], ctx->kt.pool[mk.second]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ctx->ev[0], ctx->kt.pool[mk.second + 1]);
+    if (e == cudaSuccess && mk.first >= 0 && mk.first < HBACA_KERNEL_CLASSES) {
+      iv[mk.first].emplace_back(t0, t1);
       launches[mk.first] += 1;
     }
+  }
+  for (int c = 0; c < HBACA_KERNEL_CLASSES; ++c) {
+    std::sort(iv[c].begin(), iv[c].end());
+    double tot = 0.0, a = 0.0, b = -1.0;
+    for (const auto& x : iv[c]) {
+      if (x.first > b) {
+        if (b > a) tot += b - a;
+        a = x.first;
+        b = x.second;
+      } else if (x.second > b) {
+        b = x.second;
+      }
+    }
+    if (b > a) tot += b - a;
+    ms[c] = tot;
   }
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("event timing: ") + cudaGetErrorString(e));
   tls_err.clear();

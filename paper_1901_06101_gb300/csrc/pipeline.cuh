@@ -250,15 +250,41 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     HB_TRY(cluster_config(qrcp_core_kernel<T>, nt * cqc, cqc, qc_smem, rc.st, false, cfg, attr, kWideThreads));
     HB_TIMED(KC_QRCP, HB_TRY(cudaLaunchKernelEx(&cfg, qrcp_core_kernel<T>, D)));
   }
+  // a stage's Jacobi launches: the largest (by CTAs) on the call's stream, the
+  // others concurrently on the auxiliary stream (fork after the task lists
+  // are in place, join before the next kernel)
+  auto jacobi_group_launches = [&](const std::vector<JacobiLaunch>& ls) -> cudaError_t {
+    size_t main_i = 0;
+    for (size_t i = 1; i < ls.size(); ++i)
+      if ((int64_t)ls[i].count * ls[i].cluster > (int64_t)ls[main_i].count * ls[main_i].cluster) main_i = i;
+    const bool fork = rc.aux && rc.fork_ev && rc.join_ev && ls.size() > 1;
+    if (fork) {
+      HB_TRY(cudaEventRecord(rc.fork_ev, rc.st));
+      HB_TRY(cudaStreamWaitEvent(rc.aux, rc.fork_ev, 0));
+    }
+    rc.launches += (int)ls.size();
+    for (size_t i = 0; i < ls.size(); ++i) {
+      const JacobiLaunch& jl = ls[i];
+      cudaStream_t s2 = (fork && i != main_i) ? rc.aux : rc.st;
+      const int32_t* lst = reinterpret_cast<const int32_t*>(ws + p.jlist.off) + jl.list_off;
+      if (rc.kt) HB_TRY(rc.kt->begin(KC_JACOBI, s2));
+      HB_TRY(launch_cluster(jacobi_kernel<T>, jl.count * jl.cluster, jl.cluster, jl.hdr + jl.dsm, s2, D, 40, (int)jl.hdr,
+                            (int)jl.base, (int64_t)jl.dsm, lst));
+      if (rc.kt) HB_TRY(rc.kt->end(s2));
+    }
+    if (fork) {
+      HB_TRY(cudaEventRecord(rc.join_ev, rc.aux));
+      HB_TRY(cudaStreamWaitEvent(rc.st, rc.join_ev, 0));
+    }
+    return cudaSuccess;
+  };
   if (rc.replay) {
     // captured call: the launch shapes a synchronous call chose (task lists
     // already in the workspace); kernels still check every task's sizes
-    for (const JacobiLaunch& jl : *rc.replay) {
-      if (jl.stage != si) continue;
-      const int32_t* lst = reinterpret_cast<const int32_t*>(ws + p.jlist.off) + jl.list_off;
-      HB_TRY(launch_cluster(jacobi_kernel<T>, jl.count * jl.cluster, jl.cluster, jl.hdr + jl.dsm, rc.st, D, 40,
-                            (int)jl.hdr, (int)jl.base, (int64_t)jl.dsm, lst));
-    }
+    std::vector<JacobiLaunch> ls;
+    for (const JacobiLaunch& jl : *rc.replay)
+      if (jl.stage == si) ls.push_back(jl);
+    HB_TRY(jacobi_group_launches(ls));
   } else if (rc.sizes_known) {
     // the cores' sizes are known: group the tasks by the cluster size that
     // gives each warp about one pair per round, with exactly the shared memory
@@ -316,18 +342,16 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       for (int32_t i : moved) add_task(i, c_pow[i]);
     }
     size_t off = sg.jlist_off;
+    std::vector<JacobiLaunch> ls;
     for (int g = 1; g <= 16; ++g) {
       if (groups[g].empty()) continue;
       int32_t* lst = reinterpret_cast<int32_t*>(ws + p.jlist.off) + off;
       HB_TRY(cudaMemcpyAsync(lst, groups[g].data(), groups[g].size() * 4, cudaMemcpyHostToDevice, rc.st));
-      const int cg_ = g;
-      const size_t j_hdr = j_hdr_of(cg_);
-      HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, (int)groups[g].size() * cg_, cg_, j_hdr + need[g],
-                                                rc.st, D, 40, (int)j_hdr, (int)j_base, (int64_t)need[g],
-                                                (const int32_t*)lst)));
-      if (rc.record) rc.record->push_back(JacobiLaunch{si, cg_, (int)groups[g].size(), j_hdr, j_base, need[g], off});
+      ls.push_back(JacobiLaunch{si, g, (int)groups[g].size(), j_hdr_of(g), j_base, need[g], off});
       off += groups[g].size();
     }
+    HB_TRY(jacobi_group_launches(ls));
+    if (rc.record) rc.record->insert(rc.record->end(), ls.begin(), ls.end());
   } else {
     const int cj = pick_cluster(nt, sg.kcap, rc.sms, 16);
     // header (flags, singular values, order, pair slots) then, up to the
@@ -339,14 +363,18 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     const size_t j_dsm = std::min(j_cap, (size_t)kJacobiSmemLimit - j_hdr);
     HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, 40, (int)j_hdr,
                                               (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr)));
+    ++rc.launches;
   }
-  if (!p.tape) HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+  if (!p.tape) {
+    HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+    ++rc.launches;
+  }
   HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
-  rc.launches += 2;
+  ++rc.launches;
   X.njobs = sg.nq;
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
   HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
-  rc.launches += 5;
+  rc.launches += 5;  // pack, QR, core, pivoted QR of the core, Q application
   if (sg.kind != TASK_LEAF) {
     HB_TIMED(KC_BLOCKPROD, blockprod_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
     ++rc.launches;

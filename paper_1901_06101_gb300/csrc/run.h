@@ -63,6 +63,10 @@ struct RunCtx {
   const std::vector<JacobiLaunch>* replay = nullptr;  // capture: launch these shapes, no host sync
   bool baca_only = false;                             // autotuning: the leaf BACA launch alone
   bool xgroups = true;  // QR / Q application may spread a matrix over several clusters
+  // auxiliary stream and fork / join events: a stage's smaller Jacobi launch
+  // groups run on `aux` concurrently with its largest one (null: one stream)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);
