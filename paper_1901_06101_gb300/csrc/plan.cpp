@@ -190,11 +190,25 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
     return (int64_t)leaves[x].m * leaves[x].n > (int64_t)leaves[y].m * leaves[y].n;
   });
 
-  // ---- BACA cluster size: enough CTAs to cover the SMs, shared memory within budget
+  // ---- BACA cluster size.  The persistent clusters (about sms / c of them)
+  // take the leaves in ceil(leaves / clusters) rounds of a leaf time that
+  // falls as 1 / c (the leaf work is FP64-bound and split over the cluster's
+  // SMs): pick the c in 1, 2, 4, 8 with the fewest rounds / c, ties to the
+  // smaller, at least 16 rows per CTA; shared memory within budget.
   int c = o.cluster;
   if (c == 0) {
     c = 1;
-    while (c < 8 && (int64_t)p.nleaves * c < 2 * sms && (p.mmax + c * 2 - 1) / (c * 2) >= 16) c *= 2;
+    const int64_t s_eff = std::max(sms, 1);
+    double best = 1e300;
+    for (int cc = 1; cc <= 8; cc *= 2) {
+      if (cc > 1 && (p.mmax + cc - 1) / cc < 16) break;
+      const int64_t clusters = std::max<int64_t>(1, s_eff / cc);
+      const double cost = (double)((p.nleaves + clusters - 1) / clusters) / cc;
+      if (cost < best * (1.0 - 1e-9)) {
+        best = cost;
+        c = cc;
+      }
+    }
   }
   while (baca_smem(p.esz, (p.mmax + c - 1) / c, (p.nmax + c - 1) / c, p.d) > 200 * 1024 && c < 16) c *= 2;
   p.baca_cluster = c;
