@@ -43,7 +43,8 @@ typedef enum hbaca_status {
   HBACA_INVALID_ARG = 1,    /* a NULL pointer, a size out of range, an unknown kind */
   HBACA_RANK_CAPACITY = 2,  /* a leaf or merged rank exceeded its capacity */
   HBACA_CUDA = 3,           /* a CUDA runtime call failed (message has the detail) */
-  HBACA_TIMEOUT = 4,        /* a bounded device-side wait expired */
+  HBACA_TIMEOUT = 4,        /* a bounded device-side wait expired (the inter-cluster wait of
+                               the QR / Q application, 4 s; see HBACA_FLAG_SINGLE_CLUSTER) */
   HBACA_NO_TAPE = 5,        /* backward called on a result without a recorded tape */
   HBACA_NUMERICAL = 6,      /* NaN or Inf in a norm, a pivot or a singular value */
   HBACA_WORKSPACE = 7       /* workspace too small or misaligned (256-byte alignment) */

@@ -293,6 +293,10 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
   if (hs != HBACA_OK) {
     const char* what = hs == HBACA_RANK_CAPACITY ? "a rank exceeded rank_cap or leaf_rank_cap"
                        : hs == HBACA_NUMERICAL   ? "NaN or Inf in a norm or a singular value"
+                       : hs == HBACA_TIMEOUT     ? "the clusters of a QR / Q application did not meet within 4 s "
+                                                   "(not resident together; HBACA_FLAG_SINGLE_CLUSTER avoids the wait)"
+                       : status == 8             ? "a QR / Q-application kernel ran with another launch shape than "
+                                                   "planned (nothing was touched)"
                                                  : "device-side failure";
     return fail(hs, what);
   }

@@ -101,3 +101,17 @@ def test_workspace_size_and_argument_checks(lib):
 def test_library_has_no_torch_dependency(lib):
     out = subprocess.run(["ldd", B.LIB_PATH], capture_output=True, text=True).stdout
     assert "torch" not in out and "c10" not in out
+
+
+def test_flag_and_status_constants_match_the_header():
+    """Every HBACA_FLAG_* the header defines has the same value in the
+    binding, and the status codes the binding maps agree with the enum."""
+    src = open(os.path.join(ROOT, "include", "hbaca.h")).read()
+    flags = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define HBACA_FLAG_([A-Z_]+) (\d+)u", src)}
+    assert {"ASYNC", "PROFILE", "TAPE", "GRAPH", "SINGLE_CLUSTER"} <= set(flags)
+    for name, v in flags.items():
+        assert getattr(B, "FLAG_" + name) == v, name
+    assert len(set(flags.values())) == len(flags)
+    assert all(v & (v - 1) == 0 for v in flags.values())  # one bit each
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"HBACA_([A-Z_]+) = (\d+),?", src)}
+    assert codes["TIMEOUT"] == 4 and codes["RANK_CAPACITY"] == 2 and codes["NUMERICAL"] == 6
