@@ -163,3 +163,24 @@ def test_autotune_returns_a_cluster_size_with_valid_results(ctx):
         sv = np.linalg.svd(A, compute_uv=False)
         e_opt = np.linalg.norm(sv[ol.eps_rank(sv, 1e-8):]) / np.linalg.norm(sv)
         assert err <= 2 * max(1e-8, e_opt), (err, e_opt)
+
+
+def test_graph_replay_of_a_single_block_with_cluster_groups(ctx):
+    """HBACA_FLAG_GRAPH on one 2000^2 block at L = 2: the root stage spreads
+    its QR and Q application over several clusters (a cooperative launch and
+    counter resets inside the graph) and stages with several Jacobi groups fork
+    a second stream; every replay equals the plain call bit for bit."""
+    x, y = inputs.gaussian_pair(seed=0, m=2000, n=2000)
+    spec = B.gaussian(x, y, 1.0)
+    plain = B.make_opts(1e-6, 8, 2, seed=0, rank_cap=128, leaf_rank_cap=256)
+    ref = B.compress(ctx, spec, plain)
+    torch.cuda.synchronize()
+    gopts = B.make_opts(1e-6, 8, 2, seed=0, rank_cap=128, leaf_rank_cap=256, flags=B.FLAG_GRAPH)
+    gctx = B.Context()
+    ws = torch.empty(B.workspace_size(spec.gen, gopts), dtype=torch.uint8, device="cuda")
+    first = B.compress(gctx, spec, gopts, ws=ws)
+    torch.cuda.synchronize()
+    for r in [first] + [B.compress(gctx, spec, gopts, ws=ws, out=first.buffers) for _ in range(3)]:
+        torch.cuda.synchronize()
+        assert r.rank == ref.rank
+        assert torch.equal(r.S, ref.S) and torch.equal(r.U, ref.U) and torch.equal(r.V, ref.V)
