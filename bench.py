@@ -106,6 +106,25 @@ def leaf_spans(n, L):
     return spans
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(v, world, device="cpu"):
+    """The largest value of one float over all ranks: the slowest replica sets
+    the job's time.  device: where the reduction tensor lives (a CUDA device
+    for NCCL, "cpu" for gloo)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_max, world):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank, timed by the slowest of them (weak scaling)."""
+    return world * units_per_rank / seconds_max
+
+
 def jacobi_accounting(ws, plan, complex_, accumulates=False):
     """Algorithmic FP64 flops of the Jacobi SVD launches of one compression,
     from the per-task records the kernel leaves (sizes, sweeps, rotations):
@@ -331,12 +350,8 @@ def run_ours(args, rank, world):
         wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
-    ms = float(np.mean(step_ms))
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * entries / (ms_max / 1e3)
+    ms_max = max_over_ranks(float(np.mean(step_ms)), world, dev)
+    value = job_throughput(entries, ms_max / 1e3, world)
 
     # end to end through the C ABI with host buffers: pinned inputs -> device,
     # compress, factors -> pinned host, every step
@@ -365,8 +380,8 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize(dev)
         h2d = xh.numel() * 8 + yh.numel() * 8
         d2h = k * (cfg["m"] + cfg["n"]) * 16 + k * 8
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = world * entries / e2e_s
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    e2e_value = job_throughput(entries, e2e_s, world)
 
     # per-kernel device times of the last timed compression (CUDA events around
     # every launch on the call's stream) and the roofline of the dominant one
