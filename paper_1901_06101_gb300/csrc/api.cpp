@@ -549,6 +549,8 @@ size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char*
   reg("uar", p.uar); reg("var", p.var); reg("qr", p.qr); reg("tau", p.tau); reg("core", p.core); reg("ord", p.ord);
   reg("full_u", p.full_u); reg("full_s", p.full_s); reg("full_v", p.full_v);
   reg("half_u", p.half_u); reg("half_s", p.half_s); reg("half_v", p.half_v);
+  reg("cscr", p.cscr); reg("rscr", p.rscr); reg("gscr", p.gscr); reg("tape_int", p.tape_int);
+  reg("tape_dbl", p.tape_dbl); reg("jlist", p.jlist); reg("xpart", p.xpart); reg("xcnt", p.xcnt);
   j += "\"leafout\": " + std::to_string(p.leafout_off) + ", \"leafdesc\": " + std::to_string(p.leafdesc_off) + ", ";
   j += "\"baca_cluster\": " + std::to_string(p.baca_cluster) + ", \"rank_cap\": " + std::to_string(p.rank_cap_max) + ", ";
   j += "\"stages\": [";

@@ -1,0 +1,62 @@
+"""Host-side planning (no GPU): the workspace regions of a plan are disjoint
+and inside the total, and the leaf BACA cluster size follows the rounds rule
+(persistent clusters of c CTAs take the leaves in ceil(leaves / (SMs / c))
+rounds of a leaf time that falls as 1 / c; ties to the smaller c).  The
+planner assumes 152 SMs when no device is present."""
+import numpy as np
+import pytest
+
+from paper_1901_06101_gb300 import binding as B
+
+REGIONS = ["status", "queue", "desc", "uar", "var", "qr", "tau", "core", "ord", "full_u", "full_s", "full_v",
+           "half_u", "half_s", "half_v", "cscr", "rscr", "gscr", "tape_int", "tape_dbl", "jlist", "xpart", "xcnt"]
+
+
+def _plan(m, n, L, d=16, cluster=0, cplx=True, flags=0):
+    kind, dt = (B.GEN_HELMHOLTZ, B.C128) if cplx else (B.GEN_GAUSSIAN, B.F64)
+    # the planner never dereferences the point arrays: any non-null address will do
+    g = B.Gen(kind=kind, dtype=dt, m=m, n=n, x=4096, y=8192, dim=3, k=4 * np.pi, h=1.0)
+    spec = B.GenSpec(g, ())
+    opts = B.make_opts(1e-4, d, L, seed=1, rank_cap=256, leaf_rank_cap=256, cluster=cluster, flags=flags)
+    return B.plan_json(spec, opts)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    if not os.path.exists(B.LIB_PATH):
+        pytest.skip("libhbaca.so not built")
+
+
+@pytest.mark.parametrize("flags", [0, B.FLAG_TAPE])
+def test_regions_disjoint_and_inside_the_workspace(flags):
+    j = _plan(20000, 20000, 4, flags=flags)
+    spans = sorted((j[r][0], j[r][0] + max(j[r][1], 1), r) for r in REGIONS)
+    for (a0, a1, ra), (b0, b1, rb) in zip(spans, spans[1:]):
+        assert a1 <= b0, (ra, rb)
+    assert spans[-1][1] <= j["total"]
+    assert all(j[r][0] % 256 == 0 for r in REGIONS)
+
+
+def rounds_rule(leaves, mmax, sms=152):
+    best, pick = None, 1
+    for c in (1, 2, 4, 8):
+        if c > 1 and -(-mmax // c) < 16:
+            break
+        clusters = max(1, sms // c)
+        cost = -(-leaves // clusters) / c
+        if best is None or cost < best * (1 - 1e-9):
+            best, pick = cost, c
+    return pick
+
+
+@pytest.mark.parametrize("m,L,expect", [(20000, 4, 4), (2000, 2, 8), (50000, 5, 4), (40000, 6, 1)])
+def test_baca_cluster_follows_the_rounds_rule(m, L, expect):
+    j = _plan(m, m, L)
+    leaves, mmax = 4 ** L, -(-m // 2 ** L)
+    assert rounds_rule(leaves, mmax) == expect
+    assert j["baca_cluster"] == expect
+
+
+def test_explicit_cluster_size_is_kept():
+    assert _plan(20000, 20000, 4, cluster=2)["baca_cluster"] == 2
