@@ -557,17 +557,6 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
 // accumulating the same rotation in Y.  The pairs of one round are spread over
 // all warps of all CTAs in the cluster; a cluster barrier separates rounds.
 // At the end singular values are column norms, sorted descending; s = eps-rank.
-template <typename T>
-__device__ __forceinline__ void rotate_pair(T* a, T* b, int len, double cs, double sn, T ph, int lane) {
-  // a' = c a - s ph b ; b' = s a + c ph b     (ph = e^{-i phi})
-  for (int i = lane; i < len; i += 32) {
-    const T ai = ldcg(a + i);
-    const T bi = mul(ph, ldcg(b + i));
-    a[i] = sub(scale(ai, cs), scale(bi, sn));
-    b[i] = add(scale(ai, sn), scale(bi, cs));
-  }
-}
-
 // Rotation of one Jacobi pair from alpha = |a|^2, beta = |b|^2, gamma = a^H b.
 // Returns false when the pair counts as orthogonal: |gamma| below tol times
 // |a| |b|, or both columns negligible, or a column in the denormal range.
