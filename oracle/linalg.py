@@ -93,19 +93,17 @@ def greedy_qrcp(M, kmax, candidates=None, rank_tol=None, abs_noise=0.0, forced=N
         piv.append(j)
         diag.append(best)
         cand[j] = False
-        # new basis direction: the normalised residual, orthogonalised once more
-        # against the basis.  In pivot selection (no rank_tol) a residual at the
-        # noise floor, or one that was mostly inside span(Q), adds no direction;
-        # QR(W, eps) keeps every pivot its rank rule accepts (T_tt != 0).
+        # new basis direction: the normalised residual of the chosen column
+        # (Q spans the chosen columns, the Q factor of QR(A, r) in Sec. 2),
+        # orthogonalised once more against the basis; a residual that is
+        # exactly zero adds a zero column (the chosen column is already in
+        # span(Q) and T_tt = 0)
         q = np.zeros(p, dtype=Q.dtype)
-        if best > (0.0 if rank_tol is not None else noise):
+        if best > 0.0:
             q = R[:, b] / best
             q = q - Q @ (Q.conj().T @ q)
             nq = np.linalg.norm(q)
-            if rank_tol is not None or nq >= 0.5:
-                q = q / nq
-            else:
-                q = np.zeros(p, dtype=Q.dtype)
+            q = q / nq if nq > 0.0 else np.zeros(p, dtype=Q.dtype)
         Q = np.concatenate([Q, q[:, None]], axis=1)
     if forced is not None:
         return piv, diag, margins, Q, valid  # invalid steps hold (step, best, forced, noise)

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 import scipy.linalg
 
+from oracle import apply as oapply
 from oracle import baca as ob
 from oracle import hbaca as oh
 from oracle import linalg as ol
@@ -60,3 +61,36 @@ def test_recompress_with_dropped_conjugate(monkeypatch):
         return Qu @ X, s, Yh @ Qv.T
     monkeypatch.setattr(ob, "recompress", bad)
     _expect_failure(pins.test_product_of_random_exact_rank, True)
+
+
+def test_qrcp_noise_residual_adds_no_direction(monkeypatch):
+    """A basis that skips chosen columns whose residual is at the rounding
+    level no longer spans the chosen columns."""
+    orig = ol.greedy_qrcp
+
+    def bad(M, kmax, **kw):
+        out = orig(M, kmax, **kw)
+        piv, diag, marg, Q = out[:4]
+        Q = Q.copy()
+        for t, dv in enumerate(diag):
+            if dv < 1e-12 * diag[0]:
+                Q[:, t] = 0.0
+        return (piv, diag, marg, Q) + tuple(out[4:])
+    monkeypatch.setattr(ol, "greedy_qrcp", bad)
+    _expect_failure(pins.test_greedy_qrcp_basis_spans_the_chosen_columns)
+
+
+def test_rel_error_without_square_root(monkeypatch):
+    orig = oapply.rel_error_dense
+    monkeypatch.setattr(oapply, "rel_error_dense", lambda *a, **k: orig(*a, **k) ** 2)
+    _expect_failure(pins.test_rel_error_dense_against_direct_norm)
+
+
+def test_rel_error_last_chunk_dropped(monkeypatch):
+    def bad(gen, U, s, V, row_chunk=2048, rows=None):
+        allrows = np.arange(gen.m) if rows is None else np.asarray(rows)
+        keep = allrows[: max(row_chunk, (allrows.size // row_chunk) * row_chunk)]
+        A = gen(keep, np.arange(gen.n))
+        return float(np.linalg.norm(A - (U[keep] * s) @ V) / np.linalg.norm(A))
+    monkeypatch.setattr(oapply, "rel_error_dense", bad)
+    _expect_failure(pins.test_rel_error_dense_against_direct_norm)

@@ -123,6 +123,28 @@ def test_greedy_qrcp_candidates_and_rank_tol():
     assert piv == []
 
 
+def test_greedy_qrcp_basis_spans_the_chosen_columns():
+    """Q is the orthonormal factor of the chosen columns (QR(A, r), Sec. 2):
+    M(:, piv) = Q T with T upper triangular and Q^H Q = I, also past the
+    numerical rank, where the chosen residuals are at the rounding level but
+    not zero (a rank-3 matrix, 6 pivots)."""
+    U, V = inputs.lowrank(9, 8, 30, 3)
+    M = U @ V
+    piv, diag, marg, Q = ol.greedy_qrcp(M, 6)
+    assert len(piv) == 6
+    assert min(diag[3:]) > 0.0 and max(diag[3:]) < 1e-12 * diag[0]
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(6), atol=1e-12)
+    T = Q.conj().T @ M[:, piv]
+    assert np.abs(np.tril(T, -1)).max() < 1e-12 * np.abs(M).max()
+    np.testing.assert_allclose(np.abs(np.diag(T)), diag, rtol=1e-6, atol=1e-14 * diag[0])
+    np.testing.assert_allclose(Q @ T, M[:, piv], atol=1e-13 * np.abs(M).max())
+    # an exactly zero column adds a zero direction (T_tt = 0)
+    Z = np.zeros((4, 5))
+    Z[:, 0] = [1.0, 2.0, 0.0, 0.0]
+    piv, diag, _, Q = ol.greedy_qrcp(Z, 3)
+    assert piv[0] == 0 and diag[1] == 0.0 and np.all(Q[:, 1:] == 0.0)
+
+
 def test_eps_rank_definition():
     assert ol.eps_rank([1.0, 0.5, 1e-7], 1e-6) == 2
     assert ol.eps_rank([2.0, 2e-6, 1e-7], 1e-6) == 2  # Sigma_{k+1} < eps Sigma_1 is strict
@@ -343,6 +365,26 @@ def test_hbaca_complex_helmholtz_small():
     A = g(np.arange(g.m), np.arange(g.n))
     sv = np.linalg.svd(A, compute_uv=False)
     assert res["r"] >= int(np.sum(sv > np.linalg.norm(A - (res["U"] * res["s"]) @ res["V"], 2)))
+
+
+def test_rel_error_dense_against_direct_norm():
+    """The chunked error evaluator equals ||A - U S V||_F / ||A||_F formed
+    directly (row chunks smaller than m, so the chunk loop runs several
+    times), on all rows and on a sample of rows."""
+    rng = np.random.default_rng(4)
+    x, y = inputs.gaussian_pair(seed=3, m=257, n=131)
+    g = og.Gaussian(x, y, 0.9)
+    A = g(np.arange(g.m), np.arange(g.n))
+    Uf, sf, Vf = np.linalg.svd(A, full_matrices=False)
+    U, s, V = Uf[:, :6], sf[:6] * (1 + 1e-3 * rng.standard_normal(6)), Vf[:6]
+    want = np.linalg.norm(A - (U * s) @ V) / np.linalg.norm(A)
+    assert abs(oapply.rel_error_dense(g, U, s, V, row_chunk=50) - want) <= 1e-13 * want
+    I = np.sort(rng.choice(g.m, 40, replace=False))
+    want_I = np.linalg.norm(A[I] - (U[I] * s) @ V) / np.linalg.norm(A[I])
+    assert abs(oapply.rel_error_dense(g, U, s, V, row_chunk=16, rows=I) - want_I) <= 1e-13 * want_I
+    # a closed form: U S V = truncated SVD gives the tail of the singular values
+    tail = np.sqrt(np.sum(sf[6:] ** 2) / np.sum(sf ** 2))
+    assert abs(oapply.rel_error_dense(g, Uf[:, :6], sf[:6], Vf[:6], row_chunk=64) - tail) <= 1e-12
 
 
 # ---------------------------------------------------------------- frozen-pivot replay
