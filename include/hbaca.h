@@ -47,7 +47,10 @@ typedef enum hbaca_status {
                                the QR / Q application, 4 s; see HBACA_FLAG_SINGLE_CLUSTER) */
   HBACA_NO_TAPE = 5,        /* backward called on a result without a recorded tape */
   HBACA_NUMERICAL = 6,      /* NaN or Inf in a norm, a pivot or a singular value */
-  HBACA_WORKSPACE = 7       /* workspace too small or misaligned (256-byte alignment) */
+  HBACA_WORKSPACE = 7,      /* workspace too small or misaligned (256-byte alignment) */
+  HBACA_NOT_CONVERGED = 8   /* the one-sided Jacobi SVD of a re-compression or merge core
+                               (Sec. 2, SVD(A, eps)) reached its sweep cap (40) while still
+                               rotating: singular values and eps-ranks are unreliable */
 } hbaca_status;
 
 /* Entry generators: A(i, j) computable in O(1) (abstract; Sec. 5 kernels). */
@@ -194,13 +197,21 @@ hbaca_status hbaca_compress_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca
    all belongs to another runtime's pool, or a latency-bound caller that must
    not allocate per call.  The area is HBACA_NOALLOC_WORKSPACE_BYTES per
    device; a problem whose hbaca_workspace_size exceeds it is rejected with
-   HBACA_WORKSPACE before anything is enqueued.  The first call on a device
-   (with that device current) looks up the area's address; make that first
-   call before any stream capture.  No device memory is allocated or freed.
-   All calls on one device share the area, so calls that overlap in time
-   (other threads, or other streams with work still pending) race on it:
-   serialise them.  Results, ranks and status are as for hbaca_compress; the
-   leaf records in the area are overwritten by the next call. */
+   HBACA_WORKSPACE before anything is enqueued.  Every call looks up the
+   area's address on the current device (cudaGetSymbolAddress, no stale
+   address after a device reset); the first call on a device loads the
+   module there, so make it before any stream capture.  The current device
+   must be the context's (HBACA_INVALID_ARG otherwise).  HBACA_FLAG_GRAPH
+   and HBACA_FLAG_TAPE are rejected with HBACA_INVALID_ARG: a graph replay
+   would read descriptor tables that a later call on the shared area has
+   replaced, and a tape in the area cannot be handed to
+   hbaca_apply_backward, which needs its workspace pointer.  With
+   HBACA_FLAG_ASYNC the rank is delivered through result.d_rank only.  No
+   device memory is allocated or freed.  All calls on one device share the
+   area, so calls that overlap in time (other threads, or other streams
+   with work still pending) race on it: serialise them.  Results, ranks
+   and status are as for hbaca_compress; the leaf records in the area are
+   overwritten by the next call. */
 #define HBACA_NOALLOC_WORKSPACE_BYTES (64u << 20)
 hbaca_status hbaca_compress_noalloc(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_opts* opts,
                                     hbaca_result* out, void* stream);

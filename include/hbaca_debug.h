@@ -46,6 +46,13 @@ hbaca_status hbaca_debug_fp64_probe(double* dfma_tflops, double* dmma_tflops);
 int64_t hbaca_debug_backward_json(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
                                   char* buf, int64_t len, void* stream);
 
+/* Sweep cap of the one-sided Jacobi SVD (Sec. 2, SVD(A, eps)) used by every
+   later call in this process: sweeps > 0 sets it, 0 restores the default
+   (40).  Returns the cap in force before the call.  For tests that make a
+   core stop short of convergence (the call then returns
+   HBACA_NOT_CONVERGED). */
+int32_t hbaca_debug_set_jacobi_sweeps(int32_t sweeps);
+
 #ifdef __cplusplus
 }
 #endif

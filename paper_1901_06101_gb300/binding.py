@@ -20,7 +20,7 @@ FLAG_TAPE = 4
 FLAG_GRAPH = 8
 FLAG_SINGLE_CLUSTER = 16
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
-          5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE"}
+          5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE", 8: "NOT_CONVERGED"}
 STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}
 
 
@@ -124,6 +124,7 @@ SIGNATURES = [
     ("hbaca_phase_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]),
     ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_last_error", ctypes.c_char_p, []),
     ("hbaca_version", ctypes.c_char_p, []),
 ]
@@ -267,6 +268,22 @@ def sparse_product(sp):
     return GenSpec(g, tuple(t))
 
 
+def _host_rank(res, opts):
+    """The rank a synchronous call returned on the host.  HBACA_FLAG_ASYNC
+    calls leave it at -1 (the rank goes to a device int); these helpers
+    slice the factors by the rank, so they refuse that flag."""
+    r = int(res.rank)
+    if r < 0:
+        raise HbacaError(1, "no host rank (HBACA_FLAG_ASYNC): these helpers need a synchronous call")
+    return r
+
+
+def set_jacobi_sweeps(n):
+    """hbaca_debug_set_jacobi_sweeps: Jacobi sweep cap of later calls (0 =
+    default); returns the previous cap."""
+    return int(lib().hbaca_debug_set_jacobi_sweeps(int(n)))
+
+
 class Compressed:
     """Output of compress(): U (m x r), S (r), V (r x n) as torch views, plus the
     workspace (which holds the leaf tapes)."""
@@ -295,7 +312,7 @@ def compress(ctx, spec, opts, stream=None, ws=None, out=None):
         stream = torch.cuda.current_stream().cuda_stream
     check(lib().hbaca_compress(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.byref(res),
                                ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(stream)))
-    r = int(res.rank)
+    r = _host_rank(res, opts)
     c = Compressed(Ut[:r].T, S[:r], V[:r], r, ws, res)
     c.buffers = (Ut, S, V)
     return c
@@ -317,7 +334,7 @@ def compress_noalloc(ctx, spec, opts, stream=None, out=None):
         stream = torch.cuda.current_stream().cuda_stream
     check(lib().hbaca_compress_noalloc(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.byref(res),
                                        ctypes.c_void_p(stream)))
-    r = int(res.rank)
+    r = _host_rank(res, opts)
     c = Compressed(Ut[:r].T, S[:r], V[:r], r, None, res)
     c.buffers = out
     return c

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -73,14 +74,20 @@ hbaca_status map_device_status(int ds) {
     case 2: return HBACA_RANK_CAPACITY;
     case 4: return HBACA_TIMEOUT;
     case 6: return HBACA_NUMERICAL;
+    case 10: return HBACA_NOT_CONVERGED;
     default: return HBACA_CUDA;
   }
 }
+
+constexpr int kDefaultJacobiSweeps = 40;
+std::atomic<int> g_jacobi_sweeps{kDefaultJacobiSweeps};
 
 }  // namespace
 
 namespace hbaca {
 hbaca_status record_error(hbaca_status s, const std::string& msg) { return fail(s, msg); }
+int ctx_device(const hbaca_ctx* ctx) { return ctx->device; }
+int jacobi_max_sweeps() { return g_jacobi_sweeps.load(std::memory_order_relaxed); }
 }  // namespace hbaca
 
 extern "C" {
@@ -145,6 +152,16 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
     if (!outs[b].U || !outs[b].S || !outs[b].V) return fail(HBACA_INVALID_ARG, "result U, S and V must be set");
     if (outs[b].ldu < gens[b].m || outs[b].ldv < gens[b].n)
       return fail(HBACA_INVALID_ARG, "result needs ldu >= m and ldv >= n");
+  }
+  {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HBACA_CUDA, "cudaGetDevice failed");
+    }
+    if (cur != ctx->device)
+      return fail(HBACA_INVALID_ARG, "the current device (" + std::to_string(cur) + ") is not the context's (" +
+                                         std::to_string(ctx->device) + ")");
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* ws = reinterpret_cast<char*>(workspace);
@@ -295,6 +312,8 @@ static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca
                        : hs == HBACA_NUMERICAL   ? "NaN or Inf in a norm or a singular value"
                        : hs == HBACA_TIMEOUT     ? "the clusters of a QR / Q application did not meet within 4 s "
                                                    "(not resident together; HBACA_FLAG_SINGLE_CLUSTER avoids the wait)"
+                       : hs == HBACA_NOT_CONVERGED ? "a Jacobi SVD of a re-compression or merge core reached its "
+                                                     "sweep cap while still rotating"
                        : status == 8             ? "a QR / Q-application kernel ran with another launch shape than "
                                                    "planned (nothing was touched)"
                                                  : "device-side failure";
@@ -534,6 +553,11 @@ hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES],
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("event timing: ") + cudaGetErrorString(e));
   tls_err.clear();
   return HBACA_OK;
+}
+
+int32_t hbaca_debug_set_jacobi_sweeps(int32_t sweeps) {
+  const int v = sweeps > 0 ? sweeps : kDefaultJacobiSweeps;
+  return g_jacobi_sweeps.exchange(v);
 }
 
 size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char* buf, size_t len) {

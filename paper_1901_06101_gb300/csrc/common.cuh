@@ -304,6 +304,7 @@ enum DevStatus : int {
   DS_TIMEOUT = 4,
   DS_NUMERICAL = 6,
   DS_LAUNCH = 8,  // a kernel found a launch shape other than the planned one
+  DS_NOT_CONVERGED = 10,  // a Jacobi SVD reached its sweep cap still rotating
 };
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
 

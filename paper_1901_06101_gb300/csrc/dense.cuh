@@ -874,6 +874,11 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   else
     jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
                             cmx, slots, sweep, nrot, acc_w, ctab);
+  // the sweep cap was reached while relevant rotations were still being
+  // applied: the singular values and the eps-rank come from an unconverged
+  // SVD, which the call reports (the loop leaves through its convergence
+  // test before the cap otherwise)
+  if (K > 1 && sweep >= max_sweeps && q == 0 && tid == 0) set_status(P.status, DS_NOT_CONVERGED);
   __syncthreads();
   if (use_dsm) {  // the sweeps' result back to global memory for the epilogue and finish_kernel
     for (int l = warp; l < per; l += nw) {

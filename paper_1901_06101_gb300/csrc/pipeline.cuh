@@ -268,7 +268,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       cudaStream_t s2 = (fork && i != main_i) ? rc.aux : rc.st;
       const int32_t* lst = reinterpret_cast<const int32_t*>(ws + p.jlist.off) + jl.list_off;
       if (rc.kt) HB_TRY(rc.kt->begin(KC_JACOBI, s2));
-      HB_TRY(launch_cluster(jacobi_kernel<T>, jl.count * jl.cluster, jl.cluster, jl.hdr + jl.dsm, s2, D, 40, (int)jl.hdr,
+      HB_TRY(launch_cluster(jacobi_kernel<T>, jl.count * jl.cluster, jl.cluster, jl.hdr + jl.dsm, s2, D, jacobi_max_sweeps(), (int)jl.hdr,
                             (int)jl.base, (int64_t)jl.dsm, lst));
       if (rc.kt) HB_TRY(rc.kt->end(s2));
     }
@@ -361,7 +361,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     const size_t j_hdr = j_base + (((size_t)sg.kcap + 1) / 2 + (size_t)cj * 8 - 1) / ((size_t)cj * 8) * 8 * kJSlotMax;
     const size_t j_cap = ((size_t)sg.kcap + cj - 1) / cj * 2 * (size_t)sg.kcap * sizeof(T);
     const size_t j_dsm = std::min(j_cap, (size_t)kJacobiSmemLimit - j_hdr);
-    HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, 40, (int)j_hdr,
+    HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, jacobi_max_sweeps(), (int)j_hdr,
                                               (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr)));
     ++rc.launches;
   }

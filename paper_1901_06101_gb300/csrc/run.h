@@ -72,4 +72,8 @@ cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err);
 cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err);
 // Set the calling thread's hbaca_last_error() message; returns s.
 hbaca_status record_error(hbaca_status s, const std::string& msg);
+// Device ordinal a context was created on.
+int ctx_device(const hbaca_ctx* ctx);
+// Sweep cap of the one-sided Jacobi SVD launches (hbaca_debug_set_jacobi_sweeps).
+int jacobi_max_sweeps();
 }  // namespace hbaca

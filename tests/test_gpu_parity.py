@@ -274,3 +274,22 @@ def test_single_cluster_flag_agrees_with_cluster_groups(ctx):
     A0 = (U0 * S0[None, :]) @ V0
     A1 = (U1 * S1[None, :]) @ V1
     assert np.linalg.norm(A0 - A1) <= 1e-11 * np.linalg.norm(A0)
+
+
+def test_jacobi_sweep_cap_reports_not_converged(ctx):
+    """With the sweep cap of the core SVDs lowered to one sweep the cores are
+    still rotating when the cap is reached: the call reports
+    HBACA_NOT_CONVERGED instead of returning an unconverged SVD as OK; with
+    the default cap the same call succeeds."""
+    x, y = inputs.gaussian_pair(seed=0, m=900, n=800)
+    spec = B.gaussian(x, y, 1.0)
+    opts = B.make_opts(1e-8, 8, 1, seed=0, rank_cap=256, leaf_rank_cap=256)
+    prev = B.set_jacobi_sweeps(1)
+    try:
+        with pytest.raises(B.HbacaError) as ei:
+            B.compress(ctx, spec, opts)
+        assert ei.value.code == 8
+    finally:
+        B.set_jacobi_sweeps(prev if prev != 40 else 0)
+    res = B.compress(ctx, spec, opts)
+    assert res.rank > 0
