@@ -14,6 +14,11 @@ compression (CUDA events on the launching stream).  Between timed steps L2 is
 flushed by writing a 512 MiB buffer.  With N > 1 (torchrun) every rank
 compresses its own copy of the workload (the path has no exchange between
 independent problems): weak scaling, replicas.
+
+The same line carries compact results of the other workloads (rank 0, N = 1):
+cfg1 (Gaussian 2000^2), cfg3 (coherent sparse product 50000^2, with plain ACA
+beside it), cfg4 (4096 batched Gaussian blocks against the per-block loop) and
+cfg5 (differentiated Gaussian 16384^2: backward / forward time).
 """
 import argparse
 import json
@@ -90,6 +95,9 @@ def parse():
     ap.add_argument("--no-loop", action="store_true", help="batched workload: skip the per-block loop")
     ap.add_argument("--single-cluster", action="store_true",
                     help="one cluster per matrix in QR / Q application (for profilers that serialise launches)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' keys (cfg1, cfg3-5)")
+    ap.add_argument("--loop-blocks", type=int, default=256,
+                    help="cfg4: blocks timed by the per-block loop (scaled to all blocks)")
     return ap.parse_args()
 
 
@@ -190,6 +198,50 @@ def leaf_accounting(traces, leaf_sizes, d, complex_):
     return entries, macs * (8 if complex_ else 2)
 
 
+def task_dims(ws, plan):
+    """Per stage: (kind, device-written task sizes (ntasks x 8 ints), rows of
+    the stacked QR operand per task)."""
+    import torch
+    out = []
+    for st in plan["stages"]:
+        nt = st["ntasks"]
+        d = ws[st["dims"]: st["dims"] + 32 * nt].view(torch.int32).view(nt, 8).cpu().numpy()
+        rows = np.array([t["rows_a"] for t in st["tasks"]], np.int64)
+        out.append((st["kind"], d, rows))
+    return out
+
+
+def jacobi_flops_8d(dims, complex_):
+    """Algorithmic flops of the core SVDs by the work count of the plan's
+    measurement section: 20 r^3 per leaf re-compression core (r = its
+    columns) and 20 (2 s)^3 per merge core (2 s = r1 + r2 stacked columns),
+    four times that for complex data."""
+    tot = 0.0
+    for kind, d, _ in dims:
+        ncm = d[:, 2] if kind == 0 else d[:, 0]
+        nc = np.minimum(d[:, 1], ncm).astype(np.float64)
+        tot += float(np.sum(20.0 * nc ** 3))
+    return tot * (4.0 if complex_ else 1.0)
+
+
+def whole_flops_8d(traces, leaf_sizes, d, dims, complex_):
+    """Algorithmic flops of one whole compression by the same work count:
+    per leaf (m, n, BACA rank r) (m + n) 2 r^2 (updates and norms) +
+    2 d r (m + n) (pivot QRCPs) + 2 d r n (LRID) + 4 (m + n) r^2 + 20 r^3
+    (re-compression); per merge (stacked side of `rows`, output rank s)
+    12 rows s^2 + 20 (2 s)^3; four times that for complex data."""
+    tot = 0.0
+    for tr, (m, n) in zip(traces, leaf_sizes):
+        r = float(tr["rank_baca"])
+        tot += (m + n) * 2 * r * r + 2 * d * r * (m + n) + 2 * d * r * n + 4 * (m + n) * r * r + 20 * r ** 3
+    for kind, dd, rows in dims:
+        if kind == 0:
+            continue
+        sv = dd[:, 3].astype(np.float64)
+        tot += float(np.sum(12.0 * rows * sv ** 2 + 20.0 * (2 * sv) ** 3))
+    return tot * (4.0 if complex_ else 1.0)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     def __init__(self, index):
@@ -236,59 +288,181 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
+# The oracle's own functions (BACA + re-compression per leaf, Alg. 2 and Sec.
+# 3.2; the horizontal and vertical merges of Alg. 3) in the order of
+# oracle.hbaca.hbaca, with the independent tasks of each phase spread over
+# spawned processes of one BLAS thread each.
 def _oracle_leaf(args):
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
-    x, y, k, r0, mr, c0, nc, d, eps, seed, a, b = args
+    x, y, k, d, eps, seed, a, b = args
     from oracle import baca as ob
     from oracle import generators as og
     from oracle import sampler as osamp
-    g = og.Window(og.Helmholtz(x, y, k), r0, mr, c0, nc)
+    t0 = time.perf_counter()
+    g = og.Helmholtz(x, y, k)  # the leaf's own rows / columns of the matrix
     res = ob.baca(g, d, eps, seed=seed, bid=osamp.block_id(0, a, b))
-    ob.recompress(res["U"], res["V"], eps)
-    return sum(mr * len(t["J"]) + len(t["I"]) * nc for t in res["trace"])
+    U, s, V = ob.recompress(res["U"], res["V"], eps)
+    entries = sum(g.m * len(t["J"]) + len(t["I"]) * g.n for t in res["trace"])
+    return a, b, U, s, V, entries, time.perf_counter() - t0
+
+
+def _oracle_merge(args):
+    kind, U1, s1, V1, U2, s2, V2, eps = args
+    from oracle import hbaca as oh
+    f = oh.horizontal_merge if kind == "h" else oh.vertical_merge
+    return f(U1, s1, V1, U2, s2, V2, eps)
 
 
 def _warm(_):
-    os.environ["OMP_NUM_THREADS"] = "1"
-    import oracle.baca  # noqa: F401
+    import oracle.hbaca  # noqa: F401
     return 0
 
 
-def oracle_sample(x, y, cfg, seconds, max_procs=None):
-    """The CPU oracle (leaf BACA + re-compression of Alg. 2 / Sec. 3.2) on a
-    bounded sample of the workload's leaves, processes spawned, one BLAS thread
-    each.  Returns (entries/s, cores used, description)."""
-    import multiprocessing as mp
-    L = cfg["levels"]
-    rows = leaf_spans(cfg["m"], L)
-    cols = leaf_spans(cfg["n"], L)
+class OraclePool:
+    """A pool of spawned processes with one BLAS thread each (the thread
+    limits are in the environment the children start with, so their numpy
+    reads them on import)."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        cores = len(os.sched_getaffinity(0))
+        self.procs = max(1, min(cores, procs or cores))
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.procs)
+            self.pool.map(_warm, range(self.procs))  # interpreter start-up outside any timing
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def oracle_hbaca_pool(op, x, y, k, L, d, eps, seed):
+    """Oracle H-BACA of the Helmholtz matrix (x, y, k) with 4^L leaves on the
+    pool: all leaves, then every merge level.  Returns (entries generated by
+    the leaf BACA, wall seconds, final rank)."""
+    rows = leaf_spans(x.shape[0], L)
+    cols = leaf_spans(y.shape[0], L)
     nb = 1 << L
-    cores = len(os.sched_getaffinity(0))
-    procs = max(1, min(cores, max_procs or cores))
-    ctx = mp.get_context("spawn")
-    jobs = []
-    order = np.random.default_rng(0).permutation(nb * nb)
-    for leaf in order:
-        a, b = divmod(int(leaf), nb)
-        jobs.append((x, y, cfg["k"], rows[a][0], rows[a][1], cols[b][0], cols[b][1], cfg["d"], cfg["eps"],
-                     cfg["seed"], a, b))
-    done = 0
-    entries = 0
-    with ctx.Pool(procs) as pool:
-        pool.map(_warm, range(procs))  # interpreter start-up outside the timed sample
-        t0 = time.perf_counter()
-        while done < len(jobs) and time.perf_counter() - t0 < seconds:
-            batch = jobs[done:done + procs]
-            entries += sum(pool.map(_oracle_leaf, batch))
-            done += len(batch)
-    dt = time.perf_counter() - t0
-    desc = ("oracle leaf BACA + SVD re-compression (Alg. 2, Sec. 3.2) on %d of %d leaves (%dx%d each), "
-            "%d spawned processes x 1 BLAS thread; merges not sampled" % (done, nb * nb, rows[0][1], cols[0][1], procs))
-    return entries / dt, procs, desc, dt
+    t0 = time.perf_counter()
+    jobs = [(x[rows[a][0]:rows[a][0] + rows[a][1]], y[cols[b][0]:cols[b][0] + cols[b][1]], k, d, eps, seed, a, b)
+            for a in range(nb) for b in range(nb)]
+    blocks, entries = {}, 0
+    for a, b, U, s, V, e, _ in op.pool.imap_unordered(_oracle_leaf, jobs):
+        blocks[(a, b)] = (U, s, V)
+        entries += e
+    nr = nc = nb
+    while nr > 1:
+        half = op.pool.map(_oracle_merge, [("h",) + blocks[(a, 2 * c)] + blocks[(a, 2 * c + 1)] + (eps,)
+                                           for a in range(nr) for c in range(nc // 2)])
+        nc //= 2
+        hb = {(a, c): half[a * nc + c] for a in range(nr) for c in range(nc)}
+        full = op.pool.map(_oracle_merge, [("v",) + hb[(2 * a, c)] + hb[(2 * a + 1, c)] + (eps,)
+                                           for a in range(nr // 2) for c in range(nc)])
+        nr //= 2
+        blocks = {(a, c): full[a * nc + c] for a in range(nr) for c in range(nc)}
+    return entries, time.perf_counter() - t0, len(blocks[(0, 0)][1])
+
+
+def oracle_baseline(x, y, cfg, op=None):
+    """The oracle on the whole benchmark compression (every leaf and every
+    merge).  Returns the cpu_baseline record."""
+    own = op is None
+    op = op or OraclePool()
+    try:
+        entries, dt, rank = oracle_hbaca_pool(op, x, y, cfg["k"], cfg["levels"], cfg["d"], cfg["eps"], cfg["seed"])
+    finally:
+        if own:
+            op.close()
+    desc = ("oracle H-BACA of the whole workload: BACA + SVD re-compression of all %d leaves (Alg. 2, Sec. 3.2) and "
+            "every merge level (Alg. 3), %d spawned processes x 1 BLAS thread; oracle rank %d"
+            % (4 ** cfg["levels"], op.procs, rank))
+    return {"value": entries / dt, "unit": "entries/s", "cores": op.procs, "kind": "oracle", "sample": desc,
+            "seconds": dt}
 
 
 # ------------------------------------------------------------------ GPU arm
+def _timed_calls(fn, steps, warmup, flush, stream):
+    """Run fn warmup + steps times; the last `steps` are timed with CUDA
+    events on `stream`, L2 flushed before each.  Returns the mean ms and the
+    last result."""
+    import torch
+    out = None
+    for _ in range(warmup):
+        out = fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms)), out
+
+
+def _leaf_records(B, spec, opts, ws, m, n, L):
+    nb = 1 << L
+    rows, cols = leaf_spans(m, L), leaf_spans(n, L)
+    traces, sizes = [], []
+    for leaf in range(nb * nb):
+        traces.append(B.read_leaf_trace(spec, opts, ws, leaf))
+        a, b = divmod(leaf, nb)
+        sizes.append((rows[a][1], cols[b][1]))
+    return traces, sizes
+
+
+def measure_single(B, ctx, spec, opts, cap, m, n, L, d, complex_, steps, warmup, flush, stream, dev):
+    """Time hbaca_compress on one matrix and account its work.  Returns a
+    dict: ms, entries, flops (whole compression and Jacobi, by the work
+    count of the measurement section; leaf BACA by its own count), kernel
+    times of one profiled call, phases, rank."""
+    import torch
+    dt = torch.complex128 if complex_ else torch.float64
+    ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
+    out = (torch.empty((cap, m), dtype=dt, device=dev), torch.empty(cap, dtype=torch.float64, device=dev),
+           torch.empty((cap, n), dtype=dt, device=dev))
+    ms, res = _timed_calls(lambda: B.compress(ctx, spec, opts, ws=ws, out=out), steps, warmup, flush, stream)
+    traces, sizes = _leaf_records(B, spec, opts, ws, m, n, L)
+    entries, leaf_flops = leaf_accounting(traces, sizes, d, complex_)
+    popts = B.make_opts(opts.eps, opts.d, opts.levels, seed=opts.seed, rank_cap=opts.rank_cap,
+                        leaf_rank_cap=opts.leaf_rank_cap, flags=opts.flags | B.FLAG_PROFILE, cluster=opts.cluster)
+    res = B.compress(ctx, spec, popts, ws=ws, out=out)
+    torch.cuda.synchronize(dev)
+    (tb, tr, tm, tt), launches = B.phase_times(ctx)
+    kt = B.kernel_times(ctx)
+    plan = B.plan_json(spec, popts)
+    dims = task_dims(ws, plan)
+    return dict(ms=ms, res=res, ws=ws, out=out, entries=entries, leaf_flops=leaf_flops,
+                whole_flops=whole_flops_8d(traces, sizes, d, dims, complex_),
+                jacobi_flops=jacobi_flops_8d(dims, complex_),
+                jacobi_own_flops=jacobi_accounting(ws, plan, complex_), jacobi_stages=jacobi_stage_stats(ws, plan),
+                ktimes=kt, phases={"leaf_baca_ms": tb, "leaf_recompression_ms": tr, "merge_ms": tm},
+                launches=launches, rank=res.rank)
+
+
+def roofline_of(kname, flops, ktimes, traffic=None, note=None):
+    kms, kl = ktimes[kname]
+    ach = flops / (kms / 1e3) / 1e12
+    r = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+         "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "flops_per_launch": flops / max(kl, 1),
+         "ms_per_launch": kms / max(kl, 1), "launches": kl}
+    if note:
+        r["peak_note"] = note
+    return r
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1901_06101_gb300 import binding as B
@@ -301,7 +475,7 @@ def run_ours(args, rank, world):
     ctx = B.Context()
     spec = B.helmholtz(x, y, cfg["k"])
     opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
-                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE)
+                   leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE)
     ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
     cap = cfg["rank_cap"]
     out = (torch.empty((cap, cfg["m"]), dtype=torch.complex128, device=dev),
@@ -315,14 +489,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize(dev)
     # accounting from the (deterministic) pivot records of the last run
     L = cfg["levels"]
-    nb = 1 << L
-    rows = leaf_spans(cfg["m"], L)
-    cols = leaf_spans(cfg["n"], L)
-    traces, sizes = [], []
-    for leaf in range(nb * nb):
-        traces.append(B.read_leaf_trace(spec, opts, ws, leaf))
-        a, b = divmod(leaf, nb)
-        sizes.append((rows[a][1], cols[b][1]))
+    traces, sizes = _leaf_records(B, spec, opts, ws, cfg["m"], cfg["n"], L)
     entries, flops = leaf_accounting(traces, sizes, cfg["d"], True)
     rank = res.rank
 
@@ -364,7 +531,7 @@ def run_ours(args, rank, world):
     Sh = torch.empty(cap, dtype=torch.float64).pin_memory()
     Vh = torch.empty((cap, cfg["n"]), dtype=torch.complex128).pin_memory()
     opts_e2e = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cap,
-                           leaf_rank_cap=cfg["leaf_rank_cap"])
+                       leaf_rank_cap=cfg["leaf_rank_cap"])
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -383,90 +550,233 @@ def run_ours(args, rank, world):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     e2e_value = job_throughput(entries, e2e_s, world)
 
-    # per-kernel device times of the last timed compression (CUDA events around
-    # every launch on the call's stream) and the roofline of the dominant one
+    # per-kernel device times of one more profiled compression (CUDA events
+    # around every launch on the call's stream) and the rooflines
     phases = {"leaf_baca_ms": float(np.mean(baca_ms)), "leaf_recompression_ms": float(np.mean(recomp_ms)),
               "merge_ms": float(np.mean(merge_ms))}
     res = B.compress(ctx, spec, opts, ws=ws, out=out)
     torch.cuda.synchronize(dev)
     ktimes = B.kernel_times(ctx)
     plan = B.plan_json(spec, opts)
-    jac_flops = jacobi_accounting(ws, plan, True)
+    dims = task_dims(ws, plan)
+    jac_own = jacobi_accounting(ws, plan, True)
+    jac_8d = jacobi_flops_8d(dims, True)
+    whole_8d = whole_flops_8d(traces, sizes, cfg["d"], dims, True)
     jac_stages = jacobi_stage_stats(ws, plan)
     probe = B.fp64_probe()
     peak_note = ("FP64 peak derived from 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz; live probe DFMA %.3f, "
                  "DMMA %.3f TFLOP/s" % probe)
-    dominant = max(ktimes, key=lambda k: ktimes[k][0])
-    work = {"baca_leaf_kernel": flops, "jacobi_kernel": jac_flops}
-    roofs = {}
-    for kname, fl in work.items():
-        kms, kl = ktimes[kname]
-        ach = fl / (kms / 1e3) / 1e12
-        traffic = TRAFFIC_PER_LAUNCH.get(args.workload, {}).get(kname)
-        roofs[kname] = {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "flops_per_launch": fl / max(kl, 1),
-                        "ms_per_launch": kms / max(kl, 1), "launches": kl, "peak_note": peak_note}
-    roof = roofs.get(dominant, roofs["jacobi_kernel"])
-    roof = dict(roof, dominant_kernel=dominant)
+    dominant = max(ktimes, key=lambda kk: ktimes[kk][0])
+    traffic = TRAFFIC_PER_LAUNCH.get(args.workload, {})
+    work = {"baca_leaf_kernel": flops, "jacobi_kernel": jac_8d}
+    roofs = {kn: roofline_of(kn, fl, ktimes, traffic.get(kn), peak_note) for kn, fl in work.items()}
+    roof = dict(roofs.get(dominant, roofs["jacobi_kernel"]), dominant_kernel=dominant)
+    if roof["kernel"] == "jacobi_kernel":
+        own = roofline_of("jacobi_kernel", jac_own, ktimes)
+        roof["flop_count"] = "20 r^3 per leaf core, 20 (2s)^3 per merge core, x4 complex"
+        roof["frac_by_kernel_sweeps"] = own["frac"]
+    whole = {"flops": whole_8d, "ms": ms_max, "achieved": whole_8d / (ms_max / 1e3) / 1e12,
+             "frac": whole_8d / (ms_max / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "peak": FP64_PEAK_TFLOPS,
+             "unit": "TFLOP/s", "flop_count": "leaf and merge work count of the measurement plan (r, s measured)"}
     return dict(value=value, ms=ms_max, entries=entries, flops=flops, rank=rank, phases=phases, roof=roof,
-                roof_baca=roofs["baca_leaf_kernel"], kernel_ms={k: v[0] for k, v in ktimes.items()},
-                jacobi_stages=jac_stages,
+                roof_baca=roofs["baca_leaf_kernel"], kernel_ms={kk: v[0] for kk, v in ktimes.items()},
+                jacobi_stages=jac_stages, whole=whole,
                 launches=launches, clocks=clk.summary(), wall=wall, e2e=dict(value=e2e_value, unit="entries/s",
                 h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, seconds_per_step=e2e_s), x=x, y=y)
 
 
-def run_grad(args):
-    """One step = forward (taped compression + apply) and backward of the
-    differentiated workload; reports both times and their ratio."""
+# ------------------------------------------------------------------ the other workloads
+def bench_cfg1(args, dev, flush, stream):
+    """Gaussian 2000^2, d = 8, 4 x 4 leaves, eps = 1e-6."""
     import torch
     from paper_1901_06101_gb300 import binding as B
     from paper_1901_06101_gb300 import inputs
+    x, y = inputs.gaussian_pair(seed=0, m=2000, n=2000)
+    ctx = B.Context()
+    spec = B.gaussian(x, y, 1.0)
+    opts = mk_opts(1e-6, 8, 2, seed=0, rank_cap=128, leaf_rank_cap=256)
+    r = measure_single(B, ctx, spec, opts, 128, 2000, 2000, 2, 8, False, max(3, min(args.steps, 10)),
+                       max(3, args.warmup), flush, stream, dev)
+    err = B.rel_error(ctx, spec, r["res"])
+    torch.cuda.synchronize(dev)
+    whole = r["whole_flops"] / (r["ms"] / 1e3) / 1e12
+    return {"workload": "gaussian_f64_2000_d8_L2_eps1e-6", "ms": r["ms"], "entries_per_s": r["entries"] / (r["ms"] / 1e3),
+            "rank": r["rank"], "rel_error": err,
+            "roofline_whole": {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS, "flops": r["whole_flops"]},
+            "roofline_leaf_baca": roofline_of("baca_leaf_kernel", r["leaf_flops"], r["ktimes"]),
+            "phases_ms": r["phases"], "gpu_launches": r["launches"]}
 
-    cfg = WORKLOAD
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
+
+def bench_cfg3(args, dev, flush, stream):
+    """Coherent sparse product 50000^2 (K = 50, 1% density, rank-5 dense
+    term), d = 32, 32 x 32 leaves, eps = 1e-8; plain ACA (d = 1) beside it."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+    sp = inputs.sparse_product(seed=2, m=50000, n=50000, K=50, density=0.01)
+    ctx = B.Context()
+    spec = B.sparse_product(sp)
+    out = {"workload": "sparse_product_f64_50000_K50_d32_L5_eps1e-8"}
+    for name, d in (("baca", 32), ("aca", 1)):
+        opts = mk_opts(1e-8, d, 5, seed=2, rank_cap=1024, leaf_rank_cap=512)
+        r = measure_single(B, ctx, spec, opts, 1024, 50000, 50000, 5, d, False, 3 if d > 1 else 2,
+                           3 if d > 1 else 1, flush, stream, dev)
+        err = B.rel_error(ctx, spec, r["res"])
+        torch.cuda.synchronize(dev)
+        out[name] = {"d": d, "ms": r["ms"], "rank": r["rank"], "rel_error": err,
+                     "entries_per_s": r["entries"] / (r["ms"] / 1e3), "leaf_rank_max": r["res"].res.leaf_rank_max,
+                     "leaf_iters_max": r["res"].res.leaf_iters_max}
+        if d > 1:
+            whole = r["whole_flops"] / (r["ms"] / 1e3) / 1e12
+            out[name]["roofline_whole"] = {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS}
+        del r
+        torch.cuda.empty_cache()
+    return out
+
+
+def batched_measure(nblocks, loop_blocks, steps, warmup, flush, stream, dev):
+    """hbaca_compress_batched over `nblocks` Gaussian blocks (autotuned leaf
+    cluster, CUDA-graph replay) against the plain loop of one hbaca_compress
+    per block, timed on the first `loop_blocks` blocks and scaled by the block
+    count."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+    cfg = WORKLOADS["batched4096"]
+    blocks = inputs.batched_blocks(seed=cfg["seed"], nblocks=nblocks)
+    ctx = B.Context()
+    specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
+    entries = float(sum(x.shape[0] * y.shape[0] for (x, y, _) in blocks))
+    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+                   leaf_rank_cap=cfg["leaf_rank_cap"])
+    batch = B.Batch(ctx, specs, opts)
+    tuned_cluster, tuned_ms = batch.autotune()
+    batch.opts.flags = B.FLAG_GRAPH | EXTRA_FLAGS
+    ms, _ = _timed_calls(batch.run, steps, max(warmup, 1), flush, stream)
+    ranks = batch.ranks()
+    # phase split and launch count from one profiled (uncaptured) call
+    pctx = B.Context()
+    pb = B.Batch(pctx, specs, mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+                                      leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE,
+                                      cluster=tuned_cluster), ws=batch.ws)
+    pb.run()
+    (tb, tr, tm, tt), launches = B.phase_times(pctx)
+    ws_gib = batch.ws.numel() / 2 ** 30
+    del pb, batch
+    torch.cuda.empty_cache()
+    lspecs = specs[:max(0, min(loop_blocks, nblocks))]
+    lms = float("nan")
+    loop_ranks = []
+    if lspecs:
+        lopts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
+                        leaf_rank_cap=cfg["leaf_rank_cap"])
+        lws = torch.empty(max(B.workspace_size(s.gen, lopts) for s in lspecs), dtype=torch.uint8, device=dev)
+        mmax, nmax, cap = max(s.m for s in lspecs), max(s.n for s in lspecs), cfg["rank_cap"]
+        lout = (torch.empty(cap * mmax, dtype=torch.float64, device=dev),
+                torch.empty(cap, dtype=torch.float64, device=dev),
+                torch.empty(cap * nmax, dtype=torch.float64, device=dev))
+
+        def loop():
+            rk = []
+            for s in lspecs:
+                c = min(cap, s.m, s.n)
+                o = (lout[0][:c * s.m].view(c, s.m), lout[1][:c], lout[2][:c * s.n].view(c, s.n))
+                rk.append(B.compress(ctx, s, lopts, ws=lws, out=o).rank)
+            return rk
+        lms, loop_ranks = _timed_calls(loop, 1, 1, flush, stream)
+        lms *= nblocks / len(lspecs)
+    return {"workload": cfg["workload"].replace("4096", str(nblocks)), "batched_ms": ms,
+            "per_block_loop_ms": lms, "speedup": lms / ms,
+            "loop_timing": "%d of %d blocks timed, scaled by the block count" % (len(lspecs), nblocks),
+            "entries_per_s": entries / (ms / 1e3), "batched_form": "one call, replayed CUDA graph",
+            "autotuned_leaf_cluster": tuned_cluster, "autotune_baca_ms": tuned_ms,
+            "phases_ms": {"leaf_baca_ms": tb, "leaf_recompression_ms": tr, "merge_ms": tm},
+            "gpu_launches": launches, "ranks": {"max": max(ranks), "mean": float(np.mean(ranks)),
+                                                "loop_mean": float(np.mean(loop_ranks)) if loop_ranks else None},
+            "workspace_gib": ws_gib}
+
+
+def grad_measure(steps, warmup, flush, stream, dev):
+    """Differentiated workload: forward = taped compression + y = U(S(VX)),
+    backward = dL/dh, dL/dx, dL/dy, dL/dX of L = 0.5 ||y||^2."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+    cfg = WORKLOADS["grad16384"]
     x, y = inputs.gaussian_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
     X = torch.from_numpy(inputs.rhs(cfg["seed"] + 1, cfg["n"], cfg["nrhs"])).to(dev)
     ctx = B.Context()
     spec = B.gaussian(x, y, cfg["h"])
     opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
-                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
+                   leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
     plain = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
-                        leaf_rank_cap=cfg["leaf_rank_cap"])
+                    leaf_rank_cap=cfg["leaf_rank_cap"])
     ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
     wsp = torch.empty(B.workspace_size(spec.gen, plain), dtype=torch.uint8, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        out = fn()
+        o = fn()
         e1.record(stream)
         e1.synchronize()
-        return e0.elapsed_time(e1), out
+        return e0.elapsed_time(e1), o
 
     fwd, bwd, fwd_plain = [], [], []
-    comp = Y = None
-    with ClockSampler(dev.index) as clk:
-        for it in range(args.warmup + args.steps):
-            tf, (comp, Y) = timed(lambda: (lambda c: (c, B.apply(ctx, spec, c, X)))(B.compress(ctx, spec, opts, ws=ws)))
-            tb, grads = timed(lambda: B.apply_backward(ctx, spec, opts, comp, X, Y))
-            tp, _ = timed(lambda: B.compress(ctx, spec, plain, ws=wsp))
-            if it >= args.warmup:
-                fwd.append(tf)
-                bwd.append(tb)
-                fwd_plain.append(tp)
+    comp = grads = None
+    for it in range(warmup + steps):
+        tf, (comp, Y) = timed(lambda: (lambda c: (c, B.apply(ctx, spec, c, X)))(B.compress(ctx, spec, opts, ws=ws)))
+        tb, grads = timed(lambda: B.apply_backward(ctx, spec, opts, comp, X, Y))
+        tp, _ = timed(lambda: B.compress(ctx, spec, plain, ws=wsp))
+        if it >= warmup:
+            fwd.append(tf)
+            bwd.append(tb)
+            fwd_plain.append(tp)
     f, b = float(np.mean(fwd)), float(np.mean(bwd))
-    dh = float(grads[0])
-    line = {"metric": METRIC, "value": b / f, "unit": "backward ms / forward ms", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": f + b, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    return {"workload": cfg["workload"], "forward_ms": f, "backward_ms": b, "bwd_over_fwd": b / f,
+            "forward_untaped_compress_ms": float(np.mean(fwd_plain)), "rank": comp.rank, "dL_dh": float(grads[0])}
+
+
+def extra_configs(args, dev):
+    """The other workloads' compact keys; a failure is recorded, not raised."""
+    import torch
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    jobs = [("cfg1", lambda: bench_cfg1(args, dev, flush, stream)),
+            ("cfg3", lambda: bench_cfg3(args, dev, flush, stream)),
+            ("cfg4", lambda: batched_measure(4096, args.loop_blocks, 2, 1, flush, stream, dev)),
+            ("cfg5", lambda: grad_measure(3, 2, flush, stream, dev))]
+    for name, fn in jobs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:  # noqa: BLE001 - recorded in the line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_grad(args):
+    """One step = forward (taped compression + apply) and backward of the
+    differentiated workload; reports both times and their ratio."""
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with ClockSampler(dev.index) as clk:
+        r = grad_measure(args.steps, args.warmup, flush, torch.cuda.current_stream(dev), dev)
+    cfg = WORKLOAD
+    line = {"metric": METRIC, "value": r["bwd_over_fwd"], "unit": "backward ms / forward ms", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["forward_ms"] + r["backward_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(cfg, l2="flushed between timed calls (512 MiB write)", parallelism="1 GPU"),
-            "forward_ms": f, "backward_ms": b, "forward_untaped_compress_ms": float(np.mean(fwd_plain)),
-            "rank": comp.rank, "dL_dh": dh, "clocks": clk.summary()}
+            "clocks": clk.summary()}
+    line.update({k: v for k, v in r.items() if k != "workload"})
     print(json.dumps(line))
 
 
@@ -484,7 +794,7 @@ def run_gradbatch(args):
     ctx = B.Context()
     specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
     opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
-                       leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
+                   leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_TAPE)
     bt = B.Batch(ctx, specs, opts)
     Xs = [torch.from_numpy(inputs.rhs(cfg["seed"] + 1 + b, s.n, cfg["nrhs"])).to(dev) for b, s in enumerate(specs)]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -524,98 +834,59 @@ def run_gradbatch(args):
 
 
 def run_batched(args):
-    """One step = hbaca_compress_batched over all blocks.  The plain per-block
+    """One step = hbaca_compress_batched over all blocks; the plain per-block
     loop (one hbaca_compress per block, same d, eps, leaf size and caps) is
     timed beside it on the same stream."""
     import torch
-    from paper_1901_06101_gb300 import binding as B
-    from paper_1901_06101_gb300 import inputs
-
-    cfg = WORKLOAD
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    if args.nblocks:
-        cfg = dict(cfg, nblocks=args.nblocks, workload=cfg["workload"].replace("4096", str(args.nblocks)))
-    blocks = inputs.batched_blocks(seed=cfg["seed"], nblocks=cfg["nblocks"])
-    ctx = B.Context()
-    specs = [B.gaussian(x, y, h) for (x, y, h) in blocks]
-    entries = float(sum(x.shape[0] * y.shape[0] for (x, y, _) in blocks))
-    # the batched arm: leaf cluster size from the autotuner, the call captured
-    # into a CUDA graph on its first (warm-up) run and replayed afterwards
-    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
-                       leaf_rank_cap=cfg["leaf_rank_cap"])
-    batch = B.Batch(ctx, specs, opts)
-    tuned_cluster, tuned_ms = batch.autotune()
-    batch.opts.flags = B.FLAG_GRAPH | EXTRA_FLAGS
+    nblocks = args.nblocks or WORKLOAD["nblocks"]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    for _ in range(max(args.warmup, 1)):
-        batch.run()
-    torch.cuda.synchronize(dev)
-    ranks = batch.ranks()
-    step_ms, phase = [], []
     with ClockSampler(dev.index) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            batch.run()
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-    ms = float(np.mean(step_ms))
-    # phase split and launch count from one profiled (uncaptured) call
-    pctx = B.Context()
-    pb = B.Batch(pctx, specs, mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
-                                          leaf_rank_cap=cfg["leaf_rank_cap"], flags=B.FLAG_PROFILE,
-                                          cluster=tuned_cluster), ws=batch.ws)
-    pb.run()
-    (tb, tr, tm, tt), launches = B.phase_times(pctx)
-    # the plain loop: one compress per block, shared workspace and outputs
-    lopts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=0, rank_cap=cfg["rank_cap"],
-                        leaf_rank_cap=cfg["leaf_rank_cap"])
-    wsz = max(B.workspace_size(s.gen, lopts) for s in specs)
-    lws = torch.empty(wsz, dtype=torch.uint8, device=dev)
-    mmax = max(s.m for s in specs)
-    nmax = max(s.n for s in specs)
-    cap = cfg["rank_cap"]
-    lout = (torch.empty(cap * mmax, dtype=torch.float64, device=dev),
-            torch.empty(cap, dtype=torch.float64, device=dev),
-            torch.empty(cap * nmax, dtype=torch.float64, device=dev))
-
-    def loop():
-        rk = []
-        for s in specs:
-            c = min(cap, s.m, s.n)
-            out = (lout[0][:c * s.m].view(c, s.m), lout[1][:c], lout[2][:c * s.n].view(c, s.n))
-            rk.append(B.compress(ctx, s, lopts, ws=lws, out=out).rank)
-        return rk
-
-    loop_ranks = loop() if not args.no_loop else [0]  # warm-up
-    loop_steps = max(1, min(args.steps, 2)) if not args.no_loop else 0
-    loop_ms = [float("nan")]
-    for _ in range(loop_steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        loop()
-        e1.record(stream)
-        e1.synchronize()
-        loop_ms.append(e0.elapsed_time(e1))
-    lms = float(np.mean(loop_ms[1:] if loop_steps else loop_ms))
-    line = {"metric": METRIC, "value": entries / (ms / 1e3), "unit": "matrix entries compressed/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        r = batched_measure(nblocks, 0 if args.no_loop else min(args.loop_blocks, nblocks), args.steps,
+                            args.warmup, flush, torch.cuda.current_stream(dev), dev)
+    cfg = dict(WORKLOAD, nblocks=nblocks)
+    line = {"metric": METRIC, "value": r["entries_per_s"], "unit": "matrix entries compressed/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["batched_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(cfg, l2="flushed between timed steps (512 MiB write)", parallelism="1 GPU"),
-            "batched_vs_loop": {"batched_ms": ms, "per_block_loop_ms": lms, "speedup": lms / ms,
-                                "loop_steps": loop_steps, "batched_form": "one call, replayed CUDA graph",
-                                "autotuned_leaf_cluster": tuned_cluster, "autotune_baca_ms": tuned_ms},
-            "phases_ms": {"leaf_baca_ms": tb, "leaf_recompression_ms": tr, "merge_ms": tm},
-            "gpu_launches": launches, "clocks": clk.summary(),
-            "ranks": {"max": max(ranks), "mean": float(np.mean(ranks)), "loop_mean": float(np.mean(loop_ranks))},
-            "workspace_gib": batch.ws.numel() / 2 ** 30}
+            "batched_vs_loop": r, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
+def run_reference(args, rank):
+    """The oracle arm: each step is the oracle H-BACA (all leaves and merges,
+    spawned processes of one BLAS thread) of the leading 4 x 4 leaves of the
+    benchmark matrix (rows and columns 0..4999: the same leaves, leaf sizes
+    and initial column blocks as the full workload, two merge levels)."""
+    if rank != 0:
+        return
+    from paper_1901_06101_gb300 import inputs
+    cfg = WORKLOAD
+    x, y = inputs.sphere_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
+    L = cfg["levels"]
+    Ls = min(2, L)
+    ms_, ns_ = sum(s for _, s in leaf_spans(cfg["m"], L)[:1 << Ls]), sum(s for _, s in leaf_spans(cfg["n"], L)[:1 << Ls])
+    op = OraclePool()
+    vals, secs = [], []
+    try:
+        for i in range(args.warmup + args.steps):
+            entries, dt, _ = oracle_hbaca_pool(op, x[:ms_], y[:ns_], cfg["k"], Ls, cfg["d"], cfg["eps"], cfg["seed"])
+            if i >= args.warmup:
+                vals.append(entries / dt)
+                secs.append(dt)
+    finally:
+        op.close()
+    value = float(np.mean(vals))
+    desc = ("oracle H-BACA (all %d leaves, every merge level; Alg. 2, Sec. 3.2, Alg. 3) of the leading %dx%d block "
+            "of the workload matrix (the workload's own %dx%d leaves), %d spawned processes x 1 BLAS thread"
+            % (4 ** Ls, ms_, ns_, ms_ >> Ls, ns_ >> Ls, op.procs))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(secs)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": dict({k: v for k, v in cfg.items() if k != "k"}, k="4*pi", l2="n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": "entries/s", "cores": op.procs, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -627,41 +898,14 @@ def main():
         EXTRA_FLAGS = 16  # HBACA_FLAG_SINGLE_CLUSTER
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if args.workload == "grad16384":
+    single = {"grad16384": run_grad, "gradbatch256": run_gradbatch, "batched4096": run_batched}
+    if args.workload in single:
         if args.impl == "reference" or world > 1:
-            raise SystemExit("the gradient workload is a single-GPU forward/backward comparison")
-        run_grad(args)
-        return
-    if args.workload == "gradbatch256":
-        if args.impl == "reference" or world > 1:
-            raise SystemExit("the gradient workload is a single-GPU forward/backward comparison")
-        run_gradbatch(args)
-        return
-    if args.workload == "batched4096":
-        if args.impl == "reference" or world > 1:
-            raise SystemExit("the batched workload is a single-GPU comparison of the two call forms")
-        run_batched(args)
+            raise SystemExit("this workload is a single-GPU comparison of two forms of the same GPU path")
+        single[args.workload](args)
         return
     if args.impl == "reference":
-        if rank != 0:
-            return
-        cfg = WORKLOAD
-        from paper_1901_06101_gb300 import inputs
-        x, y = inputs.sphere_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
-        per = max(5.0, min(60.0, 150.0 / max(1, args.steps + args.warmup)))
-        vals = []
-        for i in range(args.warmup + args.steps):
-            v, cores, desc, dt = oracle_sample(x, y, cfg, per)
-            if i >= args.warmup:
-                vals.append(v)
-        value = float(np.mean(vals))
-        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-                "config": dict({k: v for k, v in cfg.items() if k != "k"}, k="4*pi", l2="n/a (CPU)"),
-                "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": desc},
-                "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        run_reference(args, rank)
         return
     if world > 1:
         import torch
@@ -671,18 +915,21 @@ def main():
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, cores, desc, dt = oracle_sample(r["x"], r["y"], WORKLOAD, args.cpu_seconds)
-        cpu = {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": desc,
-               "seconds": dt}
+        cpu = oracle_baseline(r["x"], r["y"], WORKLOAD)
+    extra = {}
+    if world == 1 and not args.no_extra and args.workload == "helmholtz20000":
+        import torch
+        extra = extra_configs(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     cfg = dict({k: v for k, v in WORKLOAD.items() if k != "k"}, k="4*pi",
                l2="flushed between timed steps (512 MiB write)", parallelism="replicas" if world > 1 else "1 GPU")
     line = {"metric": METRIC, "value": r["value"], "unit": "entries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic", "config": cfg,
-            "roofline": r["roof"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
-            "clocks": r["clocks"], "phases_ms": r["phases"], "rank": r["rank"],
+            "roofline": r["roof"], "roofline_whole": r["whole"], "cpu_baseline": cpu, "e2e": r["e2e"],
+            "gpu_launches": r["launches"], "clocks": r["clocks"], "phases_ms": r["phases"], "rank": r["rank"],
             "roofline_leaf_baca": r["roof_baca"], "kernel_ms": r["kernel_ms"],
             "jacobi_stages": r["jacobi_stages"], "entries_per_step": r["entries"]}
+    line.update(extra)
     print(json.dumps(line))
 
 

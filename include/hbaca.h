@@ -279,6 +279,22 @@ hbaca_status hbaca_autotune_batched(hbaca_ctx* ctx, int32_t nblocks, const hbaca
                                     void* workspace, size_t workspace_bytes, void* stream, int32_t* best_cluster,
                                     double* best_ms);
 
+/* Accuracy of a compression, measured on the device (the relative Frobenius
+   error of the paper's accuracy study, Sec. 5.2): out[0] = ||A(I,:) -
+   U(I,:) diag(S) V||_F^2 and out[1] = ||A(I,:)||_F^2 (HOST array of two
+   doubles) over the rows I = rows[0 .. nrows-1] (a HOST array of row indices
+   in [0, m), each counted as often as it appears), or over all rows when rows
+   is NULL and nrows = 0.  The relative error is sqrt(out[0] / out[1]).  The
+   entries of A are regenerated from `gen` tile by tile; the factors are read
+   from `res` (U, S, V, ldu, ldv and the HOST rank res->rank, as a synchronous
+   hbaca_compress left them).  `workspace` (device, 256-byte aligned) holds
+   hbaca_error_workspace_size(nrows) bytes.  Synchronises `stream`.  Returns
+   HBACA_INVALID_ARG for a row index outside [0, m), a missing rank or an
+   unsupported generator. */
+size_t hbaca_error_workspace_size(int64_t nrows);
+hbaca_status hbaca_error_norms(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_result* res, const int64_t* rows,
+                               int64_t nrows, double* out, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
    by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index
    a * 2^L + b.  Arrays I, J, jbar hold `max_iters * d` entries (row-major by

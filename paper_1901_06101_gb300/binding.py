@@ -125,6 +125,10 @@ SIGNATURES = [
                                          ctypes.POINTER(ctypes.c_int32)]),
     ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
+    ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
+    ("hbaca_error_norms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Result), ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_void_p]),
     ("hbaca_last_error", ctypes.c_char_p, []),
     ("hbaca_version", ctypes.c_char_p, []),
 ]
@@ -276,6 +280,33 @@ def _host_rank(res, opts):
     if r < 0:
         raise HbacaError(1, "no host rank (HBACA_FLAG_ASYNC): these helpers need a synchronous call")
     return r
+
+
+def error_norms(ctx, spec, comp, rows=None, stream=None):
+    """hbaca_error_norms: (||A(I,:) - U(I,:) S V||_F^2, ||A(I,:)||_F^2) on the
+    device over the rows I (all rows when None) of the compressed matrix
+    ``comp`` (a Compressed from a synchronous call)."""
+    import numpy as np
+    import torch
+    if rows is None:
+        rp, nr = None, 0
+    else:
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        rp, nr = rows.ctypes.data_as(ctypes.c_void_p), rows.size
+    nbytes = lib().hbaca_error_workspace_size(nr)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = (ctypes.c_double * 2)()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib().hbaca_error_norms(ctx.ptr, ctypes.byref(spec.gen), ctypes.byref(comp.res), rp, nr, out,
+                                  ctypes.c_void_p(ws.data_ptr()), nbytes, ctypes.c_void_p(stream)))
+    return out[0], out[1]
+
+
+def rel_error(ctx, spec, comp, rows=None):
+    """sqrt(error_norms ratio): ||A - U S V||_F / ||A||_F on the device."""
+    e2, a2 = error_norms(ctx, spec, comp, rows)
+    return (e2 / a2) ** 0.5 if a2 > 0 else 0.0
 
 
 def set_jacobi_sweeps(n):

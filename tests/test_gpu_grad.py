@@ -14,6 +14,7 @@ from oracle import generators as og
 from oracle import hbaca as oh
 from paper_1901_06101_gb300 import binding as B
 from paper_1901_06101_gb300 import inputs
+from tests import oracle_pool as opool
 from tests.test_gpu_batched import levels_for
 
 pytestmark = pytest.mark.gpu
@@ -113,6 +114,46 @@ def test_gradient_matches_frozen_pivot_finite_differences(ctx, m, n, L, d):
         fd = (lp - lm) / (2 * t)
         an = float(np.sum(dx * px) + np.sum(dy * py))
         assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-12 * loss0), (an, fd)
+
+
+def test_cfg5_structure_gradient_matches_frozen_pivot_finite_differences(ctx):
+    """The differentiated workload's structure (d = 16, 8 x 8 leaves,
+    eps = 1e-8, h = 0.7) at 4096^2, where the frozen-pivot oracle is
+    affordable: dL/dh and two directional derivatives in the point
+    coordinates against central finite differences (step 1e-6) of the oracle
+    H-BACA with the GPU's pivots and the oracle's truncation ranks frozen,
+    within 1e-6 relative."""
+    eps, h, nrhs, L, d = 1e-8, 0.7, 8, 3, 16
+    x, y, X = _case(61, 4096, 4096, nrhs)
+    spec, opts, comp, Y = _forward(ctx, x, y, h, X, L, d, eps, cap=512)
+    dh, dx, dy, _ = B.apply_backward(ctx, spec, opts, comp, torch.from_numpy(X).cuda(), Y, want_dX=False)
+    dh = float(dh)
+    dx = dx.cpu().numpy()
+    dy = dy.cpu().numpy()
+    traces = {leaf: B.read_leaf_trace(spec, opts, comp.ws, leaf) for leaf in range(64)}
+    rng = np.random.default_rng(17)
+    dirs = [(rng.standard_normal(x.shape), rng.standard_normal(y.shape)) for _ in range(2)]
+    with opool.Pool() as pool:
+        r0 = opool.hbaca(pool, og.Gaussian(x, y, h), L, d, eps, seed=0, forced=traces)
+        assert r0["r"] == comp.rank
+        A0 = (r0["U"] * r0["s"][None, :]) @ r0["V"]
+        Y0 = A0 @ X
+        loss0 = 0.5 * float(np.sum(Y0 * Y0))
+        Ygpu = Y.cpu().numpy()
+        assert abs(0.5 * float(np.sum(Ygpu * Ygpu)) - loss0) <= 1e-10 * loss0
+        fr = r0["ranks"]
+        dl, t = 1e-6 * h, 1e-6
+        cases = [(x, y, h + dl, X, L, d, eps, traces, fr), (x, y, h - dl, X, L, d, eps, traces, fr)]
+        for px, py in dirs:
+            cases += [(x + t * px, y + t * py, h, X, L, d, eps, traces, fr),
+                      (x - t * px, y - t * py, h, X, L, d, eps, traces, fr)]
+        losses = opool.gaussian_losses(pool, cases)
+    fd = (losses[0] - losses[1]) / (2 * dl)
+    assert abs(dh - fd) <= 1e-6 * abs(fd), (dh, fd)
+    for i, (px, py) in enumerate(dirs):
+        fdd = (losses[2 + 2 * i] - losses[3 + 2 * i]) / (2 * t)
+        an = float(np.sum(dx * px) + np.sum(dy * py))
+        assert abs(an - fdd) <= 1e-6 * max(abs(fdd), 1e-12 * loss0), (i, an, fdd)
 
 
 def test_gradient_close_to_dense_autograd(ctx):

@@ -12,6 +12,8 @@ from oracle import linalg as ol
 from oracle import sampler as osamp
 from paper_1901_06101_gb300 import binding as B
 from paper_1901_06101_gb300 import inputs
+from oracle import apply as oapply
+from tests import oracle_pool as opool
 from tests.parity import check_leaf_replay, compare_leaf, dense_rel_error, near_threshold
 
 pytestmark = pytest.mark.gpu
@@ -156,24 +158,75 @@ def test_sparse_product_converging(ctx):
     check_result(og_, res, 1e-11, full)
 
 
-def test_sparse_product_coherent_cfg3_shape(ctx):
+def noise_allowance(traces, recs, norm_a):
+    """Rounding allowance for the final errors of two correct runs that
+    replayed the same pivots: once a leaf's cross W reaches the rounding
+    level, LRID's T^-1 amplifies that noise and the two runs' updates U_k V_k
+    agree only in size, not in value.  Their difference is at most the sum of
+    the norms nu_k = ||U_k V_k||_F of those iterations in both runs (GPU
+    record and oracle replay), relative to ||A||_F."""
+    tot = 0.0
+    for leaf, g in traces.items():
+        rr = recs.get(leaf) or []
+        noisy = [k for k, r in enumerate(rr) if r.get("noise_level")]
+        if not noisy:
+            continue
+        k0 = noisy[0]
+        tot += sum(t["nu"] for t in g["trace"][k0:]) + sum(r["nu"] for r in rr[k0:] if "nu" in r)
+    return tot / norm_a
+
+
+def compare_with_frozen_oracle(res, full, ogen, traces, rows=None, extra_tol=0.0):
+    """GPU factors against the frozen-pivot oracle H-BACA: ranks within 2
+    (equal unless a singular value sits at the threshold), singular values to
+    1e-9 sigma_1, orthonormal factors, and relative errors (on all rows, or on
+    the sampled ``rows``) within 1e-10 plus ``extra_tol`` of each other.
+    Returns (GPU error, oracle error)."""
+    U, S, V = res.U.cpu().numpy(), res.S.cpu().numpy(), res.V.cpu().numpy()
+    assert abs(res.rank - full["r"]) <= 2, (res.rank, full["r"])
+    r = min(res.rank, full["r"])
+    np.testing.assert_allclose(S[:r], full["s"][:r], rtol=0, atol=1e-9 * S[0])
+    np.testing.assert_allclose(U.conj().T @ U, np.eye(res.rank), atol=1e-10)
+    np.testing.assert_allclose(V @ V.conj().T, np.eye(res.rank), atol=1e-10)
+    eg = oapply.rel_error_dense(ogen, U, S, V, row_chunk=256, rows=rows)
+    eo = oapply.rel_error_dense(ogen, full["U"], full["s"], full["V"], row_chunk=256, rows=rows)
+    assert abs(eg - eo) <= 1e-10 + extra_tol, (eg, eo, extra_tol)
+    return eg, eo
+
+
+def all_traces(spec, opts, ws, L):
+    return {leaf: B.read_leaf_trace(spec, opts, ws, leaf) for leaf in range(4 ** L)}
+
+
+@pytest.mark.parametrize("d", [32, 1])
+def test_sparse_product_coherent_cfg3_shape(ctx, d):
     """Coherent sparse product of the benchmark's shape at 6000^2 (leaves of
-    1500, K = 50, 1% density, d = 32, eps = 1e-8).  BACA stops before reaching
-    eps here (the oracle does too) and some leaves reach crosses at the
-    rounding-noise level, after which runs legitimately differ.  Checked:
-    every leaf's pivots up to that point by frozen-pivot replay, and the
-    factors' structure; the errors are reported."""
+    1500, K = 50, 1% density, eps = 1e-8), with the benchmark's block size
+    d = 32 and with plain ACA (d = 1).  BACA stops before reaching eps here
+    (the oracle does too: premature termination on coherent matrices).
+    Checked: every leaf's pivots (free comparison while margins are unique,
+    frozen-pivot replay of the whole record), then the final factors against
+    the frozen-pivot oracle H-BACA (ranks, singular values, errors)."""
     sp = inputs.sparse_product(seed=2, m=6000, n=6000, K=50, density=0.01)
     og_ = og.SparseProduct(sp.dense_P(), sp.dense_Q(), sp.P2, sp.Q2)
     spec = B.sparse_product(sp)
-    res, compared, div, tr = run_and_compare(ctx, spec, og_, 2, 32, 1e-8, seed=2, rank_cap=512, leaf_cap=512)
-    U, S, V = res.U.cpu().numpy(), res.S.cpu().numpy(), res.V.cpu().numpy()
-    np.testing.assert_allclose(U.T @ U, np.eye(res.rank), atol=1e-10)
-    np.testing.assert_allclose(V @ V.T, np.eye(res.rank), atol=1e-10)
+    res, compared, div, tr = run_and_compare(ctx, spec, og_, 2, d, 1e-8, seed=2, rank_cap=512, leaf_cap=512)
+    full = oh.hbaca(og_, 2, d, 1e-8, seed=2, forced=tr)
+    recs = {}
+    for leaf in tr:
+        a, b = divmod(leaf, 4)
+        rows = oh.tree_levels(og_.m, 2)[0]
+        cols = oh.tree_levels(og_.n, 2)[0]
+        w = og.Window(og_, rows[a][0], rows[a][1], cols[b][0], cols[b][1])
+        recs[leaf] = ob.baca_replay(w, d, 1e-8, tr[leaf]["trace"], seed=2, bid=osamp.block_id(0, a, b),
+                                    stop=tr[leaf]["stop"])["recs"]
     A = og_(np.arange(og_.m), np.arange(og_.n))
-    full = oh.hbaca(og_, 2, 32, 1e-8, seed=2)
-    print("coherent 6000^2: GPU rank %d err %.3e; oracle (free run) rank %d err %.3e; leaves not comparable %d"
-          % (res.rank, dense_rel_error(A, U, S, V), full["r"], dense_rel_error(A, full["U"], full["s"], full["V"]), div))
+    allow = noise_allowance(tr, recs, float(np.linalg.norm(A)))
+    eg, eo = compare_with_frozen_oracle(res, full, og_, tr, extra_tol=allow)
+    ed = B.rel_error(ctx, spec, res)
+    assert abs(ed - eg) <= 1e-12 * max(eg, 1e-300)
+    print("coherent 6000^2 d=%d: GPU rank %d err %.6e; frozen-pivot oracle rank %d err %.6e; allowance %.1e"
+          % (d, res.rank, eg, full["r"], eo, allow))
 
 
 @pytest.mark.parametrize("cplx", [False, True])
@@ -228,31 +281,63 @@ def test_rank_capacity_reported(ctx):
     assert ei.value.code == 2
 
 
-def test_cfg2_helmholtz_20000_sampled_leaves(ctx):
+def test_cfg2_helmholtz_20000_against_frozen_oracle(ctx):
+    """The benchmark workload at full size (Helmholtz, complex128, 20000^2,
+    16 x 16 leaves, d = 16, eps = 1e-4): sampled leaves compared with free
+    oracle runs; then the whole frozen-pivot oracle H-BACA (every leaf
+    replayed with the GPU's pivots, every merge) against the GPU factors on
+    2000 sampled rows; the device error evaluator against the CPU one on
+    those rows, and over all rows within eps."""
     x, y = inputs.sphere_pair(seed=1, m=20000, n=20000)
     k = 4 * np.pi
     spec = B.helmholtz(x, y, k)
     og_ = og.Helmholtz(x, y, k)
-    res, compared, div, tr = run_and_compare(ctx, spec, og_, 4, 16, 1e-4, seed=1, rank_cap=256, leaf_cap=256,
-                                         check_all_leaves=False)
+    res, compared, div, _ = run_and_compare(ctx, spec, og_, 4, 16, 1e-4, seed=1, rank_cap=256, leaf_cap=256,
+                                            check_all_leaves=False)
     assert compared >= 3
-    rng = np.random.default_rng(0)
-    I = np.sort(rng.choice(20000, 64, replace=False))
-    A = og_(I, np.arange(20000))
-    U = res.U.cpu().numpy()[I]
-    E = A - (U * res.S.cpu().numpy()[None, :]) @ res.V.cpu().numpy()
-    assert np.linalg.norm(E) / np.linalg.norm(A) < 3e-4
+    opts = B.make_opts(1e-4, 16, 4, seed=1, rank_cap=256, leaf_rank_cap=256)
+    tr = all_traces(spec, opts, res.ws, 4)
+    with opool.Pool() as pool:
+        full = opool.hbaca(pool, og_, 4, 16, 1e-4, seed=1, forced=tr)
+    assert all(full["leaf_rank"][divmod(leaf, 16)] == tr[leaf]["rank_baca"] for leaf in tr)
+    rows = np.sort(np.random.default_rng(0).choice(20000, 2000, replace=False))
+    eg, eo = compare_with_frozen_oracle(res, full, og_, tr, rows=rows)
+    assert eg <= 2e-4
+    e2, a2 = B.error_norms(ctx, spec, res, rows)
+    assert abs(np.sqrt(e2 / a2) - eg) <= 1e-12 * eg
+    e_all = B.rel_error(ctx, spec, res)
+    assert e_all <= 2e-4
+    print("cfg2: rank %d (oracle %d); sampled-row error GPU %.6e oracle %.6e; all rows (device) %.6e"
+          % (res.rank, full["r"], eg, eo, e_all))
 
 
-def test_cfg3_sparse_50000_sampled_leaves(ctx):
+def test_cfg3_sparse_50000_against_frozen_oracle(ctx):
     """The full coherent sparse-product workload (50000^2, 32 x 32 leaves,
-    d = 32, eps = 1e-8): frozen-pivot replay of sampled leaves."""
+    d = 32, eps = 1e-8): sampled leaves compared with free oracle runs and
+    replayed; then the whole frozen-pivot oracle H-BACA against the GPU
+    factors on 2000 sampled rows, with the rounding allowance of leaves
+    whose crosses reached the noise level; the device error evaluator
+    against the CPU one on those rows."""
     sp = inputs.sparse_product(seed=2, m=50000, n=50000, K=50, density=0.01)
     og_ = og.SparseProduct(sp.dense_P(), sp.dense_Q(), sp.P2, sp.Q2)
     spec = B.sparse_product(sp)
-    res, compared, div, tr = run_and_compare(ctx, spec, og_, 5, 32, 1e-8, seed=2, rank_cap=1024, leaf_cap=512,
-                                             check_all_leaves=False)
-    print("cfg3: rank %d, max leaf BACA rank %d" % (res.rank, res.res.leaf_rank_max))
+    res, compared, div, _ = run_and_compare(ctx, spec, og_, 5, 32, 1e-8, seed=2, rank_cap=1024, leaf_cap=512,
+                                            check_all_leaves=False)
+    opts = B.make_opts(1e-8, 32, 5, seed=2, rank_cap=1024, leaf_rank_cap=512)
+    tr = all_traces(spec, opts, res.ws, 5)
+    with opool.Pool() as pool:
+        full = opool.hbaca(pool, og_, 5, 32, 1e-8, seed=2, forced=tr)
+    recs = {a * 32 + b: v for (a, b), v in full["leaf_recs"].items()}
+    rows = np.sort(np.random.default_rng(1).choice(50000, 2000, replace=False))
+    na = np.sqrt(sum(np.sum(og_(rows[i:i + 256], np.arange(og_.n)) ** 2) for i in range(0, rows.size, 256)))
+    # the allowance is relative to ||A||_F; on 2000 of 50000 rows ||A(I,:)||
+    # is about sqrt(2000/50000) of it
+    allow = noise_allowance(tr, recs, na / np.sqrt(2000 / 50000))
+    eg, eo = compare_with_frozen_oracle(res, full, og_, tr, rows=rows, extra_tol=allow)
+    e2, a2 = B.error_norms(ctx, spec, res, rows)
+    assert abs(np.sqrt(e2 / a2) - eg) <= 1e-12 * max(eg, 1e-300)
+    print("cfg3: rank %d (oracle %d); sampled-row error GPU %.6e oracle %.6e; allowance %.1e; leaf BACA rank max %d"
+          % (res.rank, full["r"], eg, eo, allow, res.res.leaf_rank_max))
 
 
 def test_single_cluster_flag_agrees_with_cluster_groups(ctx):
