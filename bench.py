@@ -619,11 +619,17 @@ def bench_cfg3(args, dev, flush, stream):
     out = {"workload": "sparse_product_f64_50000_K50_d32_L5_eps1e-8"}
     for name, d in (("baca", 32), ("aca", 1)):
         opts = mk_opts(1e-8, d, 5, seed=2, rank_cap=1024, leaf_rank_cap=512)
-        r = measure_single(B, ctx, spec, opts, 1024, 50000, 50000, 5, d, False, 3 if d > 1 else 2,
-                           3 if d > 1 else 1, flush, stream, dev)
+        t0 = time.perf_counter()
+        try:
+            r = measure_single(B, ctx, spec, opts, 1024, 50000, 50000, 5, d, False, 3 if d > 1 else 2,
+                               3 if d > 1 else 1, flush, stream, dev)
+        except B.HbacaError as e:
+            out[name] = {"d": d, "error": str(e), "wall_s": time.perf_counter() - t0}
+            torch.cuda.empty_cache()
+            continue
         err = B.rel_error(ctx, spec, r["res"])
         torch.cuda.synchronize(dev)
-        out[name] = {"d": d, "ms": r["ms"], "rank": r["rank"], "rel_error": err,
+        out[name] = {"d": d, "ms": r["ms"], "rank": r["rank"], "rel_error": err, "wall_s": time.perf_counter() - t0,
                      "entries_per_s": r["entries"] / (r["ms"] / 1e3), "leaf_rank_max": r["res"].res.leaf_rank_max,
                      "leaf_iters_max": r["res"].res.leaf_iters_max}
         if d > 1:

@@ -59,7 +59,11 @@ typedef enum hbaca_gen_kind {
   HBACA_GEN_GAUSSIAN = 1,       /* exp(-||x_i - y_j||^2 / (2 h^2))       (Sec. 5, kernel 1) */
   HBACA_GEN_HELMHOLTZ = 2,      /* exp(i k r) / r, r = ||x_i - y_j||     (complex128)       */
   HBACA_GEN_SPARSE_PRODUCT = 3, /* sum_k P(i,k) Q(k,j) + sum_t P2(i,t) Q2(t,j)              */
-  HBACA_GEN_LOWRANK = 4         /* sum_t LU(i,t) LV(t,j)        (Sec. 5, kernel 6)          */
+  HBACA_GEN_LOWRANK = 4,        /* sum_t LU(i,t) LV(t,j)        (Sec. 5, kernel 6)          */
+  HBACA_GEN_POLYNOMIAL = 5,     /* (x_i^t y_j + h)^2            (Sec. 5, kernel 5; float64) */
+  HBACA_GEN_HANKEL2D = 6        /* H0^(2)(k ||x_i - y_j||), the EFIE2D kernel (Sec. 5,
+                                   kernel 2; complex128); x_i != y_j (H0^(2) is singular
+                                   at 0) */
 } hbaca_gen_kind;
 
 typedef enum hbaca_dtype { HBACA_F64 = 0, HBACA_C128 = 1 } hbaca_dtype;
@@ -70,13 +74,13 @@ typedef struct hbaca_gen {
   int32_t dtype;       /* hbaca_dtype; HELMHOLTZ requires C128, GAUSSIAN and
                           SPARSE_PRODUCT require F64 */
   int64_t m, n;        /* rows, columns (1 <= m, n < 2^31) */
-  /* GAUSSIAN, HELMHOLTZ: points, row-major, `dim` doubles each */
+  /* GAUSSIAN, HELMHOLTZ, POLYNOMIAL, HANKEL2D: points, row-major, `dim` doubles each */
   const double* x;     /* m x dim */
   const double* y;     /* n x dim */
   int32_t dim;         /* 1 .. 64 */
   int32_t pad0;
-  double h;            /* Gaussian width (> 0) */
-  double k;            /* Helmholtz wavenumber */
+  double h;            /* Gaussian width (> 0); POLYNOMIAL: the shift h */
+  double k;            /* Helmholtz / HANKEL2D wavenumber (HANKEL2D: > 0) */
   /* DENSE */
   const void* a;       /* m x n column-major, scalar = dtype */
   int64_t lda;

@@ -26,6 +26,17 @@ hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts
                                     int64_t* m_out, int64_t* n_out, int64_t* rank_out, int64_t* cap_out,
                                     void* stream);
 
+/* The BACA factors of leaf `leaf` (Alg. 2 output before re-compression) of
+   a call made with HBACA_FLAG_TAPE (only then do they survive the call),
+   copied into HOST buffers: U (m_leaf x rank, column-major, ld m_leaf) and
+   V (rank x n_leaf, row-major, ld n_leaf), which must hold m_leaf * cap and
+   cap * n_leaf scalars for the leaf's rank capacity cap (opts.leaf_rank_cap
+   as resolved; at most min(m_leaf, n_leaf, 1024)).  *m_out, *n_out,
+   *rank_out receive the leaf's size and BACA rank. */
+hbaca_status hbaca_debug_read_leaf_factors(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace,
+                                           int64_t leaf, void* U, void* V, int64_t* m_out, int64_t* n_out,
+                                           int64_t* rank_out, void* stream);
+
 /* Write a JSON description of the workspace layout of (gen, opts) (region
    byte offsets, stage task tables) into buf (NUL-terminated, truncated to
    len).  Returns the length the full text needs. */
@@ -45,6 +56,14 @@ hbaca_status hbaca_debug_fp64_probe(double* dfma_tflops, double* dmma_tflops);
    full text needs, or -1. */
 int64_t hbaca_debug_backward_json(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace, int64_t nrhs,
                                   char* buf, int64_t len, void* stream);
+
+/* Entries A(rows[t], cols[t]), t < count, of the matrix described by `gen`,
+   evaluated on the device by the same entry generators the compression uses
+   (rows, cols: DEVICE int64 arrays; out: DEVICE array of count scalars of
+   gen->dtype; a pair outside [0, m) x [0, n) gives NaN).
+   Enqueued on `stream`, not synchronised.  For tests of the generators. */
+hbaca_status hbaca_debug_entries(const hbaca_gen* gen, const int64_t* rows, const int64_t* cols, int64_t count,
+                                 void* out, void* stream);
 
 /* Sweep cap of the one-sided Jacobi SVD (Sec. 2, SVD(A, eps)) used by every
    later call in this process: sweeps > 0 sets it, 0 restores the default

@@ -39,6 +39,37 @@ class Helmholtz:
         return np.exp(1j * self.k * r) / r
 
 
+class Polynomial:
+    """Polynomial kernel (x_i^t y_j + h)^2 (Sec. 5, kernel 5)."""
+    dtype = np.float64
+
+    def __init__(self, x, y, h):
+        self.x = np.asarray(x, np.float64)
+        self.y = np.asarray(y, np.float64)
+        self.h = float(h)
+        self.m, self.n = self.x.shape[0], self.y.shape[0]
+
+    def __call__(self, I, J):
+        return (self.x[np.asarray(I)] @ self.y[np.asarray(J)].T + self.h) ** 2
+
+
+class Hankel2D:
+    """EFIE2D kernel H0^(2)(k ||x_i - y_j||) (Sec. 5, kernel 2): the Hankel
+    function of the second kind of order 0 (scipy.special.hankel2)."""
+    dtype = np.complex128
+
+    def __init__(self, x, y, k):
+        self.x = np.asarray(x, np.float64)
+        self.y = np.asarray(y, np.float64)
+        self.k = float(k)
+        self.m, self.n = self.x.shape[0], self.y.shape[0]
+
+    def __call__(self, I, J):
+        import scipy.special
+        diff = self.x[np.asarray(I)][:, None, :] - self.y[np.asarray(J)][None, :, :]
+        return scipy.special.hankel2(0, self.k * np.sqrt((diff * diff).sum(axis=2)))
+
+
 class SparseProduct:
     """A = P Q + P2 Q2 with sparse P (m x K), Q (K x n) and a dense low-rank
     term: a coherent, non-smooth matrix of the kind on which ACA terminates

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhbaca.so")
 
 # hbaca_gen_kind
-GEN_DENSE, GEN_GAUSSIAN, GEN_HELMHOLTZ, GEN_SPARSE_PRODUCT, GEN_LOWRANK = 0, 1, 2, 3, 4
+GEN_DENSE, GEN_GAUSSIAN, GEN_HELMHOLTZ, GEN_SPARSE_PRODUCT, GEN_LOWRANK, GEN_POLYNOMIAL, GEN_HANKEL2D = range(7)
 # hbaca_dtype
 F64, C128 = 0, 1
 FLAG_ASYNC = 1
@@ -126,6 +126,11 @@ SIGNATURES = [
     ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
+    ("hbaca_debug_read_leaf_factors", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
+                                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+     + [ctypes.POINTER(ctypes.c_int64)] * 3 + [ctypes.c_void_p]),
+    ("hbaca_debug_entries", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     ("hbaca_error_norms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Gen), ctypes.POINTER(Result), ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
                                          ctypes.c_size_t, ctypes.c_void_p]),
@@ -235,6 +240,40 @@ def helmholtz(x, y, k):
     g = Gen(kind=GEN_HELMHOLTZ, dtype=C128, m=x.shape[0], n=y.shape[0], x=x.data_ptr(), y=y.data_ptr(),
             dim=x.shape[1], k=float(k))
     return GenSpec(g, (x, y))
+
+
+def polynomial(x, y, h):
+    """Polynomial kernel (x_i^t y_j + h)^2."""
+    import torch
+    x = _dev(x, torch.float64)
+    y = _dev(y, torch.float64)
+    g = Gen(kind=GEN_POLYNOMIAL, dtype=F64, m=x.shape[0], n=y.shape[0], x=x.data_ptr(), y=y.data_ptr(),
+            dim=x.shape[1], h=float(h))
+    return GenSpec(g, (x, y))
+
+
+def hankel2d(x, y, k):
+    """EFIE2D kernel H0^(2)(k ||x_i - y_j||) (complex128)."""
+    import torch
+    x = _dev(x, torch.float64)
+    y = _dev(y, torch.float64)
+    g = Gen(kind=GEN_HANKEL2D, dtype=C128, m=x.shape[0], n=y.shape[0], x=x.data_ptr(), y=y.data_ptr(),
+            dim=x.shape[1], k=float(k))
+    return GenSpec(g, (x, y))
+
+
+def entries(spec, rows, cols):
+    """hbaca_debug_entries: A(rows[t], cols[t]) from the device generators, as
+    a numpy array."""
+    import numpy as np
+    import torch
+    r = torch.as_tensor(np.asarray(rows, np.int64)).cuda()
+    c = torch.as_tensor(np.asarray(cols, np.int64)).cuda()
+    out = torch.empty(r.numel(), dtype=torch.complex128 if spec.complex else torch.float64, device="cuda")
+    check(lib().hbaca_debug_entries(ctypes.byref(spec.gen), ctypes.c_void_p(r.data_ptr()),
+                                    ctypes.c_void_p(c.data_ptr()), r.numel(), ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out.cpu().numpy()
 
 
 def dense(A):
@@ -539,9 +578,17 @@ class Batch:
         n = len(self.specs)
         self.gens = _gen_array(self.specs)
         if ws is None:
-            nbytes = lib().hbaca_workspace_size_batched(n, self.gens, ctypes.byref(opts))
-            if nbytes == 0:
-                raise HbacaError(1, lib().hbaca_last_error().decode())
+            # with an automatic leaf cluster size, room for every size the
+            # autotuner may try (the plans differ by their scratch)
+            sizes = [0] + ([1, 2, 4, 8, 16] if opts.cluster == 0 else [])
+            nbytes = 0
+            for c in sizes:
+                o = Opts.from_buffer_copy(opts)
+                o.cluster = c
+                nb = lib().hbaca_workspace_size_batched(n, self.gens, ctypes.byref(o))
+                if nb == 0 and c == 0:
+                    raise HbacaError(1, lib().hbaca_last_error().decode())
+                nbytes = max(nbytes, nb)
             ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         self.ws = ws
         self.res = (Result * n)()
@@ -639,6 +686,23 @@ def read_block(spec, opts, ws, store, level, block):
     U = Ub[:bm * r].reshape(r, bm).T
     V = Vb[:r * bn].reshape(r, bn)
     return U, Sb[:r], V
+
+
+def read_leaf_factors(spec, opts, ws, leaf, m_leaf, n_leaf):
+    """BACA factors (U m_leaf x r, V r x n_leaf) of one leaf of a taped call."""
+    import numpy as np
+    import torch
+    cap = min(m_leaf, n_leaf, 1024)
+    dt = np.complex128 if spec.complex else np.float64
+    Ub = np.zeros(m_leaf * cap, dt)
+    Vb = np.zeros(cap * n_leaf, dt)
+    mo, no, ro = (ctypes.c_int64() for _ in range(3))
+    check(lib().hbaca_debug_read_leaf_factors(ctypes.byref(spec.gen), ctypes.byref(opts), ctypes.c_void_p(ws.data_ptr()),
+                                              leaf, Ub.ctypes.data_as(ctypes.c_void_p), Vb.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.byref(mo), ctypes.byref(no), ctypes.byref(ro),
+                                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    r = ro.value
+    return Ub[:mo.value * r].reshape(r, mo.value).T, Vb[:r * no.value].reshape(r, no.value)
 
 
 def plan_json(spec, opts):

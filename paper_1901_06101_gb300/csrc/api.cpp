@@ -495,6 +495,38 @@ hbaca_status hbaca_debug_read_block(const hbaca_gen* gen, const hbaca_opts* opts
   return HBACA_OK;
 }
 
+hbaca_status hbaca_debug_read_leaf_factors(const hbaca_gen* gen, const hbaca_opts* opts, const void* workspace,
+                                           int64_t leaf, void* U, void* V, int64_t* m_out, int64_t* n_out,
+                                           int64_t* rank_out, void* stream) {
+  if (!gen || !opts || !workspace) return fail(HBACA_INVALID_ARG, "NULL argument");
+  if (!(opts->flags & HBACA_FLAG_TAPE))
+    return fail(HBACA_INVALID_ARG, "leaf factors survive the call only with HBACA_FLAG_TAPE");
+  hbaca::Plan p;
+  std::string err;
+  if (!hbaca::make_plan(gen, 1, *opts, current_sms(), p, err)) return fail(HBACA_INVALID_ARG, err);
+  if (leaf < 0 || leaf >= p.nleaves) return fail(HBACA_INVALID_ARG, "leaf index out of range");
+  hbaca::LeafDesc L;
+  std::memcpy(&L, p.desc.data() + p.leafdesc_off + leaf * sizeof(hbaca::LeafDesc), sizeof(L));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const char* ws = reinterpret_cast<const char*>(workspace);
+  hbaca::LeafOut lo;
+  cudaError_t e = cudaMemcpyAsync(&lo, ws + p.leafout_off + leaf * sizeof(hbaca::LeafOut), sizeof(lo),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const int r = std::max(0, std::min(lo.rank, L.rcap));
+  if (e == cudaSuccess && r > 0 && U)
+    e = cudaMemcpyAsync(U, ws + p.uar.off + (size_t)L.u_off * p.esz, (size_t)L.m * r * p.esz, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && r > 0 && V)
+    e = cudaMemcpyAsync(V, ws + p.var.off + (size_t)L.v_off * p.esz, (size_t)r * L.n * p.esz, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("leaf factor copy: ") + cudaGetErrorString(e));
+  if (m_out) *m_out = L.m;
+  if (n_out) *n_out = L.n;
+  if (rank_out) *rank_out = r;
+  tls_err.clear();
+  return HBACA_OK;
+}
+
 hbaca_status hbaca_phase_times(hbaca_ctx* ctx, double ms[4], int32_t* launches) {
   if (!ctx || !ms) return fail(HBACA_INVALID_ARG, "NULL argument");
   if (launches) *launches = ctx->launches;

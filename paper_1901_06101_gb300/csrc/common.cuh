@@ -251,6 +251,102 @@ struct GenSparseProduct {
   }
 };
 
+// Polynomial kernel (x_i^t y_j + h)^2 (Sec. 5, kernel 5).
+struct GenPolynomial {
+  __device__ __forceinline__ GenPolynomial bind(int) const { return *this; }
+  using scalar = double;
+  const double* x;
+  const double* y;
+  int dim;
+  double h;
+  __device__ __forceinline__ double operator()(int64_t i, int64_t j) const {
+    const double* xi = x + i * dim;
+    const double* yj = y + j * dim;
+    double s = h;
+    for (int t = 0; t < dim; ++t) s = fma(xi[t], yj[t], s);
+    return s * s;
+  }
+};
+
+// Hankel function of the second kind of order 0, H0^(2)(z) = J0(z) - i Y0(z),
+// for real z > 0 (the EFIE2D kernel of Sec. 5, kernel 2).
+//  z <  20: J_n(z) by Miller's backward recurrence J_{n-1} = (2n/z) J_n -
+//           J_{n+1} from a large even start N (J_{N+1} = 0), normalised by
+//           J_0 + 2 sum_k J_2k = 1; Y0 from Neumann's series
+//           Y0 = (2/pi)(ln(z/2) + gamma) J0 - (4/pi) sum_k (-1)^k J_2k / k
+//           (Abramowitz & Stegun 9.1.88, 9.12).
+//  z >= 20: Hankel's asymptotic expansion H0^(2)(z) = sqrt(2/(pi z))
+//           (P - i Q) exp(-i (z - pi/4)) with P = sum_k (-1)^k c_2k / (8z)^2k,
+//           Q = sum_k (-1)^(k+1) c_(2k+1) / (8z)^(2k+1),
+//           c_m = prod_{j<=m} (2j-1)^2 / m! (A&S 9.2.5, 9.2.9, 9.2.10), summed
+//           until the terms fall below 1e-17 (their smallest size is about
+//           exp(-2z) < 1e-17 for z >= 20).
+__device__ inline cplx hankel2_0(double z) {
+  const double kPi = 3.141592653589793238462643383;
+  if (z < 20.0) {
+    const int N = 2 * (int)((z + 24.0 + 4.0 * cbrt(z)) * 0.5) + 2;
+    const double iz = 1.0 / z;
+    double jp = 0.0, jn = 1e-30;  // J_{n+1}, J_n (unnormalised), from n = N down
+    double even = 0.0, neu = 0.0;  // sum_k J_2k and sum_k (-1)^k J_2k / k (k >= 1)
+    for (int n = N; n >= 1; --n) {
+      if ((n & 1) == 0) {
+        even += jn;
+        const int k = n >> 1;
+        neu += ((k & 1) ? -jn : jn) / (double)k;
+      }
+      const double jm = 2.0 * n * iz * jn - jp;  // J_{n-1}
+      jp = jn;
+      jn = jm;
+      if (fabs(jn) > 1e250) {  // rescale all running values
+        jp *= 1e-250;
+        jn *= 1e-250;
+        even *= 1e-250;
+        neu *= 1e-250;
+      }
+    }
+    const double norm = 1.0 / (jn + 2.0 * even);
+    const double j0 = jn * norm;
+    const double kGamma = 0.57721566490153286060651209;
+    const double y0 = (2.0 / kPi) * (log(0.5 * z) + kGamma) * j0 - (4.0 / kPi) * neu * norm;
+    return mk(j0, -y0);
+  }
+  const double w = 1.0 / (8.0 * z);
+  double P = 1.0, Q = 0.0, t = 1.0;
+  for (int m = 1; m < 80; ++m) {
+    t *= (double)((2 * m - 1) * (2 * m - 1)) * w / (double)m;
+    const int k = m >> 1;
+    if (m & 1) Q += (k & 1) ? t : -t;  // m = 2k + 1: sign (-1)^(k+1)
+    else P += (k & 1) ? -t : t;        // m = 2k: sign (-1)^k
+    if (t < 1e-17) break;
+  }
+  double sn, cs;
+  sincos(z, &sn, &cs);
+  const double amp = sqrt(2.0 / (kPi * z)) * 0.70710678118654752440;  // and 1/sqrt(2) of exp(i pi/4)
+  // exp(-i (z - pi/4)) = ((cos z + sin z) + i (cos z - sin z)) / sqrt(2)
+  const double er = cs + sn, ei = cs - sn;
+  return mk(amp * (P * er + Q * ei), amp * (P * ei - Q * er));
+}
+
+// EFIE2D kernel H0^(2)(k ||x_i - y_j||) (Sec. 5, kernel 2).
+struct GenHankel2D {
+  __device__ __forceinline__ GenHankel2D bind(int) const { return *this; }
+  using scalar = cplx;
+  const double* x;
+  const double* y;
+  int dim;
+  double k;
+  __device__ __forceinline__ cplx operator()(int64_t i, int64_t j) const {
+    const double* xi = x + i * dim;
+    const double* yj = y + j * dim;
+    double s = 0.0;
+    for (int t = 0; t < dim; ++t) {
+      double u = xi[t] - yj[t];
+      s = fma(u, u, s);
+    }
+    return hankel2_0(k * sqrt(s));
+  }
+};
+
 // Batched Gaussian blocks: each block b has its own points and width; a leaf
 // binds the generator of its block once (batched form of Alg. 2 / Alg. 3).
 struct GenGaussianBatch {

@@ -13,6 +13,7 @@
 // generator.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -114,58 +115,74 @@ __global__ void __launch_bounds__(kErrThreads) errnorm_kernel(const Gen gen, con
 
 int err_grid(int sms) { return (sms > 0 ? sms : 152) * kErrCtasPerSm; }
 
-template <typename Gen>
-cudaError_t launch_err(const Gen& gen, const hbaca_gen& g, const hbaca_result& res, const int64_t* rows, int64_t nrows,
-                       double* part, int grid, cudaStream_t st) {
-  using T = typename Gen::scalar;
-  errnorm_kernel<Gen><<<grid, kErrThreads, 0, st>>>(gen, reinterpret_cast<const T*>(res.U), res.ldu, res.S,
-                                                   reinterpret_cast<const T*>(res.V), res.ldv, (int)res.rank, rows,
-                                                   nrows, g.n, part);
-  return cudaGetLastError();
-}
-
-cudaError_t dispatch_err(const hbaca_gen& g, const hbaca_result& res, const int64_t* rows, int64_t nrows, double* part,
-                         int grid, cudaStream_t st, std::string& err) {
+// Calls f(generator functor) for the generator `g` describes (single block).
+template <typename F>
+cudaError_t visit_gen(const hbaca_gen& g, F&& f, std::string& err) {
   if (g.dtype == HBACA_F64) {
     switch (g.kind) {
       case HBACA_GEN_DENSE:
-        return launch_err(GenDense{reinterpret_cast<const double*>(g.a), g.lda}, g, res, rows, nrows, part, grid, st);
+        return f(GenDense{reinterpret_cast<const double*>(g.a), g.lda});
       case HBACA_GEN_GAUSSIAN: {
         GenGaussian gg;
         gg.x = g.x;
         gg.y = g.y;
         gg.dim = g.dim;
         gg.c = -1.0 / (2.0 * g.h * g.h);
-        return launch_err(gg, g, res, rows, nrows, part, grid, st);
+        return f(gg);
       }
       case HBACA_GEN_SPARSE_PRODUCT:
-        return launch_err(GenSparseProduct{g.p_rowptr, g.p_colidx, g.p_val, g.q_colptr, g.q_rowidx, g.q_val, g.p2,
-                                           g.q2, g.n, g.r2},
-                          g, res, rows, nrows, part, grid, st);
+        return f(GenSparseProduct{g.p_rowptr, g.p_colidx, g.p_val, g.q_colptr, g.q_rowidx, g.q_val, g.p2, g.q2, g.n,
+                                  g.r2});
       case HBACA_GEN_LOWRANK:
-        return launch_err(GenLowRank{reinterpret_cast<const double*>(g.lu), reinterpret_cast<const double*>(g.lv), g.m,
-                                     g.n, g.lr},
-                          g, res, rows, nrows, part, grid, st);
+        return f(GenLowRank{reinterpret_cast<const double*>(g.lu), reinterpret_cast<const double*>(g.lv), g.m, g.n,
+                            g.lr});
+      case HBACA_GEN_POLYNOMIAL:
+        return f(GenPolynomial{g.x, g.y, g.dim, g.h});
       default:
         break;
     }
   } else {
     switch (g.kind) {
       case HBACA_GEN_DENSE:
-        return launch_err(GenDenseC{reinterpret_cast<const cplx*>(g.a), g.lda}, g, res, rows, nrows, part, grid, st);
+        return f(GenDenseC{reinterpret_cast<const cplx*>(g.a), g.lda});
       case HBACA_GEN_HELMHOLTZ:
-        return launch_err(GenHelmholtz{g.x, g.y, g.dim, g.k / 3.14159265358979323846}, g, res, rows, nrows, part,
-                          grid, st);
+        return f(GenHelmholtz{g.x, g.y, g.dim, g.k / 3.14159265358979323846});
       case HBACA_GEN_LOWRANK:
-        return launch_err(GenLowRankC{reinterpret_cast<const cplx*>(g.lu), reinterpret_cast<const cplx*>(g.lv), g.m,
-                                      g.n, g.lr},
-                          g, res, rows, nrows, part, grid, st);
+        return f(GenLowRankC{reinterpret_cast<const cplx*>(g.lu), reinterpret_cast<const cplx*>(g.lv), g.m, g.n,
+                             g.lr});
+      case HBACA_GEN_HANKEL2D:
+        return f(GenHankel2D{g.x, g.y, g.dim, g.k});
       default:
         break;
     }
   }
   err = "generator kind not available for this dtype";
   return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_err(const hbaca_gen& g, const hbaca_result& res, const int64_t* rows, int64_t nrows, double* part,
+                         int grid, cudaStream_t st, std::string& err) {
+  return visit_gen(
+      g,
+      [&](auto gen) -> cudaError_t {
+        using T = typename decltype(gen)::scalar;
+        errnorm_kernel<decltype(gen)><<<grid, kErrThreads, 0, st>>>(gen, reinterpret_cast<const T*>(res.U), res.ldu,
+                                                                    res.S, reinterpret_cast<const T*>(res.V), res.ldv,
+                                                                    (int)res.rank, rows, nrows, g.n, part);
+        return cudaGetLastError();
+      },
+      err);
+}
+
+// An index outside the matrix gives NaN (the entry is not evaluated).
+template <typename Gen>
+__global__ void entries_kernel(const Gen gen, int64_t m, int64_t n, const int64_t* rows, const int64_t* cols,
+                               int64_t count, typename Gen::scalar* out) {
+  using T = typename Gen::scalar;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rows[t], j = cols[t];
+    out[t] = (i >= 0 && i < m && j >= 0 && j < n) ? gen(i, j) : scale(from_re<T>(1.0), __longlong_as_double(0x7ff8000000000000ll));
+  }
 }
 
 }  // namespace
@@ -239,6 +256,32 @@ hbaca_status hbaca_error_norms(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca
   }
   out[0] = s0;
   out[1] = s1;
+  hbaca::record_error(HBACA_OK, "");
+  return HBACA_OK;
+}
+
+hbaca_status hbaca_debug_entries(const hbaca_gen* gen, const int64_t* rows, const int64_t* cols, int64_t count,
+                                 void* out, void* stream) {
+  if (!gen || (count > 0 && (!rows || !cols || !out)) || count < 0)
+    return hbaca::record_error(HBACA_INVALID_ARG, "NULL argument or count < 0");
+  if (count == 0) return HBACA_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::string err;
+  const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
+  cudaError_t e = hbaca::visit_gen(
+      *gen,
+      [&](auto g) -> cudaError_t {
+        using T = typename decltype(g)::scalar;
+        hbaca::entries_kernel<decltype(g)><<<grid, 256, 0, st>>>(g, gen->m, gen->n, rows, cols, count,
+                                                                 reinterpret_cast<T*>(out));
+        return cudaGetLastError();
+      },
+      err);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return hbaca::record_error(err.empty() ? HBACA_CUDA : HBACA_INVALID_ARG,
+                               err.empty() ? std::string("entries kernel: ") + cudaGetErrorString(e) : err);
+  }
   hbaca::record_error(HBACA_OK, "");
   return HBACA_OK;
 }

@@ -1,4 +1,4 @@
-// complex128 instantiation: Helmholtz, low-rank and dense generators.
+// complex128 instantiation: Helmholtz, EFIE2D (Hankel), low-rank and dense generators.
 #include "pipeline.cuh"
 #include "run.h"
 
@@ -21,6 +21,11 @@ cudaError_t run_c128(Plan& p, RunCtx& rc, std::string& err) {
     case HBACA_GEN_LOWRANK: {
       GenLowRankC gl{reinterpret_cast<const cplx*>(g.lu), reinterpret_cast<const cplx*>(g.lv), g.m, g.n, g.lr};
       e = run_baca(p, gl, rc, err);
+      break;
+    }
+    case HBACA_GEN_HANKEL2D: {
+      GenHankel2D gk{g.x, g.y, g.dim, g.k};
+      e = run_baca(p, gk, rc, err);
       break;
     }
     default:

@@ -1,4 +1,4 @@
-// float64 instantiation: Gaussian, sparse-product, low-rank and dense generators.
+// float64 instantiation: Gaussian, polynomial, sparse-product, low-rank and dense generators.
 #include "pipeline.cuh"
 #include "run.h"
 
@@ -26,6 +26,11 @@ cudaError_t run_f64(Plan& p, RunCtx& rc, std::string& err) {
     case HBACA_GEN_LOWRANK: {
       GenLowRank gl{reinterpret_cast<const double*>(g.lu), reinterpret_cast<const double*>(g.lv), g.m, g.n, g.lr};
       e = run_baca(p, gl, rc, err);
+      break;
+    }
+    case HBACA_GEN_POLYNOMIAL: {
+      GenPolynomial gp{g.x, g.y, g.dim, g.h};
+      e = run_baca(p, gp, rc, err);
       break;
     }
     default:

@@ -64,6 +64,20 @@ bool check_gen(const hbaca_gen& g, std::string& err) {
     case HBACA_GEN_LOWRANK:
       if (!g.lu || !g.lv || g.lr < 0) { err = "LOWRANK needs lu, lv, lr >= 0"; return false; }
       break;
+    case HBACA_GEN_POLYNOMIAL:
+      if (g.dtype != HBACA_F64) { err = "POLYNOMIAL is float64"; return false; }
+      if (!g.x || !g.y || g.dim < 1 || g.dim > 1024 || !(g.h == g.h)) {
+        err = "POLYNOMIAL needs x, y, 1 <= dim <= 1024 and a finite h";
+        return false;
+      }
+      break;
+    case HBACA_GEN_HANKEL2D:
+      if (g.dtype != HBACA_C128) { err = "HANKEL2D is complex128"; return false; }
+      if (!g.x || !g.y || g.dim < 1 || g.dim > 64 || !(g.k > 0.0)) {
+        err = "HANKEL2D needs x, y, 1 <= dim <= 64, k > 0";
+        return false;
+      }
+      break;
     default:
       err = "unknown generator kind";
       return false;

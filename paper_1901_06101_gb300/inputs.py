@@ -17,6 +17,10 @@ Workloads (sizes and distributions as the benchmark configurations state):
                      y = U[0,1]^3 cube shifted by a distance U[2,4] along a
                      random unit direction; h log-uniform in [0.1, 10]
   lowrank            U (m x r), V (r x n) with i.i.d. N(0,1) entries
+  polynomial_pair    x_i, y_j i.i.d. N(0, 1/dim) in R^dim            (polynomial kernel)
+  strips_pair        n points on each of two parallel 2-D strips of length 1,
+                     1 apart (segment midpoints), k = 2 pi n / 15 (15 points
+                     per wavelength)                                 (EFIE2D kernel)
 Points are returned in the order drawn (no spatial permutation).
 """
 import numpy as np
@@ -148,3 +152,23 @@ def lowrank(seed, m, n, r, complex_=False):
 def rhs(seed, n, nrhs):
     rng = np.random.default_rng(seed)
     return rng.standard_normal((n, nrhs))
+
+
+def polynomial_pair(seed=4, m=2000, n=2000, dim=50):
+    """Random data points for the polynomial kernel: entries N(0, 1/dim), so
+    that x_i^t y_j is O(1)."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((m, dim)) / np.sqrt(dim)
+    y = rng.standard_normal((n, dim)) / np.sqrt(dim)
+    return x, y
+
+
+def strips_pair(n=2000):
+    """Discretisation points of two parallel strips of length 1 at distance
+    1 (the EFIE2D geometry): midpoints of n equal segments of [0,1] x {0}
+    and of [0,1] x {1}, and the wavenumber giving 15 points per wavelength,
+    k = 2 pi n / 15."""
+    t = (np.arange(n) + 0.5) / n
+    x = np.stack([t, np.zeros(n)], axis=1)
+    y = np.stack([t, np.ones(n)], axis=1)
+    return x, y, 2.0 * np.pi * n / 15.0

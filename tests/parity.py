@@ -29,6 +29,12 @@ def compare_leaf(o, g, eps):
         if nI < len(a["I"]):
             return k, True
         w = a["W"]
+        # a cross at the rounding level, or a kept pivot within 1e4 of it: the
+        # LRID triangle amplifies rounding noise and the two runs' updates
+        # (nu, mu, later pivots) legitimately part ways from here on
+        nz = w.get("noise", 0.0)
+        if w["diag"] and (w["diag"][0] <= 100.0 * nz or (a["dk"] > 0 and min(w["diag"][:a["dk"]]) <= 1e4 * nz)):
+            return k, True
         nW = _prefix_ok(w["marg"])
         assert a["jbar"][:nW] == b["jbar"][:nW], ("jbar", k, a["jbar"], b["jbar"])
         if nW < len(a["jbar"]):
@@ -96,3 +102,11 @@ def near_threshold(s, eps, rel=1e-6):
     if s.size == 0 or s[0] == 0:
         return False
     return bool(np.any(np.abs(s / s[0] - eps) <= rel * eps))
+
+
+def stable_prefix(recs, gtrace):
+    """Number of leading iterations of a leaf before its first rounding-level
+    cross (frozen-pivot replay records), and the BACA rank they add."""
+    k0 = next((k for k, r in enumerate(recs) if r.get("noise_level")), len(recs))
+    k0 = min(k0, len(gtrace))
+    return k0, sum(t["dk"] for t in gtrace[:k0])

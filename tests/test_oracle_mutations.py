@@ -94,3 +94,16 @@ def test_rel_error_last_chunk_dropped(monkeypatch):
         return float(np.linalg.norm(A - (U[keep] * s) @ V) / np.linalg.norm(A))
     monkeypatch.setattr(oapply, "rel_error_dense", bad)
     _expect_failure(pins.test_rel_error_dense_against_direct_norm)
+
+
+def test_hankel_of_the_first_kind(monkeypatch):
+    import scipy.special
+    monkeypatch.setattr(scipy.special, "hankel2", scipy.special.hankel1)
+    _expect_failure(pins.test_hankel2d_generator_published_values)
+
+
+def test_polynomial_without_square(monkeypatch):
+    from oracle import generators as og
+    monkeypatch.setattr(og.Polynomial, "__call__",
+                        lambda self, I, J: self.x[np.asarray(I)] @ self.y[np.asarray(J)].T + self.h)
+    _expect_failure(pins.test_polynomial_generator_closed_form_and_rank)

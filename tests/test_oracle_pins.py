@@ -73,6 +73,45 @@ def test_sparse_product_entries_by_intersection():
     assert np.all((sp.dense_Q() != 0).sum(axis=1) == 14)
 
 
+def test_polynomial_generator_closed_form_and_rank():
+    x = np.array([[1.0, 2.0], [0.0, -1.0]])
+    y = np.array([[3.0, 0.5], [1.0, 1.0]])
+    g = og.Polynomial(x, y, 0.5)
+    want = np.array([[(3.0 + 1.0 + 0.5) ** 2, (1.0 + 2.0 + 0.5) ** 2],
+                     [(0.0 - 0.5 + 0.5) ** 2, (0.0 - 1.0 + 0.5) ** 2]])
+    np.testing.assert_allclose(g([0, 1], [0, 1]), want, rtol=1e-15)
+    # (x^t y + h)^2 = h^2 + 2 h x^t y + (x^t y)^2: rank 1 + dim + dim (dim + 1) / 2
+    xs, ys = inputs.polynomial_pair(seed=1, m=80, n=70, dim=5)
+    A = og.Polynomial(xs, ys, 0.3)(np.arange(80), np.arange(70))
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert ol.eps_rank(sv, 1e-12) == 1 + 5 + 15
+
+
+def test_hankel2d_generator_published_values():
+    """H0^(2) = J0 - i Y0 at the first zeros of J0 and Y0 (Abramowitz &
+    Stegun, Table 9.5: j_01 = 2.404825557695773, y_01 = 0.8935769662791675),
+    the small-argument form Y0(z) ~ (2/pi)(ln(z/2) + gamma), the large-argument
+    amplitude sqrt(2/(pi z)), and the distance r = 5 of a 3-4-5 triangle."""
+    def H(z):
+        return og.Hankel2D(np.zeros((1, 2)), np.array([[z, 0.0]]), 1.0)([0], [0])[0, 0]
+    assert abs(H(2.404825557695773).real) < 1e-15
+    assert abs(H(0.8935769662791675).imag) < 1e-15
+    z = 1e-8
+    gamma = 0.5772156649015329
+    assert abs(H(z) - (1.0 - 1j * (2 / np.pi) * (np.log(z / 2) + gamma))) < 1e-13
+    for z in (1e3, 1e4):
+        assert abs(abs(H(z)) * np.sqrt(np.pi * z / 2) - 1.0) < 1e-3 / z
+    g = og.Hankel2D(np.array([[0.0, 0.0]]), np.array([[3.0, 4.0]]), 2.0)
+    assert g([0], [0])[0, 0] == H(10.0)
+
+
+def test_strips_geometry():
+    x, y, k = inputs.strips_pair(300)
+    assert np.allclose(x[:, 1], 0.0) and np.allclose(y[:, 1], 1.0)
+    assert np.allclose(np.diff(x[:, 0]), 1 / 300) and abs(x[0, 0] - 0.5 / 300) < 1e-15
+    assert abs(2 * np.pi / k - 15 / 300 * 1.0) < 1e-15  # 15 points per wavelength on a strip of length 1
+
+
 # ---------------------------------------------------------------- QRCP
 def _separated(rng, p, N, cplx=False):
     M = rng.standard_normal((p, N)) * np.geomspace(1, 1e-3, N)[rng.permutation(N)]
@@ -385,6 +424,52 @@ def test_rel_error_dense_against_direct_norm():
     # a closed form: U S V = truncated SVD gives the tail of the singular values
     tail = np.sqrt(np.sum(sf[6:] ** 2) / np.sum(sf ** 2))
     assert abs(oapply.rel_error_dense(g, Uf[:, :6], sf[:6], Vf[:6], row_chunk=64) - tail) <= 1e-12
+
+
+class _UlpPerturbed:
+    """A generator whose entries differ from ``gen``'s by -1, 0 or +1 unit in
+    the last place (a fixed pattern): an input change at the rounding level."""
+
+    def __init__(self, gen):
+        self.gen, self.m, self.n, self.dtype = gen, gen.m, gen.n, gen.dtype
+
+    def __call__(self, I, J):
+        A = self.gen(I, J)
+        I, J = np.asarray(I), np.asarray(J)
+        return A + ((I[:, None] * 7919 + J[None, :] * 104729) % 3 - 1) * np.spacing(A)
+
+
+def test_coherent_case_is_rounding_sensitive():
+    """On the coherent sparse product (the benchmark's 6000^2 shape, d = 32,
+    eps = 1e-8) BACA reaches crosses at the rounding level and the LRID
+    triangle amplifies rounding by up to 1/eps: a 1-ulp change of the input
+    changes a leaf's BACA rank by more than 2 and its error by far more than
+    1e-10, in the oracle itself.  So two correct implementations cannot be
+    held to rank +-2 and error 1e-10 on this input past such a cross (the GPU
+    tests compare the prefix before it).  The smooth Gaussian kernel under the
+    same perturbation keeps its rank and its error to 1e-12."""
+    sp = inputs.sparse_product(seed=2, m=6000, n=6000, K=50, density=0.01)
+    g = og.SparseProduct(sp.dense_P(), sp.dense_Q(), sp.P2, sp.Q2)
+    gp = _UlpPerturbed(g)
+    rows = oh.tree_levels(6000, 2)[0]
+    worst_rank, worst_err = 0, 0.0
+    for b in range(4):
+        res = []
+        for gen in (g, gp):
+            w = og.Window(gen, rows[0][0], rows[0][1], rows[b][0], rows[b][1])
+            r = ob.baca(w, 32, 1e-8, seed=2, bid=osamp.block_id(0, 0, b))
+            A = og.Window(g, rows[0][0], rows[0][1], rows[b][0], rows[b][1])(np.arange(1500), np.arange(1500))
+            res.append((r["r"], np.linalg.norm(A - r["U"] @ r["V"]) / np.linalg.norm(A)))
+        worst_rank = max(worst_rank, abs(res[0][0] - res[1][0]))
+        worst_err = max(worst_err, abs(res[0][1] - res[1][1]))
+    assert worst_rank > 2 and worst_err > 1e-6, (worst_rank, worst_err)
+    x, y = inputs.gaussian_pair(seed=0, m=600, n=520)
+    gg = og.Gaussian(x, y, 1.0)
+    r0, r1 = oh.hbaca(gg, 1, 8, 1e-8, seed=0), oh.hbaca(_UlpPerturbed(gg), 1, 8, 1e-8, seed=0)
+    A = gg(np.arange(600), np.arange(520))
+    e0 = np.linalg.norm(A - (r0["U"] * r0["s"]) @ r0["V"]) / np.linalg.norm(A)
+    e1 = np.linalg.norm(A - (r1["U"] * r1["s"]) @ r1["V"]) / np.linalg.norm(A)
+    assert r0["r"] == r1["r"] and abs(e0 - e1) <= 1e-12 * max(e0, 1e-300) + 1e-15
 
 
 # ---------------------------------------------------------------- frozen-pivot replay
