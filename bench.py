@@ -604,7 +604,8 @@ def bench_cfg1(args, dev, flush, stream):
             "rank": r["rank"], "rel_error": err,
             "roofline_whole": {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS, "flops": r["whole_flops"]},
             "roofline_leaf_baca": roofline_of("baca_leaf_kernel", r["leaf_flops"], r["ktimes"]),
-            "phases_ms": r["phases"], "gpu_launches": r["launches"]}
+            "phases_ms": r["phases"], "gpu_launches": r["launches"],
+            "kernel_ms": {kk: v[0] for kk, v in r["ktimes"].items()}}
 
 
 def bench_cfg3(args, dev, flush, stream):
@@ -631,7 +632,8 @@ def bench_cfg3(args, dev, flush, stream):
         torch.cuda.synchronize(dev)
         out[name] = {"d": d, "ms": r["ms"], "rank": r["rank"], "rel_error": err, "wall_s": time.perf_counter() - t0,
                      "entries_per_s": r["entries"] / (r["ms"] / 1e3), "leaf_rank_max": r["res"].res.leaf_rank_max,
-                     "leaf_iters_max": r["res"].res.leaf_iters_max}
+                     "leaf_iters_max": r["res"].res.leaf_iters_max,
+                     "kernel_ms": {kk: v[0] for kk, v in r["ktimes"].items()}, "phases_ms": r["phases"]}
         if d > 1:
             whole = r["whole_flops"] / (r["ms"] / 1e3) / 1e12
             out[name]["roofline_whole"] = {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS}

@@ -299,6 +299,34 @@ size_t hbaca_error_workspace_size(int64_t nrows);
 hbaca_status hbaca_error_norms(hbaca_ctx* ctx, const hbaca_gen* gen, const hbaca_result* res, const int64_t* rows,
                                int64_t nrows, double* out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- Geometry (host only; no device memory, no stream) ----
+
+   KD-tree ordering of n points (HOST, row-major n x dim): perm (HOST, n
+   entries) receives an ordering in which every node of the H-BACA index tree
+   (Alg. 3: a node of s indices has a first child of ceil(s/2)) down to nodes
+   of at most `leaf` points is one side of a split of its parent's points
+   along the widest side of their bounding box.  Compressing A(perm_x,
+   perm_y) is the setting of the paper's experiments (Sec. 5: rows and
+   columns permuted by a KD-tree partitioning), in which every leaf is a
+   spatial cell. */
+hbaca_status hbaca_kdtree_order(const double* points, int64_t n, int32_t dim, int64_t leaf, int64_t* perm);
+
+/* Blocks of a hierarchical-matrix partition of the kernel matrix between
+   ordered point sets x (m x dim) and y (n x dim) (HOST, row-major, each
+   ordered by hbaca_kdtree_order with the same leaf size): the block cluster
+   tree of the two halving trees, a block (tau, sigma) being admissible when
+   min(diam tau, diam sigma) <= eta dist(tau, sigma) (bounding boxes); an
+   inadmissible block is split (its larger side first) until both sides have
+   at most `leaf` points.  blocks (HOST, 5 x max_blocks int64) receives per
+   block (row start, rows, column start, columns, admissible 0/1), in tree
+   order; returns the number of blocks (-1 on invalid arguments; blocks may
+   be NULL to query the count).  The blocks tile the matrix.  Every
+   admissible block is a low-rank block for H-BACA (Sec. 1: H-BACA as the
+   compression tool of hierarchical matrices); hbaca_compress_batched
+   compresses them all in one call. */
+int64_t hbaca_hmatrix_blocks(const double* x, int64_t m, const double* y, int64_t n, int32_t dim, int64_t leaf,
+                             double eta, int64_t* blocks, int64_t max_blocks);
+
 /* Per-leaf record of one BACA run (Alg. 2), copied to HOST arrays provided
    by the caller.  Leaf (a, b) of the 2^L x 2^L partition has index
    a * 2^L + b.  Arrays I, J, jbar hold `max_iters * d` entries (row-major by

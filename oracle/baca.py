@@ -279,6 +279,16 @@ def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
         rec["valid_dk"] = ok
         if dk > 0:
             T = np.triu(Q.conj().T @ W[:, piv])
+            if np.any(np.diag(T) == 0.0):
+                # a forced pivot whose residual is exactly zero in this
+                # arithmetic (the recorded run saw rounding noise there): T^-1
+                # of LRID does not exist here, as for ACA's zero pivot (Alg. 1
+                # line 5); the record is at the rounding level and the replay
+                # ends with it
+                rec["noise_level"] = True
+                rec["singular_T"] = True
+                recs.append(rec)
+                break
             Uk = C[:, piv]
             Vk = scipy.linalg.solve_triangular(T, Q.conj().T @ R, lower=False)
             nu = lrnorm(Uk, Vk)

@@ -126,6 +126,11 @@ SIGNATURES = [
     ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
+    ("hbaca_kdtree_order", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_void_p]),
+    ("hbaca_hmatrix_blocks", ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
+                                              ctypes.c_int64]),
     ("hbaca_debug_read_leaf_factors", ctypes.c_int, [ctypes.POINTER(Gen), ctypes.POINTER(Opts), ctypes.c_void_p,
                                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
      + [ctypes.POINTER(ctypes.c_int64)] * 3 + [ctypes.c_void_p]),
@@ -686,6 +691,33 @@ def read_block(spec, opts, ws, store, level, block):
     U = Ub[:bm * r].reshape(r, bm).T
     V = Vb[:r * bn].reshape(r, bn)
     return U, Sb[:r], V
+
+
+def kdtree_order(points, leaf):
+    """hbaca_kdtree_order: a permutation (numpy int64) ordering the points so
+    that every H-BACA index-tree node down to `leaf` points is a KD cell."""
+    import numpy as np
+    P = np.ascontiguousarray(np.asarray(points, np.float64))
+    perm = np.empty(P.shape[0], np.int64)
+    check(lib().hbaca_kdtree_order(P.ctypes.data_as(ctypes.c_void_p), P.shape[0], P.shape[1], int(leaf),
+                                   perm.ctypes.data_as(ctypes.c_void_p)))
+    return perm
+
+
+def hmatrix_blocks(x, y, leaf, eta):
+    """hbaca_hmatrix_blocks for ordered point sets x, y: an (nblocks, 5) int64
+    array of (row start, rows, column start, columns, admissible)."""
+    import numpy as np
+    X = np.ascontiguousarray(np.asarray(x, np.float64))
+    Y = np.ascontiguousarray(np.asarray(y, np.float64))
+    args = (X.ctypes.data_as(ctypes.c_void_p), X.shape[0], Y.ctypes.data_as(ctypes.c_void_p), Y.shape[0],
+            X.shape[1], int(leaf), float(eta))
+    n = lib().hbaca_hmatrix_blocks(*args, None, 0)
+    if n < 0:
+        raise HbacaError(1, lib().hbaca_last_error().decode())
+    out = np.empty((n, 5), np.int64)
+    lib().hbaca_hmatrix_blocks(*args, out.ctypes.data_as(ctypes.c_void_p), n)
+    return out
 
 
 def read_leaf_factors(spec, opts, ws, leaf, m_leaf, n_leaf):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhbaca.so")
-SOURCES = ["hbaca_f64.cu", "hbaca_c128.cu", "plan.cpp", "api.cpp", "probe.cu", "noalloc.cu", "adjoint.cu", "errnorm.cu"]
+SOURCES = ["hbaca_f64.cu", "hbaca_c128.cu", "plan.cpp", "api.cpp", "probe.cu", "noalloc.cu", "adjoint.cu", "errnorm.cu", "hmatrix.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -560,17 +560,34 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
 // Rotation of one Jacobi pair from alpha = |a|^2, beta = |b|^2, gamma = a^H b.
 // Returns false when the pair counts as orthogonal: |gamma| below tol times
 // |a| |b|, or both columns negligible, or a column in the denormal range.
+//
+// The chain runs on one thread per pair while the CTA's other warps wait, so
+// it uses reciprocal square roots and reciprocals only (no divisions or
+// square roots): gamma is scaled by its larger component so that
+// q = |gamma / mx|^2 lies in [1, 2]; |gamma| = mx q rsqrt(q) and the phase
+// conj(gamma) / |gamma| = conj(gamma / mx) rsqrt(q), unit to a few ulp.  The
+// angle tan = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha)
+// / (2 |gamma|), need not be exact: cs = rsqrt(1 + tan^2) and sn = cs tan
+// make an orthogonal rotation to a few ulp whatever the rounding of tan.
 template <typename T>
 __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, double tol, double negl, double fro2,
                                                 double& cs, double& sn, T& ph) {
-  const double g = absval(ga);
-  if (g == 0.0 || al < 1e-290 || be < 1e-290 || fmax(al, be) < negl) return false;
-  if (g <= tol * sqrt(al) * sqrt(be)) return false;
-  const double zeta = (be - al) / (2.0 * g);
-  const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  cs = 1.0 / sqrt(1.0 + tt * tt);
+  if (al < 1e-290 || be < 1e-290 || fmax(al, be) < negl) return false;
+  const double mx = fmax(fabs(re_(ga)), fabs(im_(ga)));
+  if (mx == 0.0) return false;
+  const double rm = __drcp_rn(mx);
+  const double gr = re_(ga) * rm, gi = im_(ga) * rm;
+  const double q = fma(gr, gr, gi * gi);
+  const double rq = rsqrt(q);
+  const double g = mx * (q * rq);                               // |gamma|
+  if (g * rsqrt(al) * rsqrt(be) <= tol) return false;           // |gamma| <= tol |a| |b|
+  const double zeta = (be - al) * 0.5 * (rm * rq);              // (beta - alpha) / (2 |gamma|)
+  const double z2 = fma(zeta, zeta, 1.0);
+  const double tt = copysign(__drcp_rn(fabs(zeta) + z2 * rsqrt(z2)), zeta);
+  cs = rsqrt(fma(tt, tt, 1.0));
   sn = cs * tt;
-  ph = conj_phase(ga, g);  // e^{-i phi} exactly unit, gamma = |gamma| e^{i phi}
+  if constexpr (Traits<T>::is_complex) ph = mk(gr * rq, -gi * rq);  // e^{-i phi}, gamma = |gamma| e^{i phi}
+  else ph = gr >= 0.0 ? 1.0 : -1.0;
   return true;
 }
 
