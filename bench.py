@@ -557,6 +557,11 @@ def run_ours(args, rank, world):
     res = B.compress(ctx, spec, opts, ws=ws, out=out)
     torch.cuda.synchronize(dev)
     ktimes = B.kernel_times(ctx)
+    stage_ms = {}
+    for kname, st, _, kms in B.launch_times(ctx):
+        key = "leaf_baca" if st < 0 else "stage%d" % st
+        stage_ms.setdefault(key, {}).setdefault(kname, 0.0)
+        stage_ms[key][kname] += kms
     plan = B.plan_json(spec, opts)
     dims = task_dims(ws, plan)
     jac_own = jacobi_accounting(ws, plan, True)
@@ -580,7 +585,7 @@ def run_ours(args, rank, world):
              "unit": "TFLOP/s", "flop_count": "leaf and merge work count of the measurement plan (r, s measured)"}
     return dict(value=value, ms=ms_max, entries=entries, flops=flops, rank=rank, phases=phases, roof=roof,
                 roof_baca=roofs["baca_leaf_kernel"], kernel_ms={kk: v[0] for kk, v in ktimes.items()},
-                jacobi_stages=jac_stages, whole=whole,
+                jacobi_stages=jac_stages, whole=whole, stage_ms=stage_ms,
                 launches=launches, clocks=clk.summary(), wall=wall, e2e=dict(value=e2e_value, unit="entries/s",
                 h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, seconds_per_step=e2e_s), x=x, y=y)
 
@@ -606,6 +611,30 @@ def bench_cfg1(args, dev, flush, stream):
             "roofline_leaf_baca": roofline_of("baca_leaf_kernel", r["leaf_flops"], r["ktimes"]),
             "phases_ms": r["phases"], "gpu_launches": r["launches"],
             "kernel_ms": {kk: v[0] for kk, v in r["ktimes"].items()}}
+
+
+def bench_cfg2_kd(args, dev, flush, stream):
+    """The benchmark matrix with both point sets in KD-tree order (the
+    setting of the paper's experiments, Sec. 5): the same matrix up to a
+    permutation of rows and columns, whose leaves are spatial cells."""
+    import torch
+    from paper_1901_06101_gb300 import binding as B
+    from paper_1901_06101_gb300 import inputs
+    cfg = WORKLOADS["helmholtz20000"]
+    x, y = inputs.sphere_pair(seed=cfg["seed"], m=cfg["m"], n=cfg["n"])
+    leaf = cfg["m"] >> cfg["levels"]
+    xo, yo = x[B.kdtree_order(x, leaf)], y[B.kdtree_order(y, leaf)]
+    ctx = B.Context()
+    spec = B.helmholtz(xo, yo, cfg["k"])
+    opts = mk_opts(cfg["eps"], cfg["d"], cfg["levels"], seed=cfg["seed"], rank_cap=cfg["rank_cap"],
+                   leaf_rank_cap=cfg["leaf_rank_cap"])
+    r = measure_single(B, ctx, spec, opts, cfg["rank_cap"], cfg["m"], cfg["n"], cfg["levels"], cfg["d"], True,
+                       max(3, min(args.steps, 5)), 3, flush, stream, dev)
+    err = B.rel_error(ctx, spec, r["res"])
+    torch.cuda.synchronize(dev)
+    return {"workload": cfg["workload"] + "_kdtree_order", "ms": r["ms"], "entries_per_s": r["entries"] / (r["ms"] / 1e3),
+            "rank": r["rank"], "rel_error": err, "leaf_rank_max": r["res"].res.leaf_rank_max,
+            "phases_ms": r["phases"], "kernel_ms": {kk: v[0] for kk, v in r["ktimes"].items()}}
 
 
 def bench_cfg3(args, dev, flush, stream):
@@ -754,6 +783,7 @@ def extra_configs(args, dev):
     stream = torch.cuda.current_stream(dev)
     out = {}
     jobs = [("cfg1", lambda: bench_cfg1(args, dev, flush, stream)),
+            ("cfg2_kd_order", lambda: bench_cfg2_kd(args, dev, flush, stream)),
             ("cfg3", lambda: bench_cfg3(args, dev, flush, stream)),
             ("cfg4", lambda: batched_measure(4096, args.loop_blocks, 2, 1, flush, stream, dev)),
             ("cfg5", lambda: grad_measure(3, 2, flush, stream, dev))]
@@ -936,7 +966,7 @@ def main():
             "roofline": r["roof"], "roofline_whole": r["whole"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"], "phases_ms": r["phases"], "rank": r["rank"],
             "roofline_leaf_baca": r["roof_baca"], "kernel_ms": r["kernel_ms"],
-            "jacobi_stages": r["jacobi_stages"], "entries_per_step": r["entries"]}
+            "jacobi_stages": r["jacobi_stages"], "stage_kernel_ms": r["stage_ms"], "entries_per_step": r["entries"]}
     line.update(extra)
     print(json.dumps(line))
 

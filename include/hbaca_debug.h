@@ -37,6 +37,15 @@ hbaca_status hbaca_debug_read_leaf_factors(const hbaca_gen* gen, const hbaca_opt
                                            int64_t leaf, void* U, void* V, int64_t* m_out, int64_t* n_out,
                                            int64_t* rank_out, void* stream);
 
+/* Every launch of the last call made with HBACA_FLAG_PROFILE on `ctx`: its
+   kernel class (the order of hbaca_kernel_times), its stage (the index of the
+   re-compression or merge stage in plan order; -1 for the leaf BACA launch),
+   its start and its duration in ms (CUDA events on the launching stream,
+   start relative to the call's first event).  Fills at most `max` entries of
+   each (NULL arrays are skipped) and returns the number of launches, or -1. */
+int32_t hbaca_debug_launch_times(hbaca_ctx* ctx, int32_t* cls, int32_t* stage, double* start_ms, double* ms,
+                                 int32_t max);
+
 /* Write a JSON description of the workspace layout of (gen, opts) (region
    byte offsets, stage task tables) into buf (NUL-terminated, truncated to
    len).  Returns the length the full text needs. */

@@ -126,6 +126,8 @@ SIGNATURES = [
     ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
+    ("hbaca_debug_launch_times", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_int32]),
     ("hbaca_kdtree_order", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_void_p]),
     ("hbaca_hmatrix_blocks", ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
@@ -771,6 +773,22 @@ def kernel_times(ctx):
     nl = (ctypes.c_int32 * len(KERNEL_CLASSES))()
     check(lib().hbaca_kernel_times(ctx.ptr, ms, nl))
     return {k: (ms[i], nl[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def launch_times(ctx):
+    """Per launch of the last profiled call: list of (kernel class name, stage,
+    start ms, ms)."""
+    import numpy as np
+    n = lib().hbaca_debug_launch_times(ctx.ptr, None, None, None, None, 0)
+    if n < 0:
+        raise HbacaError(1, lib().hbaca_last_error().decode())
+    cls = np.zeros(n, np.int32)
+    stg = np.zeros(n, np.int32)
+    t0 = np.zeros(n)
+    ms = np.zeros(n)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    lib().hbaca_debug_launch_times(ctx.ptr, p(cls), p(stg), p(t0), p(ms), n)
+    return [(KERNEL_CLASSES[c], int(s), float(a), float(b)) for c, s, a, b in zip(cls, stg, t0, ms)]
 
 
 def phase_times(ctx):

@@ -592,6 +592,36 @@ int32_t hbaca_debug_set_jacobi_sweeps(int32_t sweeps) {
   return g_jacobi_sweeps.exchange(v);
 }
 
+int32_t hbaca_debug_launch_times(hbaca_ctx* ctx, int32_t* cls, int32_t* stage, double* start_ms, double* ms,
+                                 int32_t max) {
+  if (!ctx || !ctx->have_times) {
+    tls_err = "the last call did not run with HBACA_FLAG_PROFILE";
+    return -1;
+  }
+  if (cudaEventSynchronize(ctx->ev[3]) != cudaSuccess) {
+    cudaGetLastError();
+    tls_err = "event synchronisation failed";
+    return -1;
+  }
+  const int n = (int)ctx->kt.marks.size();
+  for (int i = 0; i < n && i < max; ++i) {
+    const auto& mk = ctx->kt.marks[i];
+    float t0 = 0.f, t1 = 0.f;
+    if (cudaEventElapsedTime(&t0, ctx->ev[0], ctx->kt.pool[mk.second]) != cudaSuccess ||
+        cudaEventElapsedTime(&t1, ctx->ev[0], ctx->kt.pool[mk.second + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      tls_err = "event timing failed";
+      return -1;
+    }
+    if (cls) cls[i] = mk.first;
+    if (stage) stage[i] = ctx->kt.mark_stage[i];
+    if (start_ms) start_ms[i] = t0;
+    if (ms) ms[i] = (double)t1 - t0;
+  }
+  tls_err.clear();
+  return n;
+}
+
 size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char* buf, size_t len) {
   if (!gen || !opts) return 0;
   hbaca::Plan p;

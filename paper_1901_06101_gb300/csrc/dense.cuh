@@ -592,7 +592,11 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, doub
 }
 
 constexpr int kJacRegs = 8;  // columns of up to 256 rows are held in registers
-constexpr int kJacKeep = 5;  // columns of up to 160 rows stay in registers from (1) to (3)
+// columns of up to 32 * JacKeep<T>::n rows stay in registers from (1) to (3)
+// (real data; complex columns are re-read, which keeps the kernel within the
+// registers of three resident CTAs per SM)
+template <typename T> struct JacKeep { static constexpr int n = 5; };
+template <> struct JacKeep<cplx> { static constexpr int n = 0; };
 
 // Loads of the Jacobi sweeps: columns in another CTA's shared memory are read
 // with plain (distributed shared memory) loads, columns in global memory
@@ -663,7 +667,8 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
   const int stride = c * nw;                             // pairs dealt per pass over the cluster's warps
   const int per_warp = (npairs + stride - 1) / stride;   // passes (pairs per warp) per round
   const bool regs = mr <= 32 * kJacRegs;
-  const bool keep = mr <= 32 * kJacKeep;
+  constexpr int kJacKeep = JacKeep<T>::n > 0 ? JacKeep<T>::n : 1;
+  const bool keep = JacKeep<T>::n > 0 && mr <= 32 * JacKeep<T>::n;
   auto pair_of = [&](int rd, int pi, int& a, int& b) {
     // circle method: pair 0 = (rd, K-1), pair i = ((rd+i) mod (K-1), (rd-i+K-1) mod (K-1))
     if (pi == 0) { a = rd; b = K - 1; }
@@ -796,7 +801,7 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DenseParams<T> P, int max_sweeps,
+__global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DenseParams<T> P, int max_sweeps,
                                                                    int hdr_bytes, int slot_off, int64_t dsm_bytes,
                                                                    const int32_t* task_list) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -826,14 +831,15 @@ __global__ void __launch_bounds__(kDenseThreads, 2) jacobi_kernel(const DensePar
   }
   // the task's columns fit the cluster's shared memory: sweep there (column j
   // in CTA j mod c), else in global memory
-  const int per = (nc + c - 1) / c;
-  const int64_t ldc = (int64_t)mr + nc;
-  T* dsm = reinterpret_cast<T*>(smem_raw + hdr_bytes);
-  const bool use_dsm = (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
   // the rotations are accumulated (W) only for a taped output, which keeps
   // every triplet; otherwise the kept right vectors of X are recovered from
-  // X^H z_i = sigma_i w_i after the sweeps (wsolve_kernel)
+  // X^H z_i = sigma_i w_i after the sweeps (wsolve_kernel), and a column's
+  // shared-memory slot holds X alone
   const bool acc_w = P.out_blocks[t.out].full_slot >= 0;
+  const int per = (nc + c - 1) / c;
+  const int64_t ldc = (int64_t)mr + (acc_w ? nc : 0);
+  T* dsm = reinterpret_cast<T*>(smem_raw + hdr_bytes);
+  const bool use_dsm = (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
   if (use_dsm) {  // own columns: X from global memory, W = I
     for (int l = warp; l < per; l += nw) {
       const int j = l * c + q;

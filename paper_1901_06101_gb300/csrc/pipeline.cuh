@@ -169,6 +169,7 @@ cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
 template <typename T>
 cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string& err) {
   char* ws = rc.ws;
+  if (rc.kt) rc.kt->stage = si;
   char* desc = ws + p.desc_region.off;
   DenseParams<T> D;
   D.tasks = reinterpret_cast<const SvdTask*>(desc + sg.tasks_off);
@@ -312,7 +313,8 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     auto share_of = [&](int i, int cc) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int nc = std::min(dh[i].kra, ncm), mr = ncm;
-      return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + nc) * sizeof(T);
+      // a column's slot: X (mr rows), and W (nc rows) when the call is taped
+      return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + (p.tape ? nc : 0)) * sizeof(T);
     };
     auto fit = [&](int i, int cc) {
       while (cc < 16 && share_of(i, cc) + j_hdr_of(cc) > kJacobiSmemLimit) ++cc;

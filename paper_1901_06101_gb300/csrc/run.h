@@ -22,8 +22,10 @@ enum KernelClass {
 struct KernelTimer {
   std::vector<cudaEvent_t> pool;
   std::vector<std::pair<int, size_t>> marks;  // (class, index of the start event; the stop is next)
+  std::vector<int> mark_stage;                // stage of each mark (-1: the leaf BACA launch)
+  int stage = -1;                             // stage whose launches are being recorded
   size_t used = 0;
-  void reset() { marks.clear(); used = 0; }
+  void reset() { marks.clear(); mark_stage.clear(); stage = -1; used = 0; }
   cudaError_t record(cudaStream_t st) {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -35,6 +37,7 @@ struct KernelTimer {
   }
   cudaError_t begin(int cls, cudaStream_t st) {
     marks.emplace_back(cls, used);
+    mark_stage.push_back(stage);
     return record(st);
   }
   cudaError_t end(cudaStream_t st) { return record(st); }

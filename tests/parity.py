@@ -7,11 +7,11 @@ import numpy as np
 MARGIN = 1e-9
 
 
-def _prefix_ok(margins):
-    """Number of leading decisions with a unique margin."""
+def _prefix_ok(margins, thr=MARGIN):
+    """Number of leading decisions with a margin above thr."""
     n = 0
     for m in margins:
-        if not (m > MARGIN):
+        if not (m > thr):
             break
         n += 1
     return n
@@ -19,12 +19,21 @@ def _prefix_ok(margins):
 
 def compare_leaf(o, g, eps):
     """o: oracle baca() dict, g: binding.read_leaf_trace() dict.
-    Returns (iterations compared, diverged flag)."""
+    Returns (iterations compared, diverged flag).
+
+    A decision counts as unique when its margin exceeds 1e-9, raised to
+    1e-13 mu_j / nu_j for the largest ratio of the iterations before it: the
+    residual A - U V is formed with cancellation of that size (the update of
+    iteration j is nu_j against an accumulated approximation of norm mu_j),
+    so two correct runs' residuals differ by about eps_mach mu / nu
+    relative."""
     ot, gt = o["trace"], g["trace"]
+    amp = 1.0
     for k in range(min(len(ot), len(gt))):
         a, b = ot[k], gt[k]
         assert a["J"] == b["J"], ("J", k, a["J"], b["J"])
-        nI = _prefix_ok(a["Imarg"])
+        thr = max(MARGIN, 1e-13 * amp)
+        nI = _prefix_ok(a["Imarg"], thr)
         assert a["I"][:nI] == b["I"][:nI], ("I", k, a["I"], b["I"])
         if nI < len(a["I"]):
             return k, True
@@ -35,7 +44,7 @@ def compare_leaf(o, g, eps):
         nz = w.get("noise", 0.0)
         if w["diag"] and (w["diag"][0] <= 100.0 * nz or (a["dk"] > 0 and min(w["diag"][:a["dk"]]) <= 1e4 * nz)):
             return k, True
-        nW = _prefix_ok(w["marg"])
+        nW = _prefix_ok(w["marg"], thr)
         assert a["jbar"][:nW] == b["jbar"][:nW], ("jbar", k, a["jbar"], b["jbar"])
         if nW < len(a["jbar"]):
             return k, True
@@ -51,11 +60,13 @@ def compare_leaf(o, g, eps):
         # nu, mu are norms of the same low-rank blocks
         assert abs(a["mu"] - b["mu"]) <= 1e-9 * max(a["mu"], 1e-300), ("mu", k, a["mu"], b["mu"])
         assert abs(a["nu"] - b["nu"]) <= 1e-9 * max(a["mu"], 1e-300), ("nu", k, a["nu"], b["nu"])
-        nJ = _prefix_ok(a["Jmarg"])
+        nJ = _prefix_ok(a["Jmarg"], thr)
         if k + 1 < len(ot) and k + 1 < len(gt):
             assert ot[k + 1]["J"][:nJ] == gt[k + 1]["J"][:nJ], ("Jnext", k)
         if nJ < len(a["Jnext"]):
             return k + 1, True
+        if a["nu"] > 0.0:
+            amp = max(amp, a["mu"] / a["nu"])
     assert len(ot) == len(gt), ("iterations", len(ot), len(gt))
     assert o["r"] == g["rank_baca"], ("rank", o["r"], g["rank_baca"])
     return len(ot), False

@@ -70,7 +70,7 @@ def test_polynomial_dim50(ctx):
     x, y = inputs.polynomial_pair(seed=6, m=2000, n=2000, dim=50)
     spec = B.polynomial(x, y, 1.0)
     ogen = og.Polynomial(x, y, 1.0)
-    res, compared, div, tr = run_and_compare(ctx, spec, ogen, 1, 16, 1e-3, seed=4, rank_cap=1024, leaf_cap=512)
+    res, compared, div, tr = run_and_compare(ctx, spec, ogen, 1, 16, 1e-3, seed=4, rank_cap=1024, leaf_cap=1000)
     full = oh.hbaca(ogen, 1, 16, 1e-3, seed=4, forced=tr)
     compare_with_frozen_oracle(res, full, ogen, tr)
 
