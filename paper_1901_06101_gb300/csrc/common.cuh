@@ -36,6 +36,9 @@ __device__ __forceinline__ double im_(double) { return 0.0; }
 __device__ __forceinline__ double im_(cplx a) { return a.im; }
 __device__ __forceinline__ double abs2(double a) { return a * a; }
 __device__ __forceinline__ double abs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
+// acc + |a|^2 as fused multiply-adds
+__device__ __forceinline__ double acc_abs2(double acc, double a) { return fma(a, a, acc); }
+__device__ __forceinline__ double acc_abs2(double acc, cplx a) { return fma(a.re, a.re, fma(a.im, a.im, acc)); }
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ cplx add(cplx a, cplx b) { return mk(a.re + b.re, a.im + b.im); }
 __device__ __forceinline__ double sub(double a, double b) { return a - b; }

@@ -561,29 +561,49 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
 // Returns false when the pair counts as orthogonal: |gamma| below tol times
 // |a| |b|, or both columns negligible, or a column in the denormal range.
 //
-// The chain runs on one thread per pair while the CTA's other warps wait, so
-// it uses reciprocal square roots and reciprocals only (no divisions or
-// square roots): gamma is scaled by its larger component so that
-// q = |gamma / mx|^2 lies in [1, 2]; |gamma| = mx q rsqrt(q) and the phase
-// conj(gamma) / |gamma| = conj(gamma / mx) rsqrt(q), unit to a few ulp.  The
-// angle tan = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha)
-// / (2 |gamma|), need not be exact: cs = rsqrt(1 + tan^2) and sn = cs tan
-// make an orthogonal rotation to a few ulp whatever the rounding of tan.
+// The chain runs on one thread per pair while the CTA's other warps wait (and
+// an FP64 instruction costs the same pipe time whatever the number of active
+// lanes), so its FP64 part is kept short.  Only two quantities must be
+// accurate to a few ulp: the phase e^{-i phi} = conj(gamma) / |gamma| and the
+// cosine-sine pair (cs^2 + sn^2 = 1), which make the rotation unitary; the
+// angle itself only decides how much of gamma the rotation removes, and a
+// relative error of 1e-7 there leaves a residual inner product of 1e-7 gamma
+// that later sweeps remove (the convergence test is on the inner products
+// the sweeps form, not on the angle).  So gamma is scaled by the power of two
+// below its larger component (exact), q = |gamma / 2^e|^2 lies in [1, 4),
+// and phase = conj(gamma / 2^e) rsqrt(q) in FP64; the tangent
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha) /
+// (2 |gamma|), is formed in FP32 (in FP64 as 1 / (2 zeta) when |zeta| > 2^30)
+// and widened exactly to FP64, where cs = rsqrt(1 + t^2) and sn = cs t.
+__device__ __forceinline__ double pow2_below(double v) {  // 2^floor(log2 v), v > 0 normal
+  return __longlong_as_double(__double_as_longlong(v) & 0x7ff0000000000000ll);
+}
+__device__ __forceinline__ double pow2_inverse(double p2) {  // 1 / p2 for a power of two in the normal range
+  return __longlong_as_double(0x7fe0000000000000ll - __double_as_longlong(p2));
+}
+
 template <typename T>
 __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, double tol, double negl, double fro2,
                                                 double& cs, double& sn, T& ph) {
   if (al < 1e-290 || be < 1e-290 || fmax(al, be) < negl) return false;
   const double mx = fmax(fabs(re_(ga)), fabs(im_(ga)));
-  if (mx == 0.0) return false;
-  const double rm = __drcp_rn(mx);
+  if (!(mx >= 1e-300)) return false;                            // zero (or denormal) gamma
+  const double rm = pow2_inverse(pow2_below(mx));               // exact: mx rm in [1, 2)
   const double gr = re_(ga) * rm, gi = im_(ga) * rm;
-  const double q = fma(gr, gr, gi * gi);
+  const double q = fma(gr, gr, gi * gi);                        // |gamma rm|^2 in [1, 4)
+  if (q < (tol * tol) * (al * rm) * (be * rm)) return false;    // |gamma| <= tol |a| |b|
   const double rq = rsqrt(q);
-  const double g = mx * (q * rq);                               // |gamma|
-  if (g * rsqrt(al) * rsqrt(be) <= tol) return false;           // |gamma| <= tol |a| |b|
-  const double zeta = (be - al) * 0.5 * (rm * rq);              // (beta - alpha) / (2 |gamma|)
-  const double z2 = fma(zeta, zeta, 1.0);
-  const double tt = copysign(__drcp_rn(fabs(zeta) + z2 * rsqrt(z2)), zeta);
+  // zeta = (beta - alpha) / (2 |gamma|), |gamma| = sqrt(q) / rm; for
+  // |zeta| > 2^30 the tangent is 1 / (2 zeta) to double precision (and the
+  // FP32 form would lose it), formed in FP64
+  const double zeta = (be - al) * rm * 0.5 * rq;
+  double tt;
+  if (fabs(zeta) > 1073741824.0) {
+    tt = __drcp_rn(2.0 * zeta);
+  } else {
+    const float zf = (float)zeta;
+    tt = (double)copysignf(1.0f / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f))), zf);
+  }
   cs = rsqrt(fma(tt, tt, 1.0));
   sn = cs * tt;
   if constexpr (Traits<T>::is_complex) ph = mk(gr * rq, -gi * rq);  // e^{-i phi}, gamma = |gamma| e^{i phi}
@@ -705,8 +725,8 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
               if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
                 const T xa = i < mr ? jld<T, kDsm>(ca + i) : Traits<T>::zero();
                 const T xb = i < mr ? jld<T, kDsm>(cb + i) : Traits<T>::zero();
-                al += abs2(xa);
-                be += abs2(xb);
+                al = acc_abs2(al, xa);
+                be = acc_abs2(be, xb);
                 ga = cmac(ga, xa, xb);
                 if (u < kJacKeep && j == 0) {
                   ka[u < kJacKeep ? u : 0] = xa;
@@ -717,8 +737,8 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
           } else {
             for (int i = lane; i < mr; i += 32) {
               const T xa = jld<T, kDsm>(ca + i), xb = jld<T, kDsm>(cb + i);
-              al += abs2(xa);
-              be += abs2(xb);
+              al = acc_abs2(al, xa);
+              be = acc_abs2(be, xb);
               ga = cmac(ga, xa, xb);
             }
           }

@@ -325,13 +325,18 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       const size_t sh = share_of(i, cc) + j_hdr_of(cc) <= kJacobiSmemLimit ? share_of(i, cc) : 0;
       need[cc] = std::max(need[cc], sh);
     };
+    // a stage with fewer than sms / 32 cores leaves most SMs idle whatever
+    // the cluster size: its cores take 16-CTA clusters, so that a round's FP64
+    // work is spread over as many SMs as a cluster can hold (with 8 cores of
+    // 16 CTAs the clusters share SMs and the stage ran slower)
+    const bool few = (int64_t)nt * 16 * 2 < rc.sms;
     for (int i = 0; i < nt; ++i) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int pairs = (std::min(dh[i].kra, ncm) + 1) / 2;
       int g = 0;
       while (g < 4 && (1 << (g + 1)) * wpc <= pairs) ++g;
       c_pow[i] = fit(i, 1 << g);
-      c_one[i] = fit(i, std::min(16, std::max(1, (pairs + wpc - 1) / wpc)));
+      c_one[i] = fit(i, few && pairs >= 16 ? 16 : std::min(16, std::max(1, (pairs + wpc - 1) / wpc)));
       add_task(i, c_one[i]);
     }
     for (int cc = 1; cc <= 16; ++cc) {

@@ -27,7 +27,7 @@ def ctx():
 
 
 def run_and_compare(ctx, spec, ogen, L, d, eps, seed=0, rank_cap=128, leaf_cap=256, cluster=0,
-                    check_all_leaves=True, dense=True):
+                    check_all_leaves=True, dense=True, free_compare=True):
     """Run the CUDA path; for every checked leaf (1) compare its pivots with a
     free oracle run while decisions are unique by margin, (2) replay its
     pivots through the oracle and require every choice valid and the norms
@@ -50,10 +50,11 @@ def run_and_compare(ctx, spec, ogen, L, d, eps, seed=0, rank_cap=128, leaf_cap=2
         bid = osamp.block_id(0, a, b)
         g = B.read_leaf_trace(spec, opts, res.ws, leaf)
         traces[leaf] = g
-        o = ob.baca(w, d, eps, seed=seed, bid=bid)
-        k, div = compare_leaf(o, g, eps)
-        compared += k
-        diverged += div
+        if free_compare:
+            o = ob.baca(w, d, eps, seed=seed, bid=bid)
+            k, div = compare_leaf(o, g, eps)
+            compared += k
+            diverged += div
         rep = check_leaf_replay(w, g, d, eps, seed, bid)
         if not rep["comparable"]:
             diverged += 1
@@ -240,7 +241,12 @@ def test_sparse_product_coherent_cfg3_shape(ctx, d):
     sp = inputs.sparse_product(seed=2, m=6000, n=6000, K=50, density=0.01)
     og_ = og.SparseProduct(sp.dense_P(), sp.dense_Q(), sp.P2, sp.Q2)
     spec = B.sparse_product(sp)
-    res, compared, div, tr = run_and_compare(ctx, spec, og_, 2, d, 1e-8, seed=2, rank_cap=512, leaf_cap=512)
+    # plain ACA on this matrix moves by more than its pivot margins under a
+    # 1-ulp input change (test_oracle_pins.test_coherent_case_is_rounding_sensitive),
+    # so its pivots are checked by the frozen-pivot replay alone (every GPU
+    # choice a valid greedy choice up to rounding)
+    res, compared, div, tr = run_and_compare(ctx, spec, og_, 2, d, 1e-8, seed=2, rank_cap=512, leaf_cap=512,
+                                             free_compare=d > 1)
     check_orthonormal(res)
     whole = compare_stable_prefixes(ctx, spec, og_, 2, d, 1e-8, 2, 512, 512, range(16), tr)
     A = og_(np.arange(og_.m), np.arange(og_.n))
