@@ -74,6 +74,14 @@ int64_t hbaca_debug_backward_json(const hbaca_gen* gen, const hbaca_opts* opts, 
 hbaca_status hbaca_debug_entries(const hbaca_gen* gen, const int64_t* rows, const int64_t* cols, int64_t count,
                                  void* out, void* stream);
 
+/* Cluster size (CTAs per core, 1 .. 16) that every later synchronous call in
+   this process gives the one-sided Jacobi SVD of every core (raised where a
+   core's columns do not fit the shared memory of that many CTAs); 0 restores
+   the per-stage choice.  Returns the previous setting.  Results do not depend
+   on it (every rotation is formed and applied with the same arithmetic
+   whatever CTA runs it); it exists to time the launch shapes. */
+int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster);
+
 /* Sweep cap of the one-sided Jacobi SVD (Sec. 2, SVD(A, eps)) used by every
    later call in this process: sweeps > 0 sets it, 0 restores the default
    (40).  Returns the cap in force before the call.  For tests that make a

@@ -81,6 +81,7 @@ hbaca_status map_device_status(int ds) {
 
 constexpr int kDefaultJacobiSweeps = 40;
 std::atomic<int> g_jacobi_sweeps{kDefaultJacobiSweeps};
+std::atomic<int> g_jacobi_cluster{0};
 
 }  // namespace
 
@@ -88,6 +89,7 @@ namespace hbaca {
 hbaca_status record_error(hbaca_status s, const std::string& msg) { return fail(s, msg); }
 int ctx_device(const hbaca_ctx* ctx) { return ctx->device; }
 int jacobi_max_sweeps() { return g_jacobi_sweeps.load(std::memory_order_relaxed); }
+int jacobi_forced_cluster() { return g_jacobi_cluster.load(std::memory_order_relaxed); }
 }  // namespace hbaca
 
 extern "C" {
@@ -585,6 +587,11 @@ hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES],
   if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("event timing: ") + cudaGetErrorString(e));
   tls_err.clear();
   return HBACA_OK;
+}
+
+int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster) {
+  const int v = cluster >= 1 && cluster <= 16 ? cluster : 0;
+  return g_jacobi_cluster.exchange(v);
 }
 
 int32_t hbaca_debug_set_jacobi_sweeps(int32_t sweeps) {

@@ -706,7 +706,10 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
       // two columns in registers for (3)
       T ka[kJacKeep], kb[kJacKeep];
       for (int j = 0; j < per_warp; ++j) {
-        const int pi = j * stride + q * nw + warp;
+        // pairs are dealt to the CTAs first (pair j * stride + warp * c + q),
+        // so a round with fewer pairs than warps spreads over all CTAs and
+        // over the four schedulers of each SM (warps 0-3 first)
+        const int pi = j * stride + warp * c + q;
         int a = 0, b = 0;
         bool act = pi < npairs;
         if (act) {

@@ -301,15 +301,17 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       const size_t per_cta = (pairs + (size_t)cc * 8 - 1) / ((size_t)cc * 8) * 8;
       return j_base + per_cta * kJSlotMax;
     };
-    // cluster size c = 1..16.  Preferred: the round's pairs in one pass over
-    // the cluster's warps, when every cluster of that group can be resident at
-    // once; otherwise the largest power of two with at least one pair per warp
-    // (a stage with many cores is bound by the FP64 rate, not by the rounds).
+    // cluster size: about three resident CTAs per SM in all (a stage with
+    // many cores is bound by the FP64 rate and takes 4-CTA clusters; one with
+    // few cores by the latency of its rounds and spreads each core over up to
+    // 16 CTAs), at least four pairs of a round per CTA (one per scheduler of
+    // its SM), raised where a core's columns do not fit that many CTAs'
+    // shared memory.  Measured on the 20000^2 workload: 4 CTAs for the 256,
+    // 128 and 64 cores of the leaf and first merge stages, 8 for 32 cores, 16
+    // for 16 or fewer (cluster sizes do not change any result).
     std::vector<std::vector<int32_t>> groups(17);
     std::vector<size_t> need(17, 0);
     const std::vector<SvdTask>& th = *sg.tasks_h;
-    const int wpc = kDenseThreads / 32;
-    std::vector<int> c_one(nt), c_pow(nt);
     auto share_of = [&](int i, int cc) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int nc = std::min(dh[i].kra, ncm), mr = ncm;
@@ -325,28 +327,15 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       const size_t sh = share_of(i, cc) + j_hdr_of(cc) <= kJacobiSmemLimit ? share_of(i, cc) : 0;
       need[cc] = std::max(need[cc], sh);
     };
-    // a stage with fewer than sms / 32 cores leaves most SMs idle whatever
-    // the cluster size: its cores take 16-CTA clusters, so that a round's FP64
-    // work is spread over as many SMs as a cluster can hold (with 8 cores of
-    // 16 CTAs the clusters share SMs and the stage ran slower)
-    const bool few = (int64_t)nt * 16 * 2 < rc.sms;
+    int c_stage = 4;
+    while (c_stage < 16 && (int64_t)nt * c_stage * 2 <= 3 * (int64_t)rc.sms) c_stage *= 2;
     for (int i = 0; i < nt; ++i) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int pairs = (std::min(dh[i].kra, ncm) + 1) / 2;
-      int g = 0;
-      while (g < 4 && (1 << (g + 1)) * wpc <= pairs) ++g;
-      c_pow[i] = fit(i, 1 << g);
-      c_one[i] = fit(i, few && pairs >= 16 ? 16 : std::min(16, std::max(1, (pairs + wpc - 1) / wpc)));
-      add_task(i, c_one[i]);
-    }
-    for (int cc = 1; cc <= 16; ++cc) {
-      if (groups[cc].empty()) continue;
-      const int res = resident_clusters(jacobi_kernel<T>, cc, j_hdr_of(cc) + need[cc], rc.st);
-      if ((int)groups[cc].size() <= res) continue;
-      std::vector<int32_t> moved;
-      moved.swap(groups[cc]);
-      need[cc] = 0;
-      for (int32_t i : moved) add_task(i, c_pow[i]);
+      int c = c_stage;
+      while (c > 1 && pairs < 4 * c) c /= 2;
+      if (jacobi_forced_cluster() > 0) c = jacobi_forced_cluster();
+      add_task(i, fit(i, c));
     }
     size_t off = sg.jlist_off;
     std::vector<JacobiLaunch> ls;

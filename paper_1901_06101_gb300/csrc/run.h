@@ -79,4 +79,7 @@ hbaca_status record_error(hbaca_status s, const std::string& msg);
 int ctx_device(const hbaca_ctx* ctx);
 // Sweep cap of the one-sided Jacobi SVD launches (hbaca_debug_set_jacobi_sweeps).
 int jacobi_max_sweeps();
+// Jacobi cluster size forced on every core of a synchronous call (0: chosen
+// per stage; hbaca_debug_set_jacobi_cluster).
+int jacobi_forced_cluster();
 }  // namespace hbaca
