@@ -365,14 +365,22 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
     ++rc.launches;
   }
-  HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(8, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+  {
+    // one warp per output column of every task: enough CTAs for the widest
+    // output, within about eight CTAs per SM over the stage
+    const int cols = p.tape ? sg.kcap : (int)std::min<int64_t>(sg.kcap, p.rank_cap_max);
+    const int gx = std::max(8, std::min((cols + 7) / 8, std::max(8, 8 * rc.sms / std::max(nt, 1))));
+    HB_TIMED(KC_FINISH, finish_kernel<T><<<dim3(gx, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+  }
   ++rc.launches;
   X.njobs = sg.nq;
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
   HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
   rc.launches += 5;  // pack, QR, core, pivoted QR of the core, Q application
   if (sg.kind != TASK_LEAF) {
-    HB_TIMED(KC_BLOCKPROD, blockprod_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+    // element-parallel; a stage with few (large) tasks spreads each over more CTAs
+    const int gx = std::max(64, std::min(1024, 8 * rc.sms / std::max(nt, 1)));
+    HB_TIMED(KC_BLOCKPROD, blockprod_kernel<T><<<dim3(gx, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
     ++rc.launches;
   }
   return cudaSuccess;

@@ -77,12 +77,32 @@ def dense_rel_error(A, U, s, V):
     return float(np.linalg.norm(E) / np.linalg.norm(A))
 
 
-def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid):
+def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid, rounding_sensitive=False):
     """Replay the GPU's pivot record through the oracle (frozen pivots): every
     GPU choice must be a valid greedy choice up to rounding, and the norms and
-    ranks must agree.  Returns the replay result."""
+    ranks must agree.  Returns the replay result.
+
+    rounding_sensitive: the input is one on which the method amplifies
+    rounding (the coherent sparse product, see
+    test_oracle_pins.test_coherent_case_is_rounding_sensitive).  There a
+    forced choice that is not greedy in the oracle's arithmetic only ends the
+    comparison when the competing residual norms are at the rounding level of
+    the leaf (below 1e-12 times the largest mu the leaf reached): the two runs'
+    residuals have parted by the amplified rounding of earlier iterations,
+    which the local noise estimate of one cross does not see."""
     from oracle import baca as ob
     rep = ob.baca_replay(ogen_leaf, d, eps, g["trace"], seed=seed, bid=bid, stop=g["stop"])
+    if rounding_sensitive and rep["recs"]:
+        last = rep["recs"][-1]
+        scale = max([r.get("mu", 0.0) for r in rep["recs"]] + [0.0])
+        why = last.get("why") or []
+        if not last.get("valid_I", True) and why and all(
+                isinstance(w, tuple) and w[1] <= 1e-12 * scale for w in why):
+            last["noise_level"] = True
+            last["valid_I"] = True
+            last.setdefault("valid_J", True)
+            last.setdefault("valid_W", True)
+            last.setdefault("valid_dk", True)
     noisy = [k for k, r in enumerate(rep["recs"]) if r.get("noise_level")]
     limit = noisy[0] + 1 if noisy else len(g["trace"])
     assert len(rep["recs"]) >= limit, ("replay stopped", len(rep["recs"]), len(g["trace"]), rep["recs"][-1])
