@@ -605,9 +605,20 @@ def bench_cfg1(args, dev, flush, stream):
     err = B.rel_error(ctx, spec, r["res"])
     torch.cuda.synchronize(dev)
     whole = r["whole_flops"] / (r["ms"] / 1e3) / 1e12
-    return {"workload": "gaussian_f64_2000_d8_L2_eps1e-6", "ms": r["ms"], "entries_per_s": r["entries"] / (r["ms"] / 1e3),
+    # the same call captured into a CUDA graph on its first run and replayed
+    # (no host planning or synchronisation between stages)
+    gopts = mk_opts(1e-6, 8, 2, seed=0, rank_cap=128, leaf_rank_cap=256, flags=B.FLAG_GRAPH)
+    gws = torch.empty(B.workspace_size(spec.gen, gopts), dtype=torch.uint8, device=dev)
+    gout = (torch.empty((128, 2000), dtype=torch.float64, device=dev), torch.empty(128, dtype=torch.float64, device=dev),
+            torch.empty((128, 2000), dtype=torch.float64, device=dev))
+    gms, gres = _timed_calls(lambda: B.compress(ctx, spec, gopts, ws=gws, out=gout), max(3, min(args.steps, 10)),
+                             max(3, args.warmup), flush, stream)
+    assert gres.rank == r["rank"]
+    return {"workload": "gaussian_f64_2000_d8_L2_eps1e-6", "ms": r["ms"], "ms_graph_replay": gms,
+            "entries_per_s": r["entries"] / (r["ms"] / 1e3),
             "rank": r["rank"], "rel_error": err,
-            "roofline_whole": {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS, "flops": r["whole_flops"]},
+            "roofline_whole": {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS, "flops": r["whole_flops"],
+                               "frac_graph_replay": r["whole_flops"] / (gms / 1e3) / 1e12 / FP64_PEAK_TFLOPS},
             "roofline_leaf_baca": roofline_of("baca_leaf_kernel", r["leaf_flops"], r["ktimes"]),
             "phases_ms": r["phases"], "gpu_launches": r["launches"],
             "kernel_ms": {kk: v[0] for kk, v in r["ktimes"].items()}}
