@@ -444,7 +444,7 @@ def measure_single(B, ctx, spec, opts, cap, m, n, L, d, complex_, steps, warmup,
     kt = B.kernel_times(ctx)
     plan = B.plan_json(spec, popts)
     dims = task_dims(ws, plan)
-    return dict(ms=ms, res=res, ws=ws, out=out, entries=entries, leaf_flops=leaf_flops,
+    return dict(ms=ms, res=res, ws=ws, out=out, entries=entries, leaf_flops=leaf_flops, traces=traces,
                 whole_flops=whole_flops_8d(traces, sizes, d, dims, complex_),
                 jacobi_flops=jacobi_flops_8d(dims, complex_),
                 jacobi_own_flops=jacobi_accounting(ws, plan, complex_), jacobi_stages=jacobi_stage_stats(ws, plan),
@@ -665,12 +665,26 @@ def bench_cfg3(args, dev, flush, stream):
             r = measure_single(B, ctx, spec, opts, 1024, 50000, 50000, 5, d, False, 3 if d > 1 else 2,
                                3 if d > 1 else 1, flush, stream, dev)
         except B.HbacaError as e:
-            out[name] = {"d": d, "error": str(e), "wall_s": time.perf_counter() - t0}
+            # the leaf stage ran; its records are in the workspace of a plain call
+            ws = torch.empty(B.workspace_size(spec.gen, opts), dtype=torch.uint8, device=dev)
+            try:
+                B.compress(ctx, spec, opts, ws=ws)
+            except B.HbacaError:
+                pass
+            tr0 = B.read_leaf_trace(spec, opts, ws, 0)
+            out[name] = {"d": d, "error": str(e), "wall_s": time.perf_counter() - t0,
+                         "leaf0_nu_over_mu": [t["nu"] / t["mu"] if t["mu"] > 0 else 0.0 for t in tr0["trace"]],
+                         "leaf0_stop": tr0["stop"], "leaf0_rank": tr0["rank_baca"]}
+            del ws
             torch.cuda.empty_cache()
             continue
         err = B.rel_error(ctx, spec, r["res"])
         torch.cuda.synchronize(dev)
+        # convergence history of the first leaf (Sec. 5.1): nu_k / mu_k per
+        # iteration, the estimate the stopping test nu < eps mu uses
+        hist = [t["nu"] / t["mu"] if t["mu"] > 0 else 0.0 for t in r["traces"][0]["trace"]]
         out[name] = {"d": d, "ms": r["ms"], "rank": r["rank"], "rel_error": err, "wall_s": time.perf_counter() - t0,
+                     "leaf0_nu_over_mu": hist, "leaf0_stop": r["traces"][0]["stop"],
                      "entries_per_s": r["entries"] / (r["ms"] / 1e3), "leaf_rank_max": r["res"].res.leaf_rank_max,
                      "leaf_iters_max": r["res"].res.leaf_iters_max,
                      "kernel_ms": {kk: v[0] for kk, v in r["ktimes"].items()}, "phases_ms": r["phases"]}

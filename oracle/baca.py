@@ -267,6 +267,9 @@ def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
         # condition number of the kept triangle: rounding in V_k = T^-1 Q^H R
         # (and so in nu, mu) is amplified by it
         rec["cond_T"] = float(diag[0] / min(diag[:dk])) if dk > 0 else 1.0
+        # relative rounding level of the smallest kept pivot: the update
+        # C T^-1 Q^H R inherits it (a diagnostic for comparisons, not used here)
+        rec["w_noise"] = float(nC / min(diag[:dk])) if dk > 0 and min(diag[:dk]) > 0 else 0.0
         # rank rule QR(W, eps): kept pivots at or above eps |T_11|, the next one below
         nxt = greedy_qrcp(W, min(dI, dJ), abs_noise=nC)[1]
         ok = True

@@ -137,7 +137,11 @@ def near_threshold(s, eps, rel=1e-6):
 
 def stable_prefix(recs, gtrace):
     """Number of leading iterations of a leaf before its first rounding-level
-    cross (frozen-pivot replay records), and the BACA rank they add."""
-    k0 = next((k for k, r in enumerate(recs) if r.get("noise_level")), len(recs))
+    cross (frozen-pivot replay records) or its first kept pivot within 1e8 of
+    the rounding level (the update C T^-1 Q^H R then carries a relative
+    rounding error above 1e-8), the BACA rank they add, and the largest
+    relative rounding level of their kept pivots."""
+    k0 = next((k for k, r in enumerate(recs) if r.get("noise_level") or r.get("w_noise", 0.0) > 1e-8), len(recs))
     k0 = min(k0, len(gtrace))
-    return k0, sum(t["dk"] for t in gtrace[:k0])
+    amp = max([0.0] + [r.get("w_noise", 0.0) for r in recs[:k0]])
+    return k0, sum(t["dk"] for t in gtrace[:k0]), amp
