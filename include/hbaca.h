@@ -147,6 +147,14 @@ typedef struct hbaca_opts {
                              re-compression, <= 1024; 0 = min(m_leaf, n_leaf, 1024) */
   uint32_t flags;         /* HBACA_FLAG_* */
   int32_t cluster;        /* CTAs per leaf (1, 2, 4, 8, 16); 0 = choose automatically */
+  double srrqr_f;         /* 0: the greedy QRCP pivots of Alg. 2.  f > 1: each greedy
+                             pivot set I_k / J_{k+1} whose smallest pivot residual is
+                             at least 1e-8 of max(first pivot residual, mu) is then
+                             refined by strong rank-revealing QR (Gu & Eisenstat 1996,
+                             one of the subset selections Sec. 3.2 names): a chosen
+                             vector is swapped for a candidate while that multiplies
+                             the chosen set's volume by more than f (at most 4k + 4
+                             swaps per set) */
 } hbaca_opts;
 
 /* Output factors (caller-owned device memory) and the rank. */

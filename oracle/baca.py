@@ -27,7 +27,7 @@ Readings of the paper taken here (the CUDA path takes the same ones):
 import numpy as np
 import scipy.linalg
 
-from .linalg import greedy_qrcp, truncated_svd
+from .linalg import greedy_qrcp, strong_rrqr, strong_rrqr_margin, truncated_svd
 from .sampler import initial_columns
 
 
@@ -88,13 +88,28 @@ def lrnormup(U, V, mu, Uk, Vk, nu):
     return float(np.sqrt(max(s, 0.0)))
 
 
-def baca(gen, d, eps, seed=0, bid=0):
+def _refine(diag, mu):
+    """Whether a greedy pivot set is refined by strong RRQR: only a set whose
+    smallest pivot residual norm is at least 1e-8 of the larger of the first
+    one and the current mu.  Below that the chosen block is numerically
+    rank-deficient or at the rounding level, where the swap criterion
+    compares rounding noise and volume gains mean nothing."""
+    return len(diag) > 0 and min(diag) >= 1e-8 * max(diag[0], mu)
+
+
+def baca(gen, d, eps, seed=0, bid=0, srrqr_f=None):
     """BACA (Alg. 2) on the whole matrix of ``gen`` (local indices).
 
     Returns a dict with U (m x r), V (r x n), rank r, and ``trace``: one
     record per iteration with the column block J (before LRID), the row
     pivots I (QRCP order, before shrinking), their margins, the next column
-    block and its margins, Jbar, d_k, nu and mu."""
+    block and its margins, Jbar, d_k, nu and mu.
+
+    ``srrqr_f``: select I_k and J_{k+1} by strong rank-revealing QR (Sec. 3.2
+    names it among the alternatives to QRCP): the greedy QRCP sets refined by
+    Gu and Eisenstat's swaps with threshold f (linalg.strong_rrqr), when the
+    greedy set is numerically of full rank (_refine); each record then also
+    holds the number of swaps and the stopping margins."""
     m, n = gen.m, gen.n
     dt = np.dtype(gen.dtype)
     U = np.zeros((m, 0), dt)
@@ -114,16 +129,24 @@ def baca(gen, d, eps, seed=0, bid=0):
         UVJ = U @ V[:, J]
         C = AJ - UVJ
         nC = _noise(AJ, np.abs(U) @ np.abs(V[:, J]))
-        I, _, imarg, _ = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC)
+        I, dgI, imarg, _ = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC)
         if len(I) == 0:
             stop = "no rows"
             break
+        swI = swJ = 0
+        smI = smJ = np.inf
+        if srrqr_f is not None and _refine(dgI, mu):
+            I, swI = strong_rrqr(C.T, I, candidates=~kept_rows, f=srrqr_f)
+            smI = strong_rrqr_margin(C.T, I, candidates=~kept_rows, f=srrqr_f)
         AI = gen(I, allcols)
         UVI = U[I, :] @ V
         R = AI - UVI
         cand = ~kept_cols
         cand[J] = False
-        Jn, _, jmarg, _ = greedy_qrcp(R, d, candidates=cand, abs_noise=_noise(AI, np.abs(U[I, :]) @ np.abs(V)))
+        Jn, dgJ, jmarg, _ = greedy_qrcp(R, d, candidates=cand, abs_noise=_noise(AI, np.abs(U[I, :]) @ np.abs(V)))
+        if srrqr_f is not None and len(Jn) and _refine(dgJ, mu):
+            Jn, swJ = strong_rrqr(R, Jn, candidates=cand, f=srrqr_f)
+            smJ = strong_rrqr_margin(R, Jn, candidates=cand, f=srrqr_f)
         W = C[I, :]
         Uk, Vk, dk, jbar, winfo = _lrid(C, W, R, eps, nC)
         nu = lrnorm(Uk, Vk) if dk else 0.0
@@ -133,7 +156,8 @@ def baca(gen, d, eps, seed=0, bid=0):
         kept_rows[I[:dk]] = True
         kept_cols[[J[p] for p in jbar]] = True
         trace.append(dict(J=list(J), I=list(I), Imarg=imarg, Jnext=list(Jn),
-                          Jmarg=jmarg, jbar=list(jbar), dk=dk, nu=nu, mu=mu, W=winfo))
+                          Jmarg=jmarg, jbar=list(jbar), dk=dk, nu=nu, mu=mu, W=winfo,
+                          swaps=(swI, swJ), smarg=(smI, smJ)))
         if nu < eps * mu:
             stop = "converged"
             break
@@ -201,7 +225,19 @@ def recompress(U, V, eps, rank=None):
     return Qu @ X, s, Yh @ Qv.conj().T
 
 
-def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
+def _srrqr_set_ok(M, forced, cand, k_expect, f, noise):
+    """A forced set of a strong-RRQR run: distinct candidates, as many as the
+    greedy selection takes, and no swap left above f^2 (up to rounding), or a
+    matrix at the rounding level."""
+    forced = list(forced)
+    if len(forced) != k_expect or len(set(forced)) != len(forced) or not all(cand[j] for j in forced):
+        return False
+    if k_expect == 0 or float(np.abs(M).max(initial=0.0)) <= 100.0 * noise:
+        return True
+    return strong_rrqr_margin(M, forced, candidates=cand, f=f) >= -1e-8
+
+
+def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged", srrqr_f=None):
     """Frozen-pivot BACA: Alg. 2 with the pivot choices I_k, J_{k+1}, Jbar,
     d_k and the iteration count taken from ``trace`` (a record of another
     run, e.g. the CUDA path).  Every forced choice is checked to be a valid
@@ -214,7 +250,12 @@ def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
     Returns U, V, r and per-iteration records with the validity flags
     (valid_I, valid_J, valid_W, valid_dk, valid_stop), nu, mu and
     noise_level (W at the rounding-noise level; records after the first such
-    one are not comparable with the recorded run)."""
+    one are not comparable with the recorded run).
+
+    ``srrqr_f``: the recorded run selected I_k and J_{k+1} by strong RRQR with
+    threshold f; a forced set is then valid when it has the greedy count of
+    distinct candidates and no swap above f^2 is left (its defining
+    property) rather than when it is the greedy choice."""
     m, n = gen.m, gen.n
     dt = np.dtype(gen.dtype)
     U = np.zeros((m, 0), dt)
@@ -232,8 +273,17 @@ def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
         UVJ = U @ V[:, J]
         C = AJ - UVJ
         nC = _noise(AJ, np.abs(U) @ np.abs(V[:, J]))
-        I, _, _, _, vI = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC, forced=list(t["I"]))
-        rec["valid_I"] = all(v is True for v in vI) and len(I) == len(t["I"])
+        if srrqr_f is None:
+            I, _, _, _, vI = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC, forced=list(t["I"]))
+            rec["valid_I"] = all(v is True for v in vI) and len(I) == len(t["I"])
+        else:
+            gI, dgI, _, _ = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC)
+            if _refine(dgI, mu):
+                I = list(t["I"])
+                vI = [_srrqr_set_ok(C.T, I, ~kept_rows, len(gI), srrqr_f, nC)]
+            else:
+                I, _, _, _, vI = greedy_qrcp(C.T, d, candidates=~kept_rows, abs_noise=nC, forced=list(t["I"]))
+            rec["valid_I"] = all(v is True for v in vI) and len(I) == len(t["I"])
         if not rec["valid_I"]:
             rec["why"] = [v for v in vI if v is not True]
             recs.append(rec)
@@ -243,7 +293,11 @@ def baca_replay(gen, d, eps, trace, seed=0, bid=0, stop="converged"):
         R = AI - UVI
         cand = ~kept_cols
         cand[J] = False
-        if k + 1 < len(trace):
+        nR = _noise(AI, np.abs(U[I, :]) @ np.abs(V))
+        gJ, dgJ, _, _ = greedy_qrcp(R, d, candidates=cand, abs_noise=nR) if srrqr_f is not None else (0, 0, 0, 0)
+        if k + 1 < len(trace) and srrqr_f is not None and _refine(dgJ, mu):
+            rec["valid_J"] = _srrqr_set_ok(R, trace[k + 1]["J"], cand, len(gJ), srrqr_f, nR)
+        elif k + 1 < len(trace):
             Jn, _, _, _, vJ = greedy_qrcp(R, d, candidates=cand, abs_noise=_noise(AI, np.abs(U[I, :]) @ np.abs(V)),
                                           forced=list(trace[k + 1]["J"]))
             # the forced block must also be as long as the greedy rule allows

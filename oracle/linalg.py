@@ -8,9 +8,12 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   complement of the t columns already chosen (classical Gram-Schmidt applied
   twice), its residual norm is computed explicitly, and the largest one is
   chosen (lowest index on exact ties).  No norm down-dating is used.
+* ``strong_rrqr``: Gu and Eisenstat's swap refinement of a chosen set, one of
+  the subset-selection alternatives to QRCP that Sec. 3.2 names.
 * ``eps_rank``: r = min{k : Sigma_{k+1,k+1} < eps Sigma_{1,1}} (Sec. 2).
 """
 import numpy as np
+import scipy.linalg
 
 
 def _project_out(Q, X):
@@ -108,6 +111,80 @@ def greedy_qrcp(M, kmax, candidates=None, rank_tol=None, abs_noise=0.0, forced=N
     if forced is not None:
         return piv, diag, margins, Q, valid  # invalid steps hold (step, best, forced, noise)
     return piv, diag, margins, Q
+
+
+def strong_rrqr_criterion(M, piv, rest):
+    """Gu & Eisenstat's swap criterion for a chosen column set: with
+    M(:, piv) = Q R11 (thin QR, piv in order), R12 = Q^H M(:, rest) and
+    gamma_j the norm of column j of the residual (I - Q Q^H) M(:, rest),
+    rho_ij = |(R11^{-1} R12)_ij|^2 + (omega_i gamma_j)^2, omega_i the norm of
+    row i of R11^{-1}; sqrt(rho_ij) is the factor by which swapping chosen
+    column i for candidate j multiplies |det R11|.  Returns rho (k x len(rest))
+    or None when R11 is singular."""
+    A = M[:, piv]
+    Q, R11 = np.linalg.qr(A)
+    if np.any(np.abs(np.diag(R11)) == 0.0):
+        return None
+    B = M[:, rest]
+    R12 = Q.conj().T @ B
+    gam = np.linalg.norm(B - Q @ R12, axis=0)
+    Ri = scipy.linalg.solve_triangular(R11, np.eye(len(piv)), lower=False)
+    om = np.linalg.norm(Ri, axis=1)
+    return np.abs(Ri @ R12) ** 2 + (om[:, None] * gam[None, :]) ** 2
+
+
+def strong_rrqr(M, piv, candidates=None, f=2.0, max_swaps=None):
+    """Strong rank-revealing QR (Gu & Eisenstat, SIAM J. Sci. Comput. 1996) as
+    a refinement of a chosen column set (one of the subset-selection methods
+    Sec. 3.2 names beside QRCP): while some chosen column i and candidate j
+    have rho_ij > f^2 (strong_rrqr_criterion), the largest such pair is
+    swapped (ties: smallest j, then smallest i), the candidate taking the
+    chosen column's position.  Every swap multiplies |det R11| by more than f,
+    so the loop ends; when the set has as many columns as M has rows this is
+    the maximum-volume (dominant submatrix) condition.  A singular R11 is left
+    as it is.  Returns (piv, number of swaps)."""
+    M = np.asarray(M)
+    N = M.shape[1]
+    piv = list(piv)
+    k = len(piv)
+    cand = np.ones(N, bool) if candidates is None else np.array(candidates, bool)
+    swaps = 0
+    max_swaps = 4 * k + 4 if max_swaps is None else max_swaps
+    while k > 0 and swaps < max_swaps:
+        chosen = np.zeros(N, bool)
+        chosen[piv] = True
+        rest = np.flatnonzero(cand & ~chosen)
+        if rest.size == 0:
+            break
+        rho = strong_rrqr_criterion(M, piv, rest)
+        if rho is None:
+            break
+        best = rho.max()
+        if not best > f * f:
+            break
+        ii, jj = np.nonzero(rho == best)
+        o = np.lexsort((ii, jj))[0]
+        piv[int(ii[o])] = int(rest[jj[o]])
+        swaps += 1
+    return piv, swaps
+
+
+def strong_rrqr_margin(M, piv, candidates=None, f=2.0):
+    """Relative margin of the stopping decision of a strong RRQR set: how far
+    the largest rho_ij lies below f^2, (f^2 - max rho) / f^2 (negative when a
+    swap is still due; inf without candidates or with a singular R11)."""
+    M = np.asarray(M)
+    N = M.shape[1]
+    cand = np.ones(N, bool) if candidates is None else np.array(candidates, bool)
+    chosen = np.zeros(N, bool)
+    chosen[list(piv)] = True
+    rest = np.flatnonzero(cand & ~chosen)
+    if rest.size == 0 or len(piv) == 0:
+        return np.inf
+    rho = strong_rrqr_criterion(M, list(piv), rest)
+    if rho is None:
+        return np.inf
+    return float((f * f - rho.max()) / (f * f))
 
 
 def eps_rank(s, eps):

@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
     _fields_ = [
         ("eps", ctypes.c_double), ("d", ctypes.c_int32), ("levels", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("rank_cap", ctypes.c_int64), ("leaf_rank_cap", ctypes.c_int64),
-        ("flags", ctypes.c_uint32), ("cluster", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("cluster", ctypes.c_int32), ("srrqr_f", ctypes.c_double),
     ]
 
 
@@ -189,9 +189,9 @@ class Context:
             pass
 
 
-def make_opts(eps, d, levels, seed=0, rank_cap=0, leaf_rank_cap=0, flags=0, cluster=0):
+def make_opts(eps, d, levels, seed=0, rank_cap=0, leaf_rank_cap=0, flags=0, cluster=0, srrqr_f=0.0):
     return Opts(eps=eps, d=d, levels=levels, seed=seed, rank_cap=rank_cap,
-                leaf_rank_cap=leaf_rank_cap, flags=flags, cluster=cluster)
+                leaf_rank_cap=leaf_rank_cap, flags=flags, cluster=cluster, srrqr_f=srrqr_f)
 
 
 def workspace_size(gen, opts):

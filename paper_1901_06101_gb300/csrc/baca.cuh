@@ -53,6 +53,7 @@ struct BacaParams {
   int d;
   uint64_t seed;
   int mr_max, nc_max, rcap_max;
+  double srrqr_f2;  // > 0: pivot sets refined by strong RRQR with threshold f^2
 };
 
 struct ArgSlot {
@@ -73,7 +74,7 @@ struct BacaSmem {
   ArgSlot* slot; // 2
   long long* wb; // 32
   int* wi;       // 32
-  double* red;   // 64
+  double* red;   // 96: reductions [0..63]; norms^2 of the chosen pivots [64..95]
   int* sI;       // d
   int* sJ;       // d
   int* sJn;      // d
@@ -93,7 +94,7 @@ __host__ __device__ inline size_t baca_smem_bytes(int mr_max, int nc_max, int d)
   b += w * sizeof(T);
   b += (size_t)(2 * d + d + 2 * d * d + d) * sizeof(T);
   b += (size_t)d * sizeof(double);
-  b += 2 * sizeof(ArgSlot) + 32 * sizeof(long long) + 32 * sizeof(int) + 64 * sizeof(double);
+  b += 2 * sizeof(ArgSlot) + 32 * sizeof(long long) + 32 * sizeof(int) + 96 * sizeof(double);
   b += (size_t)(4 * d + 16) * sizeof(int);
   int mx = mr_max > nc_max ? mr_max : nc_max;
   b += (size_t)mr_max + nc_max + mx + 64;
@@ -119,7 +120,7 @@ __device__ inline BacaSmem<T> carve(unsigned char* base, int mr_max, int nc_max,
   long long* lp = reinterpret_cast<long long*>(s.slot + 2);
   s.wb = lp; lp += 32;
   dp = reinterpret_cast<double*>(lp);
-  s.red = dp; dp += 64;
+  s.red = dp; dp += 96;
   int* ip = reinterpret_cast<int*>(dp);
   s.wi = ip; ip += 32;
   s.sI = ip; ip += d;
@@ -232,6 +233,7 @@ __device__ int qrcp_cluster(cg::cluster_group& cl, const BacaSmem<T>& S, int ldw
       if (lane == 0) {
         S.sint[1] = i2;
         S.sint[2] = ownmask ? (__ffs(ownmask) - 1) : -1;
+        if (t < 32) S.red[64 + t] = __longlong_as_double(b2);  // the pivot's residual norm^2
       }
     }
     __syncthreads();
@@ -358,6 +360,163 @@ __device__ int lrid_small(const BacaSmem<T>& S, int dI, int dJ, int d, double ep
   return dk;
 }
 
+// Strong rank-revealing QR (Gu & Eisenstat, SIAM J. Sci. Comput. 17, 1996) as
+// a refinement of the k pivots qrcp_cluster chose among this cluster's
+// vectors -- one of the subset-selection methods Sec. 3.2 names beside QRCP.
+// With the chosen vectors as columns, M(:, piv) = Q R11, R12 = Q^H M(:, j)
+// and gamma_j = the norm of the rest of the reflected vector j, the criterion
+// rho_ij = |(R11^{-1} R12)_ij|^2 + (omega_i gamma_j)^2 (omega_i = norm of row
+// i of R11^{-1}) is the squared factor by which swapping chosen i for
+// candidate j multiplies |det R11|; while the largest rho exceeds f^2 that
+// pair is swapped (ties: smaller j, then smaller i; the candidate takes the
+// chosen one's position).  The vectors are re-read from their global copy
+// (vec(g, cc): component cc of vector g); every CTA factors the chosen set
+// itself (bit-identical), forms rho for its own candidates, and the cluster
+// argmax is taken in rank order through DSMEM, so every CTA takes the same
+// swaps.  At most 4k + 4 swaps (each multiplies a volume by more than f > 1).
+// Returns the number of swaps; piv and the candidate flags are updated.
+template <typename T, typename VecF>
+__device__ int srrqr_cluster(cg::cluster_group& cl, const BacaSmem<T>& S, int ldw, int nloc, int p, int k,
+                             int gbase, int d, int* piv, VecF vec, double f2, unsigned& ctr) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
+  T* work = S.work;
+  uint8_t* cand = S.cand;
+  const int max_swaps = 4 * k + 4;
+  int swaps = 0;
+  while (swaps < max_swaps) {
+    // 1. the chosen vectors as the columns of Em (p x k), Householder QR by warp 0
+    for (int e = tid; e < p * k; e += blockDim.x) {
+      const int cc = e % p, t = e / p;
+      S.Em[t * d + cc] = vec(piv[t], cc);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int t = 0; t < k; ++t) {
+        if (lane == 0) {
+          T* x = S.Em + t * d;
+          double sig2 = 0.0;
+          for (int r = t + 1; r < p; ++r) sig2 += abs2(x[r]);
+          double beta;
+          T tau, sc;
+          householder(x[t], sig2, beta, tau, sc);
+          for (int r = t + 1; r < p; ++r) x[r] = mul(x[r], sc);
+          x[t] = from_re<T>(beta);
+          S.betav[t] = beta;
+          S.tauv[t] = tau;
+        }
+        __syncwarp();
+        if (lane > t && lane < k) {  // apply H_t^H to the later chosen columns
+          const T* u = S.Em + t * d;
+          T* y = S.Em + lane * d;
+          T w = y[t];
+          for (int r = t + 1; r < p; ++r) w = cmac(w, u[r], y[r]);
+          const T fct = mul(conj_(S.tauv[t]), w);
+          y[t] = sub(y[t], fct);
+          for (int r = t + 1; r < p; ++r) y[r] = msub(y[r], u[r], fct);
+        }
+        __syncwarp();
+      }
+      // 2. Ri = R11^{-1} (column-major ld d in Wm), lane = column; R11(s, t) = Em[t d + s]
+      if (lane < k) {
+        T* col = S.Wm + lane * d;
+        for (int t = k - 1; t >= 0; --t) {
+          T v = from_re<T>(t == lane ? 1.0 : 0.0);
+          for (int s2 = t + 1; s2 < k; ++s2) v = msub(v, S.Em[s2 * d + t], col[s2]);
+          col[t] = S.betav[t] != 0.0 ? scale(v, 1.0 / S.betav[t]) : Traits<T>::zero();
+        }
+      }
+      __syncwarp();
+      // 3. omega_i = norm of row i of Ri
+      if (lane < k) {
+        double o = 0.0;
+        for (int t = lane; t < k; ++t) o += abs2(S.Wm[t * d + lane]);
+        S.red[lane] = o;  // omega_i^2
+      }
+    }
+    __syncthreads();
+    bool singular = false;
+    for (int t = 0; t < k; ++t) singular |= (S.betav[t] == 0.0);
+    if (singular) break;
+    // 4. this CTA's candidates: reflect, rho over the chosen positions
+    long long bb = -1;
+    int bkey = INT_MAX;
+    for (int v = tid; v < nloc; v += blockDim.x) {
+      if (!cand[v]) continue;
+      for (int cc = 0; cc < p; ++cc) work[(size_t)cc * ldw + v] = vec(gbase + v, cc);
+      for (int t = 0; t < k; ++t) {
+        const T* u = S.Em + t * d;
+        T w = work[(size_t)t * ldw + v];
+        for (int cc = t + 1; cc < p; ++cc) w = cmac(w, u[cc], work[(size_t)cc * ldw + v]);
+        const T fct = mul(conj_(S.tauv[t]), w);
+        work[(size_t)t * ldw + v] = sub(work[(size_t)t * ldw + v], fct);
+        for (int cc = t + 1; cc < p; ++cc) work[(size_t)cc * ldw + v] = msub(work[(size_t)cc * ldw + v], u[cc], fct);
+      }
+      double gam2 = 0.0;
+      for (int cc = k; cc < p; ++cc) gam2 += abs2(work[(size_t)cc * ldw + v]);
+      for (int i = 0; i < k; ++i) {
+        T b = Traits<T>::zero();
+        for (int t = i; t < k; ++t) b = mac(b, S.Wm[t * d + i], work[(size_t)t * ldw + v]);
+        const double rho = abs2(b) + S.red[i] * gam2;
+        argmax_merge(bb, bkey, nbits(rho), (gbase + v) * 32 + i);
+      }
+    }
+    warp_argmax(bb, bkey);
+    if (lane == 0) { S.wb[warp] = bb; S.wi[warp] = bkey; }
+    __syncthreads();
+    const int buf = ctr & 1u;
+    ++ctr;
+    if (warp == 0) {
+      bb = lane < nw ? S.wb[lane] : -1;
+      bkey = lane < nw ? S.wi[lane] : INT_MAX;
+      warp_argmax(bb, bkey);
+      if (lane == 0) {
+        S.slot[buf].bits = bb;
+        S.slot[buf].idx = bkey;
+      }
+    }
+    cl.sync();
+    if (warp == 0) {  // cluster argmax in rank order (every CTA the same)
+      long long gb = lane < c ? cl.map_shared_rank(&S.slot[buf], lane)->bits : -1;
+      int gk = lane < c ? cl.map_shared_rank(&S.slot[buf], lane)->idx : INT_MAX;
+      warp_argmax(gb, gk);
+      if (lane == 0) {
+        S.sint[5] = gk;
+        S.sint[6] = (gb >= 0 && gk != INT_MAX && __longlong_as_double(gb) > f2) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    const int key = S.sint[5];
+    const int doswap = S.sint[6];
+    // the owner CTAs may overwrite their slots only after every CTA has read them
+    cl.sync();
+    if (!doswap) break;
+    const int i = key % 32, jn = key / 32, old = piv[i];
+    __syncthreads();
+    if (tid == 0) {
+      piv[i] = jn;
+      if (jn >= gbase && jn < gbase + nloc) cand[jn - gbase] = 0;
+      if (old >= gbase && old < gbase + nloc) cand[old - gbase] = 1;
+    }
+    __syncthreads();
+    ++swaps;
+  }
+  (void)q;
+  return swaps;
+}
+
+// Whether a greedy pivot set is refined: its smallest pivot residual norm at
+// least 1e-8 of the larger of the first one and the current mu (below that the
+// block is numerically rank-deficient or at the rounding level, where volume
+// gains compare rounding noise).  The norms^2 are those qrcp_cluster recorded.
+__device__ __forceinline__ bool srrqr_refine(const double* pn2, int k, double mu) {
+  if (k <= 0) return false;
+  double mn = pn2[0];
+  for (int t = 1; t < k; ++t) mn = fmin(mn, pn2[t]);
+  const double ref = fmax(sqrt(fmax(pn2[0], 0.0)), mu);
+  return sqrt(fmax(mn, 0.0)) >= 1e-8 * ref;
+}
+
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -437,6 +596,12 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
       const int dI = qrcp_cluster<T>(cl, S, mr, mr, dJ, min(d, dJ), ra, d, S.sI, ctr);
       __syncthreads();
       if (dI == 0) { stop = STOP_NO_ROWS; break; }
+      if (P.srrqr_f2 > 0.0 && srrqr_refine(S.red + 64, dI, sqrt(fmax(mu2, 0.0)))) {
+        // strong-RRQR refinement of I_k over the rows (vector of row g: C(g, :))
+        srrqr_cluster<T>(cl, S, mr, mr, dJ, dI, ra, d, S.sI,
+                         [&](int g, int cc) { return ldcg(Cg + (size_t)cc * m + g); }, P.srrqr_f2, ctr);
+        __syncthreads();
+      }
       // ---- R_k = A(I_k, :) - U(I_k, :) V   (line 5)
       for (int e = tid; e < nc * dI; e += blockDim.x) {
         const int jl = e % nc, s = e / nc, j = ca + jl, i = S.sI[s];
@@ -457,6 +622,12 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
       __syncthreads();
       // ---- J_{k+1}: greedy QRCP of R_k over unkept columns outside J_k   (line 6)
       const int dJn = qrcp_cluster<T>(cl, S, nc, nc, dI, min(d, dI), ca, d, S.sJn, ctr);
+      __syncthreads();
+      if (P.srrqr_f2 > 0.0 && srrqr_refine(S.red + 64, dJn, sqrt(fmax(mu2, 0.0)))) {
+        // the same for J_{k+1} over the columns (vector of column g: R(:, g))
+        srrqr_cluster<T>(cl, S, nc, nc, dI, dJn, ca, d, S.sJn,
+                         [&](int g, int s2) { return ldcg(Rg + (size_t)s2 * n + g); }, P.srrqr_f2, ctr);
+      }
       cl.sync();  // C_k and R_k (global scratch) complete in every CTA
       // ---- W_k and LRID   (lines 7-8)
       for (int e = tid; e < dI * dJ; e += blockDim.x) {

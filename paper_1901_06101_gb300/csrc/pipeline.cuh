@@ -136,6 +136,7 @@ cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
   P.mr_max = p.mr_max;
   P.nc_max = p.nc_max;
   P.rcap_max = p.rcap_max;
+  P.srrqr_f2 = p.opts.srrqr_f > 0.0 ? p.opts.srrqr_f * p.opts.srrqr_f : 0.0;
   auto kern = baca_leaf_kernel<Gen>;
   const int c = p.baca_cluster;
   HB_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.baca_smem));

@@ -32,7 +32,7 @@ size_t baca_smem(size_t esz, int mr, int nc, int d) {
   size_t b = w * esz;
   b += (size_t)(2 * d + d + 2 * d * d + d) * esz;
   b += (size_t)d * 8;
-  b += 2 * 16 + 32 * 8 + 32 * 4 + 64 * 8;
+  b += 2 * 16 + 32 * 8 + 32 * 4 + 96 * 8;
   b += (size_t)(4 * d + 16) * 4;
   b += (size_t)mr + nc + std::max(mr, nc) + 64;
   return b;
@@ -128,6 +128,9 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
   }
   if (!(o.eps > 0.0 && o.eps < 1.0)) { err = "eps must be in (0, 1)"; return false; }
   if (o.d < 1 || o.d > 32) { err = "d must be in [1, 32]"; return false; }
+  if (!(o.srrqr_f == 0.0 || (o.srrqr_f > 1.0 && o.srrqr_f < 1e150))) {
+    err = "srrqr_f must be 0 or a finite value > 1"; return false;
+  }
   if (o.levels > 12 || o.levels < -(1 << 30)) { err = "levels out of range"; return false; }
   if (o.cluster != 0 && (o.cluster < 1 || o.cluster > 16 || (o.cluster & (o.cluster - 1)))) {
     err = "cluster must be 0 or a power of two <= 16";

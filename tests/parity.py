@@ -77,7 +77,7 @@ def dense_rel_error(A, U, s, V):
     return float(np.linalg.norm(E) / np.linalg.norm(A))
 
 
-def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid, rounding_sensitive=False):
+def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid, rounding_sensitive=False, srrqr_f=None):
     """Replay the GPU's pivot record through the oracle (frozen pivots): every
     GPU choice must be a valid greedy choice up to rounding, and the norms and
     ranks must agree.  Returns the replay result.
@@ -89,9 +89,12 @@ def check_leaf_replay(ogen_leaf, g, d, eps, seed, bid, rounding_sensitive=False)
     comparison when the competing residual norms are at the rounding level of
     the leaf (below 1e-12 times the largest mu the leaf reached): the two runs'
     residuals have parted by the amplified rounding of earlier iterations,
-    which the local noise estimate of one cross does not see."""
+    which the local noise estimate of one cross does not see.
+
+    srrqr_f: the run refined its pivot sets by strong RRQR with this
+    threshold; a forced set is then valid when no swap above f^2 is left."""
     from oracle import baca as ob
-    rep = ob.baca_replay(ogen_leaf, d, eps, g["trace"], seed=seed, bid=bid, stop=g["stop"])
+    rep = ob.baca_replay(ogen_leaf, d, eps, g["trace"], seed=seed, bid=bid, stop=g["stop"], srrqr_f=srrqr_f)
     if rounding_sensitive and rep["recs"]:
         last = rep["recs"][-1]
         scale = max([r.get("mu", 0.0) for r in rep["recs"]] + [0.0])

@@ -53,7 +53,7 @@ int main(void) {
   printf("hbaca_gen %zu\nhbaca_opts %zu\nhbaca_result %zu\nhbaca_leaf_trace %zu\n",
          sizeof(hbaca_gen), sizeof(hbaca_opts), sizeof(hbaca_result), sizeof(hbaca_leaf_trace));
   F(hbaca_gen, h) F(hbaca_gen, a) F(hbaca_gen, K) F(hbaca_gen, q2) F(hbaca_gen, r2)
-  F(hbaca_opts, seed) F(hbaca_opts, flags) F(hbaca_opts, cluster)
+  F(hbaca_opts, seed) F(hbaca_opts, flags) F(hbaca_opts, cluster) F(hbaca_opts, srrqr_f)
   F(hbaca_result, d_rank) F(hbaca_result, rank) F(hbaca_result, leaf_iters_max)
   F(hbaca_leaf_trace, I) F(hbaca_leaf_trace, mu)
   return 0;

@@ -27,14 +27,15 @@ def ctx():
 
 
 def run_and_compare(ctx, spec, ogen, L, d, eps, seed=0, rank_cap=128, leaf_cap=256, cluster=0,
-                    check_all_leaves=True, dense=True, free_compare=True, rounding_sensitive=False):
+                    check_all_leaves=True, dense=True, free_compare=True, rounding_sensitive=False, srrqr_f=None):
     """Run the CUDA path; for every checked leaf (1) compare its pivots with a
     free oracle run while decisions are unique by margin, (2) replay its
     pivots through the oracle and require every choice valid and the norms
     and ranks equal.  Returns the result, the number of iterations matched by
     (1), the number of leaves whose free run diverged, and the pivot records
     (leaf -> record) for a frozen-pivot oracle H-BACA."""
-    opts = B.make_opts(eps, d, L, seed=seed, rank_cap=rank_cap, leaf_rank_cap=leaf_cap, cluster=cluster)
+    opts = B.make_opts(eps, d, L, seed=seed, rank_cap=rank_cap, leaf_rank_cap=leaf_cap, cluster=cluster,
+                       srrqr_f=srrqr_f or 0.0)
     res = B.compress(ctx, spec, opts)
     torch.cuda.synchronize()
     rows = oh.tree_levels(ogen.m, L)[0]
@@ -55,7 +56,7 @@ def run_and_compare(ctx, spec, ogen, L, d, eps, seed=0, rank_cap=128, leaf_cap=2
             k, div = compare_leaf(o, g, eps)
             compared += k
             diverged += div
-        rep = check_leaf_replay(w, g, d, eps, seed, bid, rounding_sensitive)
+        rep = check_leaf_replay(w, g, d, eps, seed, bid, rounding_sensitive, srrqr_f)
         if not rep["comparable"]:
             diverged += 1
             continue
@@ -273,6 +274,46 @@ def test_product_of_random_exact_rank(ctx, cplx):
     A = LU @ LV
     err = dense_rel_error(A, res.U.cpu().numpy(), res.S.cpu().numpy(), res.V.cpu().numpy())
     assert err < 1e-12
+
+
+def _pivot_sets(tr):
+    return [(tuple(t["I"]), tuple(t["J"])) for leaf in sorted(tr) for t in tr[leaf]["trace"]]
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_strong_rrqr_pivots(ctx, cplx):
+    """BACA with strong-RRQR pivot sets (f = 1.1): every GPU set passes the
+    oracle's frozen replay with the strong criterion (no swap above f^2 left,
+    the greedy count of distinct candidates), norms and ranks agree; the
+    criterion is discriminating (the greedy GPU record of the same leaves
+    fails it somewhere, and the refined sets differ from the greedy ones);
+    the final error meets the tolerance."""
+    f = 1.1
+    if cplx:
+        x, y = inputs.sphere_pair(seed=6, m=1000, n=900)
+        spec, og_ = B.helmholtz(x, y, 4 * np.pi), og.Helmholtz(x, y, 4 * np.pi)
+    else:
+        x, y = inputs.gaussian_pair(seed=6, m=1000, n=900)
+        spec, og_ = B.gaussian(x, y, 0.8), og.Gaussian(x, y, 0.8)
+    eps, d, L = 1e-8, 8, 1
+    res, _, div, tr = run_and_compare(ctx, spec, og_, L, d, eps, seed=3, rank_cap=256, leaf_cap=256,
+                                      free_compare=False, srrqr_f=f)
+    assert div == 0
+    greedy, _, _, tr0 = run_and_compare(ctx, spec, og_, L, d, eps, seed=3, rank_cap=256, leaf_cap=256,
+                                        free_compare=False)
+    assert _pivot_sets(tr) != _pivot_sets(tr0)
+    rows = oh.tree_levels(og_.m, L)[0]
+    cols = oh.tree_levels(og_.n, L)[0]
+    failed = 0
+    for leaf, g in tr0.items():
+        a, b = divmod(leaf, 1 << L)
+        w = og.Window(og_, rows[a][0], rows[a][1], cols[b][0], cols[b][1])
+        rep = ob.baca_replay(w, d, eps, g["trace"], seed=3, bid=osamp.block_id(0, a, b), stop=g["stop"],
+                             srrqr_f=f)
+        failed += any(not (r["valid_I"] and r.get("valid_J", True)) for r in rep["recs"])
+    assert failed > 0
+    e = B.rel_error(ctx, spec, res)
+    assert e <= 10 * eps and res.rank <= greedy.rank + 4, (e, res.rank, greedy.rank)
 
 
 def test_aca_d1_matches_oracle(ctx):

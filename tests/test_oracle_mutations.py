@@ -107,3 +107,15 @@ def test_polynomial_without_square(monkeypatch):
     monkeypatch.setattr(og.Polynomial, "__call__",
                         lambda self, I, J: self.x[np.asarray(I)] @ self.y[np.asarray(J)].T + self.h)
     _expect_failure(pins.test_polynomial_generator_closed_form_and_rank)
+
+
+def test_strong_rrqr_criterion_without_residual_term(monkeypatch):
+    orig = ol.strong_rrqr_criterion
+
+    def bad(M, piv, rest):
+        A = M[:, piv]
+        Q, R11 = np.linalg.qr(A)
+        Ri = scipy.linalg.solve_triangular(R11, np.eye(len(piv)), lower=False)
+        return np.abs(Ri @ (Q.conj().T @ M[:, rest])) ** 2
+    monkeypatch.setattr(ol, "strong_rrqr_criterion", bad)
+    _expect_failure(pins.test_strong_rrqr_criterion_is_the_volume_ratio_of_a_swap, 9, 5)

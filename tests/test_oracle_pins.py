@@ -184,6 +184,50 @@ def test_greedy_qrcp_basis_spans_the_chosen_columns():
     assert piv[0] == 0 and diag[1] == 0.0 and np.all(Q[:, 1:] == 0.0)
 
 
+def _vol(M, piv):
+    """|det R11| of the chosen columns, from their singular values."""
+    return float(np.prod(np.linalg.svd(M[:, list(piv)], compute_uv=False)))
+
+
+@pytest.mark.parametrize("p,k", [(6, 6), (9, 5)])
+def test_strong_rrqr_criterion_is_the_volume_ratio_of_a_swap(p, k):
+    """sqrt(rho_ij) equals |det R11| after swapping chosen column i for
+    candidate j over |det R11| before (Gu & Eisenstat's Lemma), checked by
+    forming every swapped set; with p > k the residual norms gamma_j enter."""
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((p, 20)) + 1j * rng.standard_normal((p, 20))
+    piv = [3, 7, 11, 0, 15, 2][:k]
+    rest = [j for j in range(20) if j not in piv]
+    rho = ol.strong_rrqr_criterion(M, piv, rest)
+    v0 = _vol(M, piv)
+    for i in range(k):
+        for jj, j in enumerate(rest):
+            sw = list(piv)
+            sw[i] = j
+            assert abs(np.sqrt(rho[i, jj]) - _vol(M, sw) / v0) <= 1e-10 * (1 + _vol(M, sw) / v0)
+
+
+def test_strong_rrqr_ends_at_a_local_volume_maximum():
+    """After the refinement no single swap raises the volume by more than f
+    (brute force over every swap), every swap raised it by more than f, and
+    the volume is at least the greedy QRCP set's."""
+    rng = np.random.default_rng(6)
+    for trial in range(20):
+        M = rng.standard_normal((4, 25)) @ np.diag(rng.uniform(0.3, 1.5, 25))
+        g, _, _, _ = ol.greedy_qrcp(M, 4)
+        for f in (1.0, 1.2):
+            piv, sw = ol.strong_rrqr(M, g, f=f)
+            v = _vol(M, piv)
+            assert v >= _vol(M, g) * f ** sw * (1 - 1e-12)
+            for i in range(4):
+                for j in range(25):
+                    if j in piv:
+                        continue
+                    t = list(piv)
+                    t[i] = j
+                    assert _vol(M, t) <= f * v * (1 + 1e-10)
+
+
 def test_eps_rank_definition():
     assert ol.eps_rank([1.0, 0.5, 1e-7], 1e-6) == 2
     assert ol.eps_rank([2.0, 2e-6, 1e-7], 1e-6) == 2  # Sigma_{k+1} < eps Sigma_1 is strict
@@ -470,6 +514,32 @@ def test_coherent_case_is_rounding_sensitive():
     e0 = np.linalg.norm(A - (r0["U"] * r0["s"]) @ r0["V"]) / np.linalg.norm(A)
     e1 = np.linalg.norm(A - (r1["U"] * r1["s"]) @ r1["V"]) / np.linalg.norm(A)
     assert r0["r"] == r1["r"] and abs(e0 - e1) <= 1e-12 * max(e0, 1e-300) + 1e-15
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_baca_with_strong_rrqr_pivots(cplx):
+    """BACA with strong-RRQR pivot sets (f = 1.05): exact rank and rounding
+    error on a product of random factors, the cross property on the kept
+    columns, and the frozen replay of its own record valid (sets without a
+    swap above f^2 left)."""
+    LU, LV = inputs.lowrank(21, 160, 150, 11, complex_=cplx)
+    g = og.LowRank(LU, LV)
+    res = ob.baca(g, 8, 1e-10, seed=3, srrqr_f=1.05)
+    A = LU @ LV
+    assert len(ob.recompress(res["U"], res["V"], 1e-10)[1]) == 11
+    assert np.linalg.norm(A - res["U"] @ res["V"]) <= 1e-12 * np.linalg.norm(A)
+    rep = ob.baca_replay(g, 8, 1e-10, res["trace"], seed=3, stop=res["stop"], srrqr_f=1.05)
+    for r in rep["recs"]:
+        if r.get("noise_level"):
+            break
+        assert r["valid_I"] and r["valid_J"] and r["valid_W"] and r["valid_dk"], r
+    x, y = inputs.gaussian_pair(seed=9, m=300, n=280)
+    gg = og.Gaussian(x, y, 0.6)
+    res = ob.baca(gg, 8, 1e-9, seed=1, srrqr_f=1.0)
+    E = gg(np.arange(300), np.arange(280)) - res["U"] @ res["V"]
+    kept = [t["J"][p] for t in res["trace"] for p in t["jbar"]]
+    assert np.abs(E[:, kept]).max() <= 1e-10 * np.abs(E).max() + 1e-14
+    assert sum(sum(t["swaps"]) for t in res["trace"]) > 0  # the refinement acted
 
 
 # ---------------------------------------------------------------- frozen-pivot replay
