@@ -82,6 +82,15 @@ hbaca_status hbaca_debug_entries(const hbaca_gen* gen, const int64_t* rows, cons
    whatever CTA runs it); it exists to time the launch shapes. */
 int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster);
 
+/* Cluster size (CTAs per matrix, 1 .. 16) of the Householder QR and the Q
+   application of every merge and re-compression stage in every later
+   synchronous call in this process, one cluster per matrix; 0 restores the
+   per-stage choice (which may spread a matrix over several clusters).
+   Returns the previous setting.  The partial sums are combined in CTA order,
+   so results depend on it at the rounding level; it exists to time the
+   launch shapes. */
+int32_t hbaca_debug_set_qr_cluster(int32_t cluster);
+
 /* Sweep cap of the one-sided Jacobi SVD (Sec. 2, SVD(A, eps)) used by every
    later call in this process: sweeps > 0 sets it, 0 restores the default
    (40).  Returns the cap in force before the call.  For tests that make a

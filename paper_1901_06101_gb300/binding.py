@@ -126,6 +126,7 @@ SIGNATURES = [
     ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_jacobi_cluster", ctypes.c_int32, [ctypes.c_int32]),
+    ("hbaca_debug_set_qr_cluster", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
     ("hbaca_debug_launch_times", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_void_p, ctypes.c_int32]),
@@ -354,6 +355,13 @@ def rel_error(ctx, spec, comp, rows=None):
     """sqrt(error_norms ratio): ||A - U S V||_F / ||A||_F on the device."""
     e2, a2 = error_norms(ctx, spec, comp, rows)
     return (e2 / a2) ** 0.5 if a2 > 0 else 0.0
+
+
+def set_qr_cluster(c):
+    """hbaca_debug_set_qr_cluster: CTAs per matrix of the QR and Q-application
+    launches of later calls (0 = per-stage choice); returns the previous
+    setting."""
+    return int(lib().hbaca_debug_set_qr_cluster(int(c)))
 
 
 def set_jacobi_cluster(c):

@@ -82,6 +82,7 @@ hbaca_status map_device_status(int ds) {
 constexpr int kDefaultJacobiSweeps = 40;
 std::atomic<int> g_jacobi_sweeps{kDefaultJacobiSweeps};
 std::atomic<int> g_jacobi_cluster{0};
+std::atomic<int> g_qr_cluster{0};
 
 }  // namespace
 
@@ -90,6 +91,7 @@ hbaca_status record_error(hbaca_status s, const std::string& msg) { return fail(
 int ctx_device(const hbaca_ctx* ctx) { return ctx->device; }
 int jacobi_max_sweeps() { return g_jacobi_sweeps.load(std::memory_order_relaxed); }
 int jacobi_forced_cluster() { return g_jacobi_cluster.load(std::memory_order_relaxed); }
+int qr_forced_cluster() { return g_qr_cluster.load(std::memory_order_relaxed); }
 }  // namespace hbaca
 
 extern "C" {
@@ -592,6 +594,11 @@ hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES],
 int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster) {
   const int v = cluster >= 1 && cluster <= 16 ? cluster : 0;
   return g_jacobi_cluster.exchange(v);
+}
+
+int32_t hbaca_debug_set_qr_cluster(int32_t cluster) {
+  const int v = cluster >= 1 && cluster <= 16 ? cluster : 0;
+  return g_qr_cluster.exchange(v);
 }
 
 int32_t hbaca_debug_set_jacobi_sweeps(int32_t sweeps) {

@@ -380,6 +380,77 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Warp sums of N doubles per lane (N a power of two <= 32) by recursive
+// halving: at the shuffle distance 16 >> t a lane keeps half of its values
+// and adds its partner's copies of them, so every FP64 add is a full-warp
+// one (N - 1 + 5 - log2 N adds for N sums instead of 5 N).  Returns, in lane
+// L, the sum of value reduce_scatter_index<N>(L).
+template <int N>
+__device__ __forceinline__ double warp_reduce_scatter(double (&v)[N], int lane) {
+  static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "N must be a power of two <= 32");
+#pragma unroll
+  for (int t = 0; (N >> t) > 1; ++t) {
+    const int o = 16 >> t, half = N >> (t + 1);
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const double send = up ? v[k] : v[k + half];
+      const double keep = up ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  constexpr int lg = N >= 32 ? 5 : N >= 16 ? 4 : N >= 8 ? 3 : N >= 4 ? 2 : N >= 2 ? 1 : 0;
+#pragma unroll
+  for (int o = 16 >> lg; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
+template <int N>
+__device__ __forceinline__ int reduce_scatter_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int t = 0; (N >> t) > 1; ++t) idx += ((lane >> (4 - t)) & 1) * (N >> (t + 1));
+  return idx;
+}
+
+// Warp sums of two values of type T per lane: lane L ends with component
+// comp of value col (T = double: one component), and it is the first lane
+// holding that sum when (L & mask) == 0.
+template <typename T>
+__device__ __forceinline__ double warp_sum2(T a0, T a1, int lane, int& col, int& comp, bool& first);
+template <>
+__device__ __forceinline__ double warp_sum2<double>(double a0, double a1, int lane, int& col, int& comp, bool& first) {
+  double v[2] = {a0, a1};
+  const double s = warp_reduce_scatter<2>(v, lane);
+  col = reduce_scatter_index<2>(lane);
+  comp = 0;
+  first = (lane & 15) == 0;
+  return s;
+}
+template <>
+__device__ __forceinline__ double warp_sum2<cplx>(cplx a0, cplx a1, int lane, int& col, int& comp, bool& first) {
+  double v[4] = {a0.re, a0.im, a1.re, a1.im};
+  const double s = warp_reduce_scatter<4>(v, lane);
+  const int idx = reduce_scatter_index<4>(lane);
+  col = idx >> 1;
+  comp = idx & 1;
+  first = (lane & 7) == 0;
+  return s;
+}
+
+// Both warp sums of two values per lane, in every lane.
+__device__ __forceinline__ void warp_sum2_all(double& a0, double& a1, int lane) {
+  double v[2] = {a0, a1};
+  const double s = warp_reduce_scatter<2>(v, lane);
+  a0 = __shfl_sync(0xffffffffu, s, 0);
+  a1 = __shfl_sync(0xffffffffu, s, 16);
+}
+__device__ __forceinline__ void warp_sum2_all(cplx& a0, cplx& a1, int lane) {
+  double v[4] = {a0.re, a0.im, a1.re, a1.im};
+  const double s = warp_reduce_scatter<4>(v, lane);
+  a0 = mk(__shfl_sync(0xffffffffu, s, 0), __shfl_sync(0xffffffffu, s, 8));
+  a1 = mk(__shfl_sync(0xffffffffu, s, 16), __shfl_sync(0xffffffffu, s, 24));
+}
+
 // (bits, index) argmax: larger bits win, ties go to the smaller index.
 __device__ __forceinline__ void argmax_merge(long long& b, int& i, long long ob, int oi) {
   if (ob > b || (ob == b && oi < i)) {

@@ -247,18 +247,35 @@ __global__ void __launch_bounds__(kDenseThreads) qr_kernel(const DenseParams<T> 
     T* pb = part + (j & 1) * plen;
     const int i0 = max(ra, j + 1);
     const int ncol = k - j;  // column j and trailing ones
-    for (int l = warp; l < ncol; l += nw) {
+    // two columns per warp: their inner products with column j share its
+    // loads and are summed over the warp together
+    for (int l0 = 2 * warp; l0 < ncol; l0 += 2 * nw) {
       const T* colj = A + (int64_t)j * lda;
-      const T* coll = A + (int64_t)(j + l) * lda;
-      T acc = Traits<T>::zero();
-      for (int i = i0 + lane; i < rb; i += 32) acc = cmac(acc, colj[i], coll[i]);
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        if (l == 0) pb[0] = acc;
-        else pb[2 + (l - 1)] = acc;
+      const T* c0 = A + (int64_t)(j + l0) * lda;
+      const bool two = l0 + 1 < ncol;  // warp-uniform
+      T a0 = Traits<T>::zero(), a1 = Traits<T>::zero();
+      if (two) {
+        for (int i = i0 + lane; i < rb; i += 32) {
+          const T xj = colj[i];
+          a0 = cmac(a0, xj, c0[i]);
+          a1 = cmac(a1, xj, c0[lda + i]);
+        }
+      } else {
+        for (int i = i0 + lane; i < rb; i += 32) a0 = cmac(a0, colj[i], c0[i]);
+      }
+      int col, comp;
+      bool first;
+      const double sum = warp_sum2<T>(a0, a1, lane, col, comp, first);
+      const int l = l0 + col;
+      if (first && l < ncol) {
+        T* dst = l == 0 ? pb : pb + 2 + (l - 1);
+        reinterpret_cast<double*>(dst)[comp] = sum;
+      }
+      if (lane < 2 && l0 + lane < ncol) {
+        const int lh = l0 + lane;
         const bool own = (j >= ra && j < rb);
-        if (l == 0) pb[1] = own ? A[(int64_t)j * lda + j] : Traits<T>::zero();
-        else pb[2 + t.kcap + (l - 1)] = own ? A[(int64_t)(j + l) * lda + j] : Traits<T>::zero();
+        if (lh == 0) pb[1] = own ? A[(int64_t)j * lda + j] : Traits<T>::zero();
+        else pb[2 + t.kcap + (lh - 1)] = own ? A[(int64_t)(j + lh) * lda + j] : Traits<T>::zero();
       }
     }
     __syncthreads();
@@ -457,13 +474,21 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
   const int own = (nc - q + c - 1) / c;  // columns q, q + c, ...
   for (int st = 0; st < p; ++st) {
     // norms of this CTA's unchosen columns, local argmax
-    for (int l = warp; l < own; l += nw) {
-      const int j = q + l * c;
-      if (chosen[j]) continue;
-      double a = 0.0;
-      for (int i = st + lane; i < mr; i += 32) a += abs2(M[(int64_t)j * ld + i]);
-      a = warp_sum(a);
-      if (lane == 0) nrm[j] = a;
+    // two columns per warp, summed over the warp together
+    for (int l = 2 * warp; l < own; l += 2 * nw) {
+      const int j0 = q + l * c, j1 = j0 + c;
+      const bool u0 = !chosen[j0], u1 = l + 1 < own && !chosen[j1];  // warp-uniform
+      if (!u0 && !u1) continue;
+      double a0 = 0.0, a1 = 0.0;
+      for (int i = st + lane; i < mr; i += 32) {
+        if (u0) a0 += abs2(M[(int64_t)j0 * ld + i]);
+        if (u1) a1 += abs2(M[(int64_t)j1 * ld + i]);
+      }
+      warp_sum2_all(a0, a1, lane);
+      if (lane == 0) {
+        if (u0) nrm[j0] = a0;
+        if (u1) nrm[j1] = a1;
+      }
     }
     __syncthreads();
     long long bb = -1;
@@ -518,17 +543,31 @@ __global__ void __launch_bounds__(kWideThreads) qrcp_core_kernel(const DensePara
     for (int i = st + 1 + tid; i < mr; i += blockDim.x) rv[i] = ldcg(col + i);
     const T ctau = *cl.map_shared_rank(coef, owner);
     __syncthreads();
-    for (int l = warp; l < own; l += nw) {
-      const int j = q + l * c;
-      if (chosen[j]) continue;
-      T* y = M + (int64_t)j * ld;
-      T w = Traits<T>::zero();
-      for (int i = st + 1 + lane; i < mr; i += 32) w = cmac(w, rv[i], y[i]);
-      w = warp_sum(w);
-      w = add(w, y[st]);
-      const T f = mul(ctau, w);
-      if (lane == 0) y[st] = sub(y[st], f);
-      for (int i = st + 1 + lane; i < mr; i += 32) y[i] = msub(y[i], rv[i], f);
+    for (int l = 2 * warp; l < own; l += 2 * nw) {  // two columns per warp
+      const int j0 = q + l * c, j1 = j0 + c;
+      const bool u0 = !chosen[j0], u1 = l + 1 < own && !chosen[j1];  // warp-uniform
+      if (!u0 && !u1) continue;
+      T* y0 = M + (int64_t)j0 * ld;
+      T* y1 = M + (int64_t)j1 * ld;
+      T w0 = Traits<T>::zero(), w1 = Traits<T>::zero();
+      for (int i = st + 1 + lane; i < mr; i += 32) {
+        const T r = rv[i];
+        if (u0) w0 = cmac(w0, r, y0[i]);
+        if (u1) w1 = cmac(w1, r, y1[i]);
+      }
+      warp_sum2_all(w0, w1, lane);
+      if (u0) {
+        const T f = mul(ctau, add(w0, y0[st]));
+        __syncwarp();
+        if (lane == 0) y0[st] = sub(y0[st], f);
+        for (int i = st + 1 + lane; i < mr; i += 32) y0[i] = msub(y0[i], rv[i], f);
+      }
+      if (u1) {
+        const T f = mul(ctau, add(w1, y1[st]));
+        __syncwarp();
+        if (lane == 0) y1[st] = sub(y1[st], f);
+        for (int i = st + 1 + lane; i < mr; i += 32) y1[i] = msub(y1[i], rv[i], f);
+      }
     }
     // the owner may overwrite coef only after every CTA has read it
     cl.sync();
@@ -660,7 +699,8 @@ struct JPair {
   T ga;
   double cs, sn;
   T sp, cp;
-  int ok, a, b, pad;  // a, b: the pair's columns
+  int ok, a, b;  // a, b: the pair's columns
+  float c2;      // |gamma|^2 / (alpha beta) of a rotation that counts against convergence
 };
 constexpr int kJSlotMax = 96;  // bytes reserved per pair slot (>= sizeof(JPair<cplx>))
 
@@ -675,7 +715,7 @@ template <typename T, bool kDsm>
 __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
                               T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
                               int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot,
-                              bool acc_w, T* const* ctab) {
+                              bool acc_w, T* const* ctab, int* c2bits, bool& converged) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   // column addresses from the table (no division by the cluster size per access)
   auto colX = [&](int j) -> T* { return ctab[j]; };
@@ -699,7 +739,7 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
   for (; sweep < max_sweeps && K > 1; ++sweep) {
     const double tau2 = 0.01 * eps * eps * cmax;
     double wmax = 0.0;
-    if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; }
+    if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; c2bits[fb & 1] = 0; }
     __syncthreads();
     for (int rd = 0; rd < K - 1; ++rd) {
       // (1) inner products of this warp's pairs; the first pass keeps its
@@ -745,9 +785,14 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
               ga = cmac(ga, xa, xb);
             }
           }
-          al = warp_sum(al);
-          be = warp_sum(be);
-          ga = warp_sum(ga);
+          // the four sums by recursive halving (6 FP64 adds instead of 20),
+          // then every lane takes them from the lanes that hold them
+          double v4[4] = {al, be, re_(ga), im_(ga)};
+          const double sum = warp_reduce_scatter<4>(v4, lane);
+          al = __shfl_sync(0xffffffffu, sum, 0);
+          be = __shfl_sync(0xffffffffu, sum, 8);
+          if constexpr (Traits<T>::is_complex) ga = mk(__shfl_sync(0xffffffffu, sum, 16), __shfl_sync(0xffffffffu, sum, 24));
+          else ga = __shfl_sync(0xffffffffu, sum, 16);
           wmax = fmax(wmax, fmax(al, be));
         }
         if (lane == 0) {
@@ -772,6 +817,11 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
           sl.sn = sn;
           sl.sp = scale(ph, sn);
           sl.cp = scale(ph, cs);
+          if (fmax(sl.al, sl.be) >= tau2) {  // counts; the largest cosine^2 of the sweep's counted rotations
+            sl.ok = 2;
+            const float c2 = (float)(abs2(sl.ga) / (sl.al * sl.be));
+            atomicMax(&c2bits[fb & 1], __float_as_int(c2));
+          }
         } else {
           sl.ok = 0;
         }
@@ -784,7 +834,7 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
         const int a = sl.a, b = sl.b;
         const double cs = sl.cs, sn = sl.sn;
         const T spv = sl.sp, cpv = sl.cp;
-        if (lane == 0 && fmax(sl.al, sl.be) >= tau2) flag[fb & 1] = 1;
+        if (lane == 0 && sl.ok == 2) flag[fb & 1] = 1;
         ++nrot;
         T* ca = colX(a);
         T* cb = colX(b);
@@ -809,17 +859,22 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(cmx), (unsigned long long)__double_as_longlong(wmax));
     __syncthreads();
     cl.sync();
-    // any relevant rotation anywhere in the cluster this sweep?
-    int any = 0;
+    // any relevant rotation anywhere in the cluster this sweep?  And the
+    // largest cosine among them: the sweeps converge quadratically, so after a
+    // sweep whose cosines are all below 0.1 sqrt(tol) the next one would find
+    // none above tol (its only work would be the inner products): stop here
+    int any = 0, c2b = 0;
     double cm = 0.0;
     for (int r = 0; r < c; ++r) {
       any |= *cl.map_shared_rank(&flag[fb & 1], r);
       cm = fmax(cm, *cl.map_shared_rank(cmx, r));
+      c2b = max(c2b, *cl.map_shared_rank(&c2bits[fb & 1], r));
     }
     if (cm > 0.0) cmax = cm;
     ++fb;
     cl.sync();
-    if (!any) break;
+    if (!any) { converged = true; break; }
+    if ((double)__int_as_float(c2b) < 0.01 * tol) { converged = true; break; }  // sweep = executed - 1, as above
   }
 }
 
@@ -908,6 +963,10 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   if (tid == 0) { flag[0] = 0; flag[1] = 0; }
   cl.sync();
   JPair<T>* slots = reinterpret_cast<JPair<T>*>(smem_raw + slot_off);
+  // two ints of the header's slack just below the pair slots (slot_off is at
+  // least 56 bytes past the order table)
+  int* c2bits = reinterpret_cast<int*>(smem_raw + slot_off - 8);
+  bool converged = false;
   // column addresses of X for the sweeps, in the singular-value area (free
   // until the epilogue): column j in CTA j mod c (DSMEM) or in global memory
   T** ctab = reinterpret_cast<T**>(sv);
@@ -916,15 +975,15 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   __syncthreads();
   if (use_dsm)
     jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
-                           slots, sweep, nrot, acc_w, ctab);
+                           slots, sweep, nrot, acc_w, ctab, c2bits, converged);
   else
     jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
-                            cmx, slots, sweep, nrot, acc_w, ctab);
+                            cmx, slots, sweep, nrot, acc_w, ctab, c2bits, converged);
   // the sweep cap was reached while relevant rotations were still being
   // applied: the singular values and the eps-rank come from an unconverged
   // SVD, which the call reports (the loop leaves through its convergence
   // test before the cap otherwise)
-  if (K > 1 && sweep >= max_sweeps && q == 0 && tid == 0) set_status(P.status, DS_NOT_CONVERGED);
+  if (K > 1 && !converged && q == 0 && tid == 0) set_status(P.status, DS_NOT_CONVERGED);
   __syncthreads();
   if (use_dsm) {  // the sweeps' result back to global memory for the epilogue and finish_kernel
     for (int l = warp; l < per; l += nw) {
@@ -1007,10 +1066,13 @@ constexpr int kMaxWsolveCols = 1024;  // kept triplets of one output (rank caps 
 
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads) wsolve_kernel(const DenseParams<T> P) {
-  const int ti = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
+  const int ti = blockIdx.x / c;
   const SvdTask t = P.tasks[ti];
   const BlockRef ob = P.out_blocks[t.out];
-  if (ob.full_slot >= 0) return;  // taped: W was accumulated
+  if (ob.full_slot >= 0) return;  // taped: W was accumulated (uniform over the cluster)
   const TaskDims dm = P.dims[ti];
   const int s = min(dm.nout, kMaxWsolveCols);
   const int ncm = t.kind == TASK_LEAF ? dm.krb : dm.k;
@@ -1024,49 +1086,83 @@ __global__ void __launch_bounds__(kDenseThreads) wsolve_kernel(const DenseParams
   const int32_t* ord = P.ord + t.ord_off;
   const double* sg = out_s(P, ob);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // w_tc(r) = sum_{c >= r} R2(r, c) z_ord(c) / sigma_tc; a thread per (tc, r)
-  for (int tc = warp; tc < s; tc += nw) {
+  // w_tc(r) = sum_{c >= r} R2(r, c) z_ord(c) / sigma_tc; a warp per tc (dealt
+  // over the cluster), a lane per r
+  for (int tc = q * nw + warp; tc < s; tc += c * nw) {
     const int j = ord[tc];
     const double inv = sg[tc] > 0.0 ? 1.0 / sg[tc] : 0.0;
     const T* z = Z + (int64_t)j * ld;
     T* w = W + (int64_t)j * ld;
     for (int r = lane; r < p; r += 32) {
       T acc = Traits<T>::zero();
-      for (int c = r; c < ncm; ++c) acc = mac(acc, R2[(int64_t)perm[c] * ld + r], ldcg(z + c));
+      for (int cc = r; cc < ncm; ++cc) acc = mac(acc, R2[(int64_t)perm[cc] * ld + r], ldcg(z + cc));
       w[r] = scale(acc, inv);
     }
   }
-  __syncthreads();
   // one classical Gram-Schmidt pass in the sorted order (the columns are
-  // orthonormal up to ~eps_mach / eps, so one pass suffices)
-  __shared__ double red[32];
-  __shared__ T dd[kMaxWsolveCols];
+  // orthonormal up to ~eps_mach / eps, so one pass suffices); CTA q of the
+  // cluster owns a slice of the rows, and the inner products and norms are
+  // summed over the cluster in rank order (the same totals in every CTA)
+  T* part = reinterpret_cast<T*>(smem_raw);   // [2][s] partial inner products (step parity)
+  T* dd = part + 2 * s;                        // [s] totals
+  double* pn = reinterpret_cast<double*>(dd + s);  // [2] partial norms^2 (step parity)
+  double* red = pn + 2;                        // [32]
+  const int chunk = (p + c - 1) / c;
+  const int ra = min(p, q * chunk), rb = min(p, ra + chunk);
+  __syncthreads();
+  cl.sync();  // every W column complete (other CTAs' rows are read through L2)
   for (int tc = 0; tc < s; ++tc) {
     T* wt = W + (int64_t)ord[tc] * ld;
-    for (int u = warp; u < tc; u += nw) {  // d_u = w_u^H w_tc
-      const T* wu = W + (int64_t)ord[u] * ld;
-      T part = Traits<T>::zero();
-      for (int r = lane; r < p; r += 32) part = cmac(part, wu[r], wt[r]);
-      part = warp_sum(part);
-      if (lane == 0) dd[u] = part;
+    T* pb = part + (tc & 1) * s;
+    for (int u = 2 * warp; u < tc; u += 2 * nw) {  // partial d_u = w_u^H w_tc, two per warp
+      const bool two = u + 1 < tc;  // warp-uniform
+      const T* wu0 = W + (int64_t)ord[u] * ld;
+      const T* wu1 = W + (int64_t)ord[two ? u + 1 : u] * ld;
+      T p0 = Traits<T>::zero(), p1 = Traits<T>::zero();
+      for (int r = ra + lane; r < rb; r += 32) {
+        const T x = ldcg(wt + r);
+        p0 = cmac(p0, ldcg(wu0 + r), x);
+        if (two) p1 = cmac(p1, ldcg(wu1 + r), x);
+      }
+      warp_sum2_all(p0, p1, lane);
+      if (lane == 0) {
+        pb[u] = p0;
+        if (two) pb[u + 1] = p1;
+      }
     }
     __syncthreads();
-    double part = 0.0;
-    for (int r = tid; r < p; r += blockDim.x) {  // w_tc -= sum_u w_u d_u
-      T v = wt[r];
-      for (int u = 0; u < tc; ++u) v = msub(v, W[(int64_t)ord[u] * ld + r], dd[u]);
+    if (tc > 0) {
+      cl.sync();
+      for (int u = tid; u < tc; u += blockDim.x) {
+        T sum = Traits<T>::zero();
+        for (int r = 0; r < c; ++r) sum = add(sum, cl.map_shared_rank(part + (tc & 1) * s, r)[u]);
+        dd[u] = sum;
+      }
+      __syncthreads();
+    }
+    double nloc = 0.0;
+    for (int r = ra + tid; r < rb; r += blockDim.x) {  // w_tc -= sum_u w_u d_u (own rows)
+      T v = ldcg(wt + r);
+      for (int u = 0; u < tc; ++u) v = msub(v, ldcg(W + (int64_t)ord[u] * ld + r), dd[u]);
       wt[r] = v;
-      part += abs2(v);
+      nloc += abs2(v);
     }
-    part = warp_sum(part);
-    if (lane == 0) red[warp] = part;
+    nloc = warp_sum(nloc);
+    if (lane == 0) red[warp] = nloc;
     __syncthreads();
+    if (tid == 0) {
+      double a = 0.0;
+      for (int q2 = 0; q2 < nw; ++q2) a += red[q2];
+      pn[tc & 1] = a;
+    }
+    cl.sync();
     double nrm = 0.0;
-    for (int q2 = 0; q2 < nw; ++q2) nrm += red[q2];
+    for (int r = 0; r < c; ++r) nrm += *cl.map_shared_rank(pn + (tc & 1), r);
     const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-    for (int r = tid; r < p; r += blockDim.x) wt[r] = scale(wt[r], inv);
+    for (int r = ra + tid; r < rb; r += blockDim.x) wt[r] = scale(wt[r], inv);
     __syncthreads();
   }
+  cl.sync();  // the normalised W complete before any CTA leaves (DSMEM reads done)
 }
 
 // ------------------------------------------------------------------ finish
@@ -1153,64 +1249,102 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
   const int chunk = (rows + np - 1) / np;
   const int ra = min(rows, (g * c + q) * chunk), rb = min(rows, ra + chunk);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  T* part = reinterpret_cast<T*>(smem_raw);  // 2 x s partials
-  T* wv = part + 2 * s;                       // s combined
+  // reflectors are applied two at a time (H_{j-1} H_j): with a = u_j^H D,
+  // b = u_{j-1}^H D and gamma = u_{j-1}^H u_j,
+  //   H_{j-1} H_j D = D - u_j w - u_{j-1} w',  w = tau_j a,  w' = tau_{j-1} (b - gamma w),
+  // so one pass over D forms both inner products and one pass updates it
+  const int plen = 2 * s + 1;                 // a (s), b (s), gamma
+  T* part = reinterpret_cast<T*>(smem_raw);  // 2 x plen partials (step parity)
+  T* tot = part + 2 * plen;                   // plen combined, then w (s), w' (s)
   for (int tc = 0; tc < s; ++tc)
     for (int i = ra + tid; i < rb; i += blockDim.x)
       D[(int64_t)tc * ldd + i] = i < kk ? Z[(int64_t)tc * t.kcap + i] : Traits<T>::zero();
   __syncthreads();
-  for (int j = kk - 1; j >= 0; --j) {
-    T* pb = part + (j & 1) * s;
+  const T one = from_re<T>(1.0), zero = Traits<T>::zero();
+  int step = 0;
+  for (int j = kk - 1; j >= 0; j -= 2, ++step) {
+    const bool pair = j >= 1;  // block-uniform
+    const int jm = j - 1;
+    T* pb = part + (step & 1) * plen;
     const T tj = tau[j];
-    const int i0 = max(ra, j);
+    const T tjm = pair ? tau[jm] : zero;
+    const int i0 = max(ra, pair ? jm : j);
+    const T* uj = A + (int64_t)j * lda;
+    const T* ujm = A + (int64_t)(pair ? jm : j) * lda;
     for (int tc = warp; tc < s; tc += nw) {
-      T acc = Traits<T>::zero();
+      const T* d = D + (int64_t)tc * ldd;
+      T a0 = zero, a1 = zero;
       for (int i = i0 + lane; i < rb; i += 32) {
-        const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];
-        acc = cmac(acc, u, D[(int64_t)tc * ldd + i]);
+        const T x = d[i];
+        const T vj = i < j ? zero : (i == j ? one : uj[i]);
+        a0 = cmac(a0, vj, x);
+        if (pair) a1 = cmac(a1, i == jm ? one : ujm[i], x);
       }
-      acc = warp_sum(acc);
-      if (lane == 0) pb[tc] = acc;
+      int col, comp;
+      bool first;
+      const double sum = warp_sum2<T>(a0, a1, lane, col, comp, first);
+      if (first) reinterpret_cast<double*>(pb + col * s + tc)[comp] = sum;
+    }
+    if (warp == nw - 1) {  // gamma over this CTA's rows (u_j vanishes above row j)
+      T g = zero;
+      if (pair)
+        for (int i = max(ra, j) + lane; i < rb; i += 32) g = cmac(g, ujm[i], i == j ? one : uj[i]);
+      g = warp_sum(g);
+      if (lane == 0) pb[2 * s] = g;
     }
     __syncthreads();
     cl.sync();
-    for (int tc = tid; tc < s; tc += blockDim.x) {
-      T sum = Traits<T>::zero();
-      for (int r = 0; r < c; ++r) sum = add(sum, cl.map_shared_rank(part + (j & 1) * s, r)[tc]);
-      wv[tc] = G > 1 ? sum : mul(tj, sum);
+    for (int e = tid; e < plen; e += blockDim.x) {
+      T sum = zero;
+      for (int r = 0; r < c; ++r) sum = add(sum, cl.map_shared_rank(part + (step & 1) * plen, r)[e]);
+      tot[e] = sum;
     }
     __syncthreads();
     if (G > 1) {
       if (q == 0) {
-        T* xs = X.xpart + ((size_t)cid * 2 + (j & 1)) * X.xplen;
-        for (int tc = tid; tc < s; tc += blockDim.x) xs[tc] = wv[tc];
+        T* xs = X.xpart + ((size_t)cid * 2 + (step & 1)) * X.xplen;
+        for (int e = tid; e < plen; e += blockDim.x) xs[e] = tot[e];
         __syncthreads();
-        if (tid == 0) xok = xgroup_arrive_wait(X.xcnt + job, (unsigned)(kk - j) * G, P.status);
+        if (tid == 0) xok = xgroup_arrive_wait(X.xcnt + job, (unsigned)(step + 1) * G, P.status);
       }
       cl.sync();
       if (*cl.map_shared_rank(&xok, 0) == 0) break;
-      for (int tc = tid; tc < s; tc += blockDim.x) {
-        T sum = Traits<T>::zero();
-        for (int gg = 0; gg < G; ++gg) sum = add(sum, ldcg(X.xpart + ((size_t)(job * G + gg) * 2 + (j & 1)) * X.xplen + tc));
-        wv[tc] = mul(tj, sum);
+      for (int e = tid; e < plen; e += blockDim.x) {
+        T sum = zero;
+        for (int gg = 0; gg < G; ++gg) sum = add(sum, ldcg(X.xpart + ((size_t)(job * G + gg) * 2 + (step & 1)) * X.xplen + e));
+        tot[e] = sum;
       }
       __syncthreads();
     }
-    // D(i, tc) -= u_i wv_tc: one thread per row, four columns per step
+    const T gam = tot[2 * s];
+    for (int tc = tid; tc < s; tc += blockDim.x) {
+      const T w = mul(tj, tot[tc]);
+      tot[tc] = w;
+      tot[s + tc] = pair ? mul(tjm, msub(tot[s + tc], gam, w)) : zero;
+    }
+    __syncthreads();
+    // D(i, tc) -= u_j(i) w_tc + u_{j-1}(i) w'_tc: one thread per row, four columns per step
+    const T* wa = tot;
+    const T* wb = tot + s;
     for (int i = i0 + tid; i < rb; i += blockDim.x) {
-      const T u = (i == j) ? from_re<T>(1.0) : A[(int64_t)j * lda + i];
+      const T vj = i < j ? zero : (i == j ? one : uj[i]);
+      const T vm = !pair ? zero : (i == jm ? one : ujm[i]);
       int tc = 0;
       for (; tc + 3 < s; tc += 4) {
         T* d0 = D + (int64_t)tc * ldd + i;
-        const T v0 = d0[0], v1 = d0[ldd], v2 = d0[2 * ldd], v3 = d0[3 * ldd];
-        d0[0] = msub(v0, u, wv[tc]);
-        d0[ldd] = msub(v1, u, wv[tc + 1]);
-        d0[2 * ldd] = msub(v2, u, wv[tc + 2]);
-        d0[3 * ldd] = msub(v3, u, wv[tc + 3]);
+        T v0 = d0[0], v1 = d0[ldd], v2 = d0[2 * ldd], v3 = d0[3 * ldd];
+        v0 = msub(msub(v0, vj, wa[tc]), vm, wb[tc]);
+        v1 = msub(msub(v1, vj, wa[tc + 1]), vm, wb[tc + 1]);
+        v2 = msub(msub(v2, vj, wa[tc + 2]), vm, wb[tc + 2]);
+        v3 = msub(msub(v3, vj, wa[tc + 3]), vm, wb[tc + 3]);
+        d0[0] = v0;
+        d0[ldd] = v1;
+        d0[2 * ldd] = v2;
+        d0[3 * ldd] = v3;
       }
       for (; tc < s; ++tc) {
         T* d0 = D + (int64_t)tc * ldd + i;
-        *d0 = msub(*d0, u, wv[tc]);
+        *d0 = msub(msub(*d0, vj, wa[tc]), vm, wb[tc]);
       }
     }
     __syncthreads();

@@ -97,6 +97,24 @@ inline int pick_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
   return c;
 }
 
+// CTAs per matrix of the QR and the Q application: the smallest of 1, 2, 4,
+// 8, 12, 16 that gives each CTA at most 420 rows, stepped down while the
+// stage would exceed 256 CTAs with more than 4 per matrix (at least 64 rows
+// per CTA).  From a sweep of forced sizes on the 20000^2 workload (QR + Q
+// application ms per stage, sizes 4 / 8 / 12 / 16): 1250-row matrices of the
+// leaf stage (512 of them) 140 / 153 / 218 / 233; 64 merges of 2500 rows 50
+// / 56 / 56 / 62; 32 of 2500 rows 33 / 27 / 31 / 31; 16 of 5000 rows 59 / 49
+// / 35 / 38; 8 of 5000 rows 55 / 29 / 20 / 26.  Stages of at most four
+// matrices spread each over several clusters instead (pick_groups).
+inline int pick_qr_cluster(int jobs, int rows, int min_rows_per_cta) {
+  static const int kSizes[] = {1, 2, 4, 8, 12, 16};
+  int k = 0;
+  while (k < 5 && rows > 420 * kSizes[k]) ++k;
+  while (k > 0 && kSizes[k] > 4 && (int64_t)jobs * kSizes[k] > 256) --k;
+  while (k > 0 && rows / kSizes[k] < min_rows_per_cta) --k;
+  return kSizes[k];
+}
+
 // Clusters per matrix when a stage has too few matrices to fill the machine
 // with one 16-CTA cluster each: 8-CTA clusters, as many per matrix as the
 // SMs (and the exchange slots) allow; 1 when that is not more than 16 CTAs.
@@ -221,13 +239,14 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   const QJob* aj = reinterpret_cast<const QJob*>(desc + sg.qjobs_off);
 
   HB_TIMED(KC_PACK, pack_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
-  int cq = pick_cluster(sg.nqr, sg.rows_max, rc.sms, 64);
+  int cq = pick_qr_cluster(sg.nqr, sg.rows_max, 64);
+  if (qr_forced_cluster() > 0) cq = qr_forced_cluster();
   const size_t qr_smem = (size_t)(3 * (2 + 2 * sg.kcap) + 4) * sizeof(T);
   const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
-  const size_t qa_smem = 3 * qa_cols * sizeof(T) + 64;
+  const size_t qa_smem = (6 * qa_cols + 3) * sizeof(T) + 64;
   XGroup<T> X{1, cq, sg.nqr, p.xplen, reinterpret_cast<T*>(ws + p.xpart.off),
               reinterpret_cast<unsigned*>(ws + p.xcnt.off)};
-  if (rc.xgroups && cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
+  if (rc.xgroups && qr_forced_cluster() == 0 && cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
     const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
                              resident_clusters(qapply_kernel<T>, 8, qa_smem, rc.st));
     const int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
@@ -363,7 +382,13 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     ++rc.launches;
   }
   if (!p.tape) {
-    HB_TIMED(KC_FINISH, wsolve_kernel<T><<<nt, kDenseThreads, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+    // a cluster per task (rows of the Gram-Schmidt pass split over it) while
+    // the stage has fewer tasks than SMs
+    int cw = 1;
+    while (cw < 16 && (int64_t)nt * cw * 2 <= rc.sms) cw *= 2;
+    const int wcols = p.tape ? sg.kcap : (int)std::min<int64_t>(sg.kcap, p.rank_cap_max);
+    const size_t ws_smem = (size_t)3 * std::min(wcols, kMaxWsolveCols) * sizeof(T) + 34 * sizeof(double);
+    HB_TIMED(KC_FINISH, HB_TRY(launch_cluster(wsolve_kernel<T>, nt * cw, cw, ws_smem, rc.st, D)));
     ++rc.launches;
   }
   {

@@ -82,4 +82,7 @@ int jacobi_max_sweeps();
 // Jacobi cluster size forced on every core of a synchronous call (0: chosen
 // per stage; hbaca_debug_set_jacobi_cluster).
 int jacobi_forced_cluster();
+// CTAs per matrix of the QR and Q-application launches forced by
+// hbaca_debug_set_qr_cluster (0: the per-stage choice).
+int qr_forced_cluster();
 }  // namespace hbaca
