@@ -136,13 +136,15 @@ def job_throughput(units_per_rank, seconds_max, world):
 def jacobi_accounting(ws, plan, complex_, accumulates=False):
     """Algorithmic FP64 flops of the Jacobi SVD launches of one compression,
     from the per-task records the kernel leaves (sizes, sweeps, rotations):
-    every sweep forms the three inner products of each of the nc (nc - 1) / 2
-    column pairs over the mr rows of the core, and every applied rotation
-    updates both columns of the core (mr rows), and of the accumulated
-    rotation (nc rows) when the call is taped (``accumulates``).  Per element:
-    inner products 16 flops (complex) / 6 (real), rotation 18 / 7."""
+    every sweep forms the squared norm of each of the nc columns once and the
+    inner product of each of the nc (nc - 1) / 2 column pairs over the mr rows
+    of the core (the norms are carried through the rotations), and every
+    applied rotation updates both columns of the core (mr rows), and of the
+    accumulated rotation (nc rows) when the call is taped (``accumulates``).
+    Per element: norm 4 flops (complex) / 2 (real), inner product 8 / 2,
+    rotation 18 / 7."""
     import torch
-    fd, fr = (16.0, 18.0) if complex_ else (6.0, 7.0)
+    fn, fd, fr = (4.0, 8.0, 18.0) if complex_ else (2.0, 2.0, 7.0)
     total = 0.0
     for st in plan["stages"]:
         nt = st["ntasks"]
@@ -153,7 +155,7 @@ def jacobi_accounting(ws, plan, complex_, accumulates=False):
             if nc < 2:
                 continue
             nsw = min(int(sweeps) + 1, 40)
-            total += nsw * nc * (nc - 1) / 2 * mr * fd + float(rot) * (mr + (nc if accumulates else 0)) * fr
+            total += nsw * (nc * mr * fn + nc * (nc - 1) / 2 * mr * fd) + float(rot) * (mr + (nc if accumulates else 0)) * fr
     return total
 
 

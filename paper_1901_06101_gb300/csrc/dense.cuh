@@ -20,6 +20,7 @@
 
 #include <cooperative_groups.h>
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "types.h"
@@ -623,7 +624,7 @@ __device__ __forceinline__ double pow2_inverse(double p2) {  // 1 / p2 for a pow
 
 template <typename T>
 __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, double tol, double negl, double fro2,
-                                                double& cs, double& sn, T& ph) {
+                                                double& cs, double& sn, T& ph, double& tout, double& gabs) {
   if (al < 1e-290 || be < 1e-290 || fmax(al, be) < negl) return false;
   const double mx = fmax(fabs(re_(ga)), fabs(im_(ga)));
   if (!(mx >= 1e-300)) return false;                            // zero (or denormal) gamma
@@ -645,6 +646,8 @@ __device__ __forceinline__ bool jacobi_rotation(double al, double be, T ga, doub
   }
   cs = rsqrt(fma(tt, tt, 1.0));
   sn = cs * tt;
+  tout = tt;
+  gabs = q * rq * pow2_below(mx);  // |gamma| = sqrt(q) / rm
   if constexpr (Traits<T>::is_complex) ph = mk(gr * rq, -gi * rq);  // e^{-i phi}, gamma = |gamma| e^{i phi}
   else ph = gr >= 0.0 ? 1.0 : -1.0;
   return true;
@@ -715,14 +718,31 @@ template <typename T, bool kDsm>
 __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
                               T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
                               int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot,
-                              bool acc_w, T* const* ctab, int* c2bits, bool& converged) {
+                              bool acc_w, T* const* ctab, int* c2bits, bool& converged, double* gnrm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   // column addresses from the table (no division by the cluster size per access)
   auto colX = [&](int j) -> T* { return ctab[j]; };
   auto colW = [&](int j) -> T* {
-    if constexpr (kDsm) return ctab[j] + mr;
+    if constexpr (kDsm) return ctab[j] + mr + 1;
     else return Y + (int64_t)j * ld;
   };
+  // The squared column norms (in the column's shared-memory slot after X, or
+  // in gnrm[j] on the global-memory path) are formed exactly at the start of
+  // every sweep and carried through the sweep's rotations by |a'|^2 = |a|^2 -
+  // t |gamma|, |b'|^2 = |b|^2 + t |gamma| (t the tangent), so a pair's inner
+  // product is gamma alone; an update that loses more than three digits to
+  // cancellation (the new value below 1e-3 of the old) is marked -1 and the
+  // norm is formed again with the pair's inner product.  Both paths do the
+  // same arithmetic.
+  auto nrm = [&](int j) -> double* {
+    if constexpr (kDsm) return reinterpret_cast<double*>(ctab[j] + mr);
+    else return gnrm + j;
+  };
+  auto nrm_ld = [&](int j) -> double {
+    if constexpr (kDsm) return *nrm(j);
+    else return ldcg(gnrm + j);
+  };
+  const int per = (nc + c - 1) / c;
   const int npairs = K / 2;
   const int stride = c * nw;                             // pairs dealt per pass over the cluster's warps
   const int per_warp = (npairs + stride - 1) / stride;   // passes (pairs per warp) per round
@@ -740,6 +760,18 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     const double tau2 = 0.01 * eps * eps * cmax;
     double wmax = 0.0;
     if (tid == 0) { flag[fb & 1] = 0; *cmx = 0.0; c2bits[fb & 1] = 0; }
+    for (int l = warp; l < per; l += nw) {  // this CTA's columns, exactly
+      const int j = l * c + q;
+      if (j >= nc) continue;
+      const T* cj = colX(j);
+      double v = 0.0;
+      for (int i = lane; i < mr; i += 32) v = acc_abs2(v, jld<T, kDsm>(cj + i));
+      v = warp_sum(v);
+      if (lane == 0) *nrm(j) = v;
+      wmax = fmax(wmax, v);
+    }
+    __syncthreads();
+    cl.sync();
     __syncthreads();
     for (int rd = 0; rd < K - 1; ++rd) {
       // (1) inner products of this warp's pairs; the first pass keeps its
@@ -761,39 +793,61 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
         if (act) {
           const T* ca = colX(a);
           const T* cb = colX(b);
-          if (regs) {
+          // the pair's inner products over the rows; with_norms: also |a|^2, |b|^2
+          auto dots = [&](auto with_norms) {
+            constexpr bool kN = decltype(with_norms)::value;
+            if (regs) {
 #pragma unroll
-            for (int u = 0; u < kJacRegs; ++u) {
-              const int i = lane + 32 * u;
-              if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
-                const T xa = i < mr ? jld<T, kDsm>(ca + i) : Traits<T>::zero();
-                const T xb = i < mr ? jld<T, kDsm>(cb + i) : Traits<T>::zero();
-                al = acc_abs2(al, xa);
-                be = acc_abs2(be, xb);
-                ga = cmac(ga, xa, xb);
-                if (u < kJacKeep && j == 0) {
-                  ka[u < kJacKeep ? u : 0] = xa;
-                  kb[u < kJacKeep ? u : 0] = xb;
+              for (int u = 0; u < kJacRegs; ++u) {
+                const int i = lane + 32 * u;
+                if (32 * u < mr) {  // warp-uniform: no FP64 work on padding
+                  const T xa = i < mr ? jld<T, kDsm>(ca + i) : Traits<T>::zero();
+                  const T xb = i < mr ? jld<T, kDsm>(cb + i) : Traits<T>::zero();
+                  if constexpr (kN) {
+                    al = acc_abs2(al, xa);
+                    be = acc_abs2(be, xb);
+                  }
+                  ga = cmac(ga, xa, xb);
+                  if (u < kJacKeep && j == 0) {
+                    ka[u < kJacKeep ? u : 0] = xa;
+                    kb[u < kJacKeep ? u : 0] = xb;
+                  }
                 }
               }
+            } else {
+              for (int i = lane; i < mr; i += 32) {
+                const T xa = jld<T, kDsm>(ca + i), xb = jld<T, kDsm>(cb + i);
+                if constexpr (kN) {
+                  al = acc_abs2(al, xa);
+                  be = acc_abs2(be, xb);
+                }
+                ga = cmac(ga, xa, xb);
+              }
             }
+          };
+          const double na = nrm_ld(a), nb = nrm_ld(b);
+          if (na < 0.0 || nb < 0.0) {  // warp-uniform
+            dots(std::true_type{});
+            // the four sums by recursive halving (6 FP64 adds instead of 20),
+            // then every lane takes them from the lanes that hold them
+            double v4[4] = {al, be, re_(ga), im_(ga)};
+            const double sum = warp_reduce_scatter<4>(v4, lane);
+            al = __shfl_sync(0xffffffffu, sum, 0);
+            be = __shfl_sync(0xffffffffu, sum, 8);
+            if constexpr (Traits<T>::is_complex) ga = mk(__shfl_sync(0xffffffffu, sum, 16), __shfl_sync(0xffffffffu, sum, 24));
+            else ga = __shfl_sync(0xffffffffu, sum, 16);
           } else {
-            for (int i = lane; i < mr; i += 32) {
-              const T xa = jld<T, kDsm>(ca + i), xb = jld<T, kDsm>(cb + i);
-              al = acc_abs2(al, xa);
-              be = acc_abs2(be, xb);
-              ga = cmac(ga, xa, xb);
+            dots(std::false_type{});
+            if constexpr (Traits<T>::is_complex) {
+              double v2[2] = {ga.re, ga.im};
+              const double sum = warp_reduce_scatter<2>(v2, lane);
+              ga = mk(__shfl_sync(0xffffffffu, sum, 0), __shfl_sync(0xffffffffu, sum, 16));
+            } else {
+              ga = warp_sum(ga);
             }
+            al = na;
+            be = nb;
           }
-          // the four sums by recursive halving (6 FP64 adds instead of 20),
-          // then every lane takes them from the lanes that hold them
-          double v4[4] = {al, be, re_(ga), im_(ga)};
-          const double sum = warp_reduce_scatter<4>(v4, lane);
-          al = __shfl_sync(0xffffffffu, sum, 0);
-          be = __shfl_sync(0xffffffffu, sum, 8);
-          if constexpr (Traits<T>::is_complex) ga = mk(__shfl_sync(0xffffffffu, sum, 16), __shfl_sync(0xffffffffu, sum, 24));
-          else ga = __shfl_sync(0xffffffffu, sum, 16);
-          wmax = fmax(wmax, fmax(al, be));
         }
         if (lane == 0) {
           JPair<T>& sl = slots[j * nw + warp];
@@ -810,9 +864,9 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
       for (int sidx = tid; sidx < per_warp * nw; sidx += blockDim.x) {
         JPair<T>& sl = slots[sidx];
         if (!sl.ok) continue;
-        double cs, sn;
+        double cs, sn, tt, gabs;
         T ph;
-        if (jacobi_rotation(sl.al, sl.be, sl.ga, tol, negl, fro2, cs, sn, ph)) {
+        if (jacobi_rotation(sl.al, sl.be, sl.ga, tol, negl, fro2, cs, sn, ph, tt, gabs)) {
           sl.cs = cs;
           sl.sn = sn;
           sl.sp = scale(ph, sn);
@@ -821,6 +875,11 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
             sl.ok = 2;
             const float c2 = (float)(abs2(sl.ga) / (sl.al * sl.be));
             atomicMax(&c2bits[fb & 1], __float_as_int(c2));
+          }
+          {  // the pair's norms after the rotation
+            const double na = fma(-tt, gabs, sl.al), nb = fma(tt, gabs, sl.be);
+            sl.al = na >= 1e-3 * sl.al ? na : -1.0;
+            sl.be = nb >= 1e-3 * sl.be ? nb : -1.0;
           }
         } else {
           sl.ok = 0;
@@ -834,7 +893,11 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
         const int a = sl.a, b = sl.b;
         const double cs = sl.cs, sn = sl.sn;
         const T spv = sl.sp, cpv = sl.cp;
-        if (lane == 0 && sl.ok == 2) flag[fb & 1] = 1;
+        if (lane == 0) {
+          if (sl.ok == 2) flag[fb & 1] = 1;
+          *nrm(a) = sl.al;
+          *nrm(b) = sl.be;
+        }
         ++nrot;
         T* ca = colX(a);
         T* cb = colX(b);
@@ -915,7 +978,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   // shared-memory slot holds X alone
   const bool acc_w = P.out_blocks[t.out].full_slot >= 0;
   const int per = (nc + c - 1) / c;
-  const int64_t ldc = (int64_t)mr + (acc_w ? nc : 0);
+  const int64_t ldc = (int64_t)mr + 1 + (acc_w ? nc : 0);  // X, the squared norm, W
   T* dsm = reinterpret_cast<T*>(smem_raw + hdr_bytes);
   const bool use_dsm = (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
   if (use_dsm) {  // own columns: X from global memory, W = I
@@ -925,7 +988,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
       T* dst = dsm + (int64_t)l * ldc;
       for (int i = lane; i < mr; i += 32) dst[i] = M[(int64_t)j * ld + i];
       if (acc_w)
-        for (int i = lane; i < nc; i += 32) dst[mr + i] = from_re<T>(i == j ? 1.0 : 0.0);
+        for (int i = lane; i < nc; i += 32) dst[mr + 1 + i] = from_re<T>(i == j ? 1.0 : 0.0);
     }
   } else if (acc_w) {  // Y = I
     const int j0 = q * per, j1 = min(nc, j0 + per);
@@ -967,6 +1030,9 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   // least 56 bytes past the order table)
   int* c2bits = reinterpret_cast<int*>(smem_raw + slot_off - 8);
   bool converged = false;
+  // the squared column norms of the global-memory path, in the compact-X
+  // area of the task (written only after the sweeps, by finish_kernel)
+  double* gnrm = reinterpret_cast<double*>(P.core + t.xs_off);
   // column addresses of X for the sweeps, in the singular-value area (free
   // until the epilogue): column j in CTA j mod c (DSMEM) or in global memory
   T** ctab = reinterpret_cast<T**>(sv);
@@ -975,10 +1041,10 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   __syncthreads();
   if (use_dsm)
     jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
-                           slots, sweep, nrot, acc_w, ctab, c2bits, converged);
+                           slots, sweep, nrot, acc_w, ctab, c2bits, converged, gnrm);
   else
     jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
-                            cmx, slots, sweep, nrot, acc_w, ctab, c2bits, converged);
+                            cmx, slots, sweep, nrot, acc_w, ctab, c2bits, converged, gnrm);
   // the sweep cap was reached while relevant rotations were still being
   // applied: the singular values and the eps-rank come from an unconverged
   // SVD, which the call reports (the loop leaves through its convergence
@@ -992,7 +1058,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
       const T* src = dsm + (int64_t)l * ldc;
       for (int i = lane; i < mr; i += 32) M[(int64_t)j * ld + i] = src[i];
       if (acc_w)
-        for (int i = lane; i < nc; i += 32) Y[(int64_t)j * ld + i] = src[mr + i];
+        for (int i = lane; i < nc; i += 32) Y[(int64_t)j * ld + i] = src[mr + 1 + i];
     }
   }
   cl.sync();

@@ -104,13 +104,20 @@ inline int pick_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
 // application ms per stage, sizes 4 / 8 / 12 / 16): 1250-row matrices of the
 // leaf stage (512 of them) 140 / 153 / 218 / 233; 64 merges of 2500 rows 50
 // / 56 / 56 / 62; 32 of 2500 rows 33 / 27 / 31 / 31; 16 of 5000 rows 59 / 49
-// / 35 / 38; 8 of 5000 rows 55 / 29 / 20 / 26.  Stages of at most four
-// matrices spread each over several clusters instead (pick_groups).
-inline int pick_qr_cluster(int jobs, int rows, int min_rows_per_cta) {
+// / 35 / 38; 8 of 5000 rows 55 / 29 / 20 / 26.  A stage that would still
+// leave half of the SMs idle is bound by the latency of its column steps and
+// takes as many CTAs per matrix as keep 60 rows each (the 2000^2 Gaussian
+// workload, QR + Q application ms per stage with 2 / 8 / 16 CTAs: 32 matrices
+// of 500 rows 1.45 / 1.13 / 1.23; 8 of 1000 rows 2.21 / 1.17 / 1.06; one of
+// 2000 rows 4.27 / 1.50 / 1.22).  Stages of at most four matrices spread
+// each over several clusters instead (pick_groups).
+inline int pick_qr_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
   static const int kSizes[] = {1, 2, 4, 8, 12, 16};
   int k = 0;
   while (k < 5 && rows > 420 * kSizes[k]) ++k;
   while (k > 0 && kSizes[k] > 4 && (int64_t)jobs * kSizes[k] > 256) --k;
+  if ((int64_t)jobs * kSizes[k] * 2 < sms)
+    while (k < 5 && rows / kSizes[k + 1] >= 60) ++k;
   while (k > 0 && rows / kSizes[k] < min_rows_per_cta) --k;
   return kSizes[k];
 }
@@ -239,7 +246,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   const QJob* aj = reinterpret_cast<const QJob*>(desc + sg.qjobs_off);
 
   HB_TIMED(KC_PACK, pack_kernel<T><<<dim3(64, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
-  int cq = pick_qr_cluster(sg.nqr, sg.rows_max, 64);
+  int cq = pick_qr_cluster(sg.nqr, sg.rows_max, rc.sms, 32);
   if (qr_forced_cluster() > 0) cq = qr_forced_cluster();
   const size_t qr_smem = (size_t)(3 * (2 + 2 * sg.kcap) + 4) * sizeof(T);
   const size_t qa_cols = p.tape ? std::max<size_t>((size_t)p.rank_cap_max, (size_t)sg.kcap) : (size_t)p.rank_cap_max;
@@ -335,8 +342,9 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     auto share_of = [&](int i, int cc) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int nc = std::min(dh[i].kra, ncm), mr = ncm;
-      // a column's slot: X (mr rows), and W (nc rows) when the call is taped
-      return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + (p.tape ? nc : 0)) * sizeof(T);
+      // a column's slot: X (mr rows), its squared norm, and W (nc rows) when
+      // the call is taped
+      return (size_t)((nc + cc - 1) / cc) * (size_t)(mr + 1 + (p.tape ? nc : 0)) * sizeof(T);
     };
     auto fit = [&](int i, int cc) {
       while (cc < 16 && share_of(i, cc) + j_hdr_of(cc) > kJacobiSmemLimit) ++cc;
@@ -375,7 +383,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     // they fit)
     const size_t j_base = (16 + (size_t)sg.kcap * 12 + 64 + 15) & ~(size_t)15;
     const size_t j_hdr = j_base + (((size_t)sg.kcap + 1) / 2 + (size_t)cj * 8 - 1) / ((size_t)cj * 8) * 8 * kJSlotMax;
-    const size_t j_cap = ((size_t)sg.kcap + cj - 1) / cj * 2 * (size_t)sg.kcap * sizeof(T);
+    const size_t j_cap = ((size_t)sg.kcap + cj - 1) / cj * (2 * (size_t)sg.kcap + 1) * sizeof(T);
     const size_t j_dsm = std::min(j_cap, (size_t)kJacobiSmemLimit - j_hdr);
     HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, jacobi_max_sweeps(), (int)j_hdr,
                                               (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr)));
