@@ -384,6 +384,39 @@ class Compressed:
         self.U, self.S, self.V, self.rank, self.ws, self.res = U, S, V, rank, ws, res
 
 
+_WS_CHECKED = {}
+
+
+def _check_workspace(ws, need_fn, key):
+    """The library cannot see the size of a caller's buffer: refuse a
+    workspace smaller than the plan of these arguments needs (the answer is
+    cached per argument bytes and buffer)."""
+    k = key + (ws.data_ptr(), ws.numel() * ws.element_size())
+    if k in _WS_CHECKED:
+        return
+    need = need_fn()
+    have = ws.numel() * ws.element_size()
+    if not ws.is_cuda or have < need:
+        raise HbacaError(7, "workspace of %d bytes; these arguments need %d" % (have, need))
+    if len(_WS_CHECKED) > 4096:
+        _WS_CHECKED.clear()
+    _WS_CHECKED[k] = True
+
+
+def _check_out(Ut, S, V, cap, m, n, dt):
+    """Caller-provided output buffers must hold cap x m, cap and cap x n."""
+    ok = (Ut.is_cuda and S.is_cuda and V.is_cuda and Ut.dtype == dt and V.dtype == dt and S.dtype == _torch().float64
+          and Ut.is_contiguous() and V.is_contiguous() and S.is_contiguous()
+          and Ut.numel() >= cap * m and S.numel() >= cap and V.numel() >= cap * n)
+    if not ok:
+        raise HbacaError(1, "output buffers must be contiguous device tensors of %d x %d, %d and %d x %d" % (cap, m, cap, cap, n))
+
+
+def _torch():
+    import torch
+    return torch
+
+
 def compress(ctx, spec, opts, stream=None, ws=None, out=None):
     """hbaca_compress on the current torch stream.  ``ws`` / ``out`` may be
     passed to reuse device buffers across calls."""
@@ -393,12 +426,15 @@ def compress(ctx, spec, opts, stream=None, ws=None, out=None):
     dt = torch.complex128 if spec.complex else torch.float64
     if ws is None:
         ws = torch.empty(workspace_size(spec.gen, opts), dtype=torch.uint8, device="cuda")
+    else:
+        _check_workspace(ws, lambda: workspace_size(spec.gen, opts), (bytes(spec.gen), bytes(opts)))
     if out is None:
         Ut = torch.empty((cap, m), dtype=dt, device="cuda")
         S = torch.empty(cap, dtype=torch.float64, device="cuda")
         V = torch.empty((cap, n), dtype=dt, device="cuda")
     else:
         Ut, S, V = out
+        _check_out(Ut, S, V, min(cap, m, n), m, n, dt)
     res = Result(U=Ut.data_ptr(), ldu=m, S=S.data_ptr(), V=V.data_ptr(), ldv=n)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
@@ -602,13 +638,13 @@ class Batch:
         if ws is None:
             # with an automatic leaf cluster size, room for every size the
             # autotuner may try (the plans differ by their scratch)
-            sizes = [0] + ([1, 2, 4, 8, 16] if opts.cluster == 0 else [])
+            sizes = [opts.cluster] + ([1, 2, 4, 8, 16] if opts.cluster == 0 else [])
             nbytes = 0
             for c in sizes:
                 o = Opts.from_buffer_copy(opts)
                 o.cluster = c
                 nb = lib().hbaca_workspace_size_batched(n, self.gens, ctypes.byref(o))
-                if nb == 0 and c == 0:
+                if nb == 0 and c == sizes[0]:
                     raise HbacaError(1, lib().hbaca_last_error().decode())
                 nbytes = max(nbytes, nb)
             ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -628,6 +664,9 @@ class Batch:
         import torch
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
+        n = len(self.specs)
+        _check_workspace(self.ws, lambda: lib().hbaca_workspace_size_batched(n, self.gens, ctypes.byref(self.opts)),
+                         (bytes(self.gens), bytes(self.opts)))
         check(lib().hbaca_compress_batched(self.ctx.ptr, len(self.specs), self.gens, ctypes.byref(self.opts),
                                            self.res, ctypes.c_void_p(self.ws.data_ptr()),
                                            ctypes.c_void_p(stream)))

@@ -122,6 +122,31 @@ def _same_results(a, b):
         assert torch.equal(ra.S, rb.S) and torch.equal(ra.U, rb.U) and torch.equal(ra.V, rb.V)
 
 
+def test_explicit_leaf_cluster_and_workspace_checks(ctx):
+    """A batch with a fixed leaf cluster size gets a workspace planned for
+    that size and the same factors as the automatic choice (the cluster size
+    never changes a result); a workspace or output buffer smaller than the
+    plan needs is refused before anything is launched."""
+    blocks = inputs.batched_blocks(seed=13, nblocks=12, lo=64, hi=600)
+    specs = _specs(blocks)
+    mk = lambda c: B.make_opts(1e-8, 8, -256, seed=0, rank_cap=256, leaf_rank_cap=256, cluster=c)
+    auto = B.Batch(ctx, specs, mk(0)).run()
+    for c in (1, 16):
+        one = B.Batch(ctx, specs, mk(c)).run()
+        torch.cuda.synchronize()
+        _same_results(auto, one)
+    small = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.HbacaError):
+        B.Batch(ctx, specs, mk(1), ws=small).run()
+    with pytest.raises(B.HbacaError):
+        B.compress(ctx, specs[0], mk(0), ws=small)
+    s0 = specs[0]
+    tiny = (torch.empty((1, s0.m), dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64, device="cuda"),
+            torch.empty((1, s0.n), dtype=torch.float64, device="cuda"))
+    with pytest.raises(B.HbacaError):
+        B.compress(ctx, s0, mk(0), out=tiny)
+
+
 def test_graph_replay_bit_identical_and_follows_new_data(ctx):
     """HBACA_FLAG_GRAPH: the first call runs and captures itself, later calls
     replay the graph; every replay equals a plain call bit for bit, also after
