@@ -91,6 +91,15 @@ int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster);
    launch shapes. */
 int32_t hbaca_debug_set_qr_cluster(int32_t cluster);
 
+/* Clusters of 16 CTAs per core (1 .. 32) for the one-sided Jacobi SVD of the
+   cores whose columns do not fit one cluster's shared memory, in every later
+   synchronous call in this process: 1 keeps one cluster per core, 0 restores
+   the automatic choice (several clusters sweep one such core through global
+   memory, with bounded waits; HBACA_TIMEOUT on expiry).  Returns the previous
+   setting.  Results do not depend on it (every rotation is formed and applied
+   with the same arithmetic whichever CTA runs it). */
+int32_t hbaca_debug_set_jacobi_groups(int32_t groups);
+
 /* Sweep cap of the one-sided Jacobi SVD (Sec. 2, SVD(A, eps)) used by every
    later call in this process: sweeps > 0 sets it, 0 restores the default
    (40).  Returns the cap in force before the call.  For tests that make a

@@ -127,6 +127,7 @@ SIGNATURES = [
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_jacobi_cluster", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_qr_cluster", ctypes.c_int32, [ctypes.c_int32]),
+    ("hbaca_debug_set_jacobi_groups", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
     ("hbaca_debug_launch_times", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_void_p, ctypes.c_int32]),
@@ -355,6 +356,13 @@ def rel_error(ctx, spec, comp, rows=None):
     """sqrt(error_norms ratio): ||A - U S V||_F / ||A||_F on the device."""
     e2, a2 = error_norms(ctx, spec, comp, rows)
     return (e2 / a2) ** 0.5 if a2 > 0 else 0.0
+
+
+def set_jacobi_groups(g):
+    """hbaca_debug_set_jacobi_groups: clusters per core for the Jacobi SVD of
+    cores too large for one cluster (0 = automatic, 1 = one); returns the
+    previous setting."""
+    return int(lib().hbaca_debug_set_jacobi_groups(int(g)))
 
 
 def set_qr_cluster(c):

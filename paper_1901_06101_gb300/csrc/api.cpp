@@ -83,6 +83,7 @@ constexpr int kDefaultJacobiSweeps = 40;
 std::atomic<int> g_jacobi_sweeps{kDefaultJacobiSweeps};
 std::atomic<int> g_jacobi_cluster{0};
 std::atomic<int> g_qr_cluster{0};
+std::atomic<int> g_jacobi_groups{0};
 
 }  // namespace
 
@@ -92,6 +93,7 @@ int ctx_device(const hbaca_ctx* ctx) { return ctx->device; }
 int jacobi_max_sweeps() { return g_jacobi_sweeps.load(std::memory_order_relaxed); }
 int jacobi_forced_cluster() { return g_jacobi_cluster.load(std::memory_order_relaxed); }
 int qr_forced_cluster() { return g_qr_cluster.load(std::memory_order_relaxed); }
+int jacobi_forced_groups() { return g_jacobi_groups.load(std::memory_order_relaxed); }
 }  // namespace hbaca
 
 extern "C" {
@@ -594,6 +596,11 @@ hbaca_status hbaca_kernel_times(hbaca_ctx* ctx, double ms[HBACA_KERNEL_CLASSES],
 int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster) {
   const int v = cluster >= 1 && cluster <= 16 ? cluster : 0;
   return g_jacobi_cluster.exchange(v);
+}
+
+int32_t hbaca_debug_set_jacobi_groups(int32_t groups) {
+  const int v = groups >= 1 && groups <= hbaca::kXSlots ? groups : 0;
+  return g_jacobi_groups.exchange(v);
 }
 
 int32_t hbaca_debug_set_qr_cluster(int32_t cluster) {

@@ -714,11 +714,25 @@ constexpr int kJSlotMax = 96;  // bytes reserved per pair slot (>= sizeof(JPair<
 // warps of the cluster; each CTA (1) forms the inner products of all its
 // pairs, (2) turns them into rotations, one thread per pair, (3) rotates its
 // pairs' columns; one cluster barrier ends the round.
+// A core too large for one cluster's shared memory may be swept by G
+// clusters at once (columns in global memory, a cooperative launch): the
+// pairs of a round are dealt over all G c CTAs, and a round ends with the
+// cluster barrier plus an arrival count on the task's counter (bounded wait,
+// HBACA_TIMEOUT on expiry); the per-sweep decisions are summed over the
+// clusters through global slots.  Every rotation is formed and applied with
+// the same arithmetic as with one cluster, so the result does not depend on G.
+struct JGroup {
+  int G;              // clusters per core (1: no grouping)
+  unsigned* cnt;      // arrival counter per core of the launch (zeroed before it)
+  double* slots;      // [cluster of the launch][2][4] per-sweep values
+};
+
 template <typename T, bool kDsm>
 __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int nc, int K, T* M, T* Y, int64_t ld,
                               T* dsm, int64_t ldc, double tol, double negl, double fro2, double& cmax, double eps,
                               int max_sweeps, int* flag, double* cmx, JPair<T>* slots, int& sweep, int& nrot,
-                              bool acc_w, T* const* ctab, int* c2bits, bool& converged, double* gnrm) {
+                              bool acc_w, T* const* ctab, int* c2bits, bool& converged, double* gnrm,
+                              int ql, int csz, const JGroup& jg, int tl, int g, int* xok, int* status) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   // column addresses from the table (no division by the cluster size per access)
   auto colX = [&](int j) -> T* { return ctab[j]; };
@@ -742,6 +756,20 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     if constexpr (kDsm) return *nrm(j);
     else return ldcg(gnrm + j);
   };
+  // the end of a round: every CTA of the cluster, and with G > 1 every
+  // cluster of the core (columns written by one cluster are read by others
+  // in the next round: each writer fences, the leader counts the cluster in)
+  unsigned nbar = 0;
+  auto group_barrier = [&]() -> bool {
+    if (jg.G > 1) __threadfence();
+    cl.sync();
+    if (jg.G == 1) return true;
+    ++nbar;
+    if (ql == 0 && threadIdx.x == 0) *xok = xgroup_arrive_wait(jg.cnt + tl, nbar * (unsigned)jg.G, status);
+    cl.sync();
+    return *cl.map_shared_rank(xok, 0) != 0;
+  };
+  bool ok = true;
   const int per = (nc + c - 1) / c;
   const int npairs = K / 2;
   const int stride = c * nw;                             // pairs dealt per pass over the cluster's warps
@@ -771,7 +799,7 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
       wmax = fmax(wmax, v);
     }
     __syncthreads();
-    cl.sync();
+    if (!group_barrier()) break;
     __syncthreads();
     for (int rd = 0; rd < K - 1; ++rd) {
       // (1) inner products of this warp's pairs; the first pass keeps its
@@ -916,8 +944,9 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
         }
         if (acc_w) rotate_pair_t<T, kDsm>(colW(a), colW(b), nc, cs, sn, spv, cpv, lane);
       }
-      cl.sync();
+      if (!(ok = group_barrier())) break;
     }
+    if (!ok) break;
     // the largest column norm^2 of this sweep, over the cluster (for the next tau)
     if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(cmx), (unsigned long long)__double_as_longlong(wmax));
     __syncthreads();
@@ -928,10 +957,28 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
     // none above tol (its only work would be the inner products): stop here
     int any = 0, c2b = 0;
     double cm = 0.0;
-    for (int r = 0; r < c; ++r) {
+    for (int r = 0; r < csz; ++r) {
       any |= *cl.map_shared_rank(&flag[fb & 1], r);
       cm = fmax(cm, *cl.map_shared_rank(cmx, r));
       c2b = max(c2b, *cl.map_shared_rank(&c2bits[fb & 1], r));
+    }
+    if (jg.G > 1) {  // over the clusters of the core, in cluster order
+      double* mine = jg.slots + ((size_t)(tl * jg.G + g) * 2 + (fb & 1)) * 4;
+      if (ql == 0 && threadIdx.x == 0) {
+        mine[0] = (double)any;
+        mine[1] = cm;
+        mine[2] = (double)__int_as_float(c2b);
+      }
+      if (!group_barrier()) break;
+      any = 0;
+      c2b = 0;
+      cm = 0.0;
+      for (int gg = 0; gg < jg.G; ++gg) {
+        const double* sl2 = jg.slots + ((size_t)(tl * jg.G + gg) * 2 + (fb & 1)) * 4;
+        any |= ldcg(sl2) != 0.0;
+        cm = fmax(cm, ldcg(sl2 + 1));
+        c2b = max(c2b, __float_as_int((float)ldcg(sl2 + 2)));
+      }
     }
     if (cm > 0.0) cmax = cm;
     ++fb;
@@ -944,11 +991,17 @@ __device__ void jacobi_sweeps(cg::cluster_group& cl, int q, int c, int mr, int n
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DenseParams<T> P, int max_sweeps,
                                                                    int hdr_bytes, int slot_off, int64_t dsm_bytes,
-                                                                   const int32_t* task_list) {
+                                                                   const int32_t* task_list, const JGroup jg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int xok;
   cg::cluster_group cl = cg::this_cluster();
-  const int q = (int)cl.block_rank(), c = (int)cl.num_blocks();
-  const int ti = task_list ? task_list[blockIdx.x / c] : (int)(blockIdx.x / c);
+  // ql / csz: rank in the cluster and cluster size; q / c: rank and number
+  // of CTAs over the jg.G clusters that sweep one core (the same with G = 1)
+  const int ql = (int)cl.block_rank(), csz = (int)cl.num_blocks();
+  const int cid = (int)(blockIdx.x / csz);
+  const int tl = cid / jg.G, g = cid - tl * jg.G;
+  const int q = g * csz + ql, c = jg.G * csz;
+  const int ti = task_list ? task_list[tl] : tl;
   const SvdTask t = P.tasks[ti];
   const TaskDims dm = P.dims[ti];
   // the sweeps orthogonalise the columns of X = R2^H (nc_M x p), accumulating W
@@ -980,7 +1033,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   const int per = (nc + c - 1) / c;
   const int64_t ldc = (int64_t)mr + 1 + (acc_w ? nc : 0);  // X, the squared norm, W
   T* dsm = reinterpret_cast<T*>(smem_raw + hdr_bytes);
-  const bool use_dsm = (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
+  const bool use_dsm = jg.G == 1 && (int64_t)per * ldc * (int64_t)sizeof(T) <= dsm_bytes;
   if (use_dsm) {  // own columns: X from global memory, W = I
     for (int l = warp; l < per; l += nw) {
       const int j = l * c + q;
@@ -1037,14 +1090,14 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   // until the epilogue): column j in CTA j mod c (DSMEM) or in global memory
   T** ctab = reinterpret_cast<T**>(sv);
   for (int j = tid; j < nc; j += blockDim.x)
-    ctab[j] = use_dsm ? cl.map_shared_rank(dsm, j % c) + (int64_t)(j / c) * ldc : M + (int64_t)j * ld;
+    ctab[j] = use_dsm ? cl.map_shared_rank(dsm, j % csz) + (int64_t)(j / csz) * ldc : M + (int64_t)j * ld;
   __syncthreads();
   if (use_dsm)
     jacobi_sweeps<T, true>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag, cmx,
-                           slots, sweep, nrot, acc_w, ctab, c2bits, converged, gnrm);
+                           slots, sweep, nrot, acc_w, ctab, c2bits, converged, gnrm, ql, csz, jg, tl, g, &xok, P.status);
   else
     jacobi_sweeps<T, false>(cl, q, c, mr, nc, K, M, Y, ld, dsm, ldc, tol, negl, fro2, cmax, P.eps, max_sweeps, flag,
-                            cmx, slots, sweep, nrot, acc_w, ctab, c2bits, converged, gnrm);
+                            cmx, slots, sweep, nrot, acc_w, ctab, c2bits, converged, gnrm, ql, csz, jg, tl, g, &xok, P.status);
   // the sweep cap was reached while relevant rotations were still being
   // applied: the singular values and the eps-rank come from an unconverged
   // SVD, which the call reports (the loop leaves through its convergence
@@ -1063,6 +1116,9 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
   }
   cl.sync();
   if (lane == 0 && nrot) atomicAdd(&P.dims[ti].rotations, nrot);
+  // the first cluster of the core finishes it (the others' columns are in
+  // global memory, fenced before their last arrival)
+  if (g != 0) return;
   // singular values and their order (CTA 0); then every CTA normalises a
   // share of the kept columns of M in place (X = M / sigma) and writes S
   int* ord = reinterpret_cast<int*>(sv + nc);
@@ -1107,7 +1163,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
     const int* ord0 = cl.map_shared_rank(ord, 0);
     const int s = *cl.map_shared_rank(sshare, 0);
     const BlockRef ob = P.out_blocks[t.out];
-    for (int tc = q * nw + warp; tc < s; tc += c * nw) {
+    for (int tc = ql * nw + warp; tc < s; tc += csz * nw) {
       const int j = ord0[tc];
       const double sg = sv0[j];
       const double inv = sg > 0.0 ? 1.0 / sg : 0.0;  // a zero singular value (taped outputs only)

@@ -281,7 +281,10 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   // a stage's Jacobi launches: the largest (by CTAs) on the call's stream, the
   // others concurrently on the auxiliary stream (fork after the task lists
   // are in place, join before the next kernel)
-  auto jacobi_group_launches = [&](const std::vector<JacobiLaunch>& ls) -> cudaError_t {
+  const JGroup jg1{1, nullptr, nullptr};
+  auto jacobi_group_launches = [&](const std::vector<JacobiLaunch>& all) -> cudaError_t {
+    std::vector<JacobiLaunch> ls, grouped;
+    for (const JacobiLaunch& jl : all) (jl.groups > 1 ? grouped : ls).push_back(jl);
     size_t main_i = 0;
     for (size_t i = 1; i < ls.size(); ++i)
       if ((int64_t)ls[i].count * ls[i].cluster > (int64_t)ls[main_i].count * ls[main_i].cluster) main_i = i;
@@ -297,12 +300,24 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       const int32_t* lst = reinterpret_cast<const int32_t*>(ws + p.jlist.off) + jl.list_off;
       if (rc.kt) HB_TRY(rc.kt->begin(KC_JACOBI, s2));
       HB_TRY(launch_cluster(jacobi_kernel<T>, jl.count * jl.cluster, jl.cluster, jl.hdr + jl.dsm, s2, D, jacobi_max_sweeps(), (int)jl.hdr,
-                            (int)jl.base, (int64_t)jl.dsm, lst));
+                            (int)jl.base, (int64_t)jl.dsm, lst, jg1));
       if (rc.kt) HB_TRY(rc.kt->end(s2));
     }
     if (fork) {
       HB_TRY(cudaEventRecord(rc.join_ev, rc.aux));
       HB_TRY(cudaStreamWaitEvent(rc.st, rc.join_ev, 0));
+    }
+    // cores swept by several clusters: a cooperative launch on the call's
+    // stream after the others (arrival counters zeroed first)
+    for (const JacobiLaunch& jl : grouped) {
+      const int32_t* lst = reinterpret_cast<const int32_t*>(ws + p.jlist.off) + jl.list_off;
+      const JGroup jg{jl.groups, X.xcnt, reinterpret_cast<double*>(X.xpart)};
+      ++rc.launches;
+      HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
+      if (rc.kt) HB_TRY(rc.kt->begin(KC_JACOBI, rc.st));
+      HB_TRY(launch_cluster_x(jacobi_kernel<T>, jl.count * jl.groups * jl.cluster, jl.cluster, jl.hdr, rc.st, true, D,
+                              jacobi_max_sweeps(), (int)jl.hdr, (int)jl.base, (int64_t)0, lst, jg));
+      if (rc.kt) HB_TRY(rc.kt->end(rc.st));
     }
     return cudaSuccess;
   };
@@ -357,13 +372,38 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     };
     int c_stage = 4;
     while (c_stage < 16 && (int64_t)nt * c_stage * 2 <= 3 * (int64_t)rc.sms) c_stage *= 2;
+    // cores whose columns do not fit 16 CTAs' shared memory and have at least
+    // 256 pairs a round: swept by several 16-CTA clusters at once
+    std::vector<int32_t> huge;
+    int huge_pairs = 0;
     for (int i = 0; i < nt; ++i) {
       const int ncm = th[i].kind == TASK_LEAF ? dh[i].krb : dh[i].k;
       const int pairs = (std::min(dh[i].kra, ncm) + 1) / 2;
       int c = c_stage;
       while (c > 1 && pairs < 4 * c) c /= 2;
       if (jacobi_forced_cluster() > 0) c = jacobi_forced_cluster();
-      add_task(i, fit(i, c));
+      c = fit(i, c);
+      if (rc.xgroups && jacobi_forced_groups() != 1 && c == 16 && pairs >= 256 &&
+          share_of(i, 16) + j_hdr_of(16) > kJacobiSmemLimit) {
+        huge.push_back(i);
+        huge_pairs = std::max(huge_pairs, pairs);
+      } else {
+        add_task(i, c);
+      }
+    }
+    int G = 1;
+    if (!huge.empty()) {
+      // every cluster of the cooperative launch resident, one arrival counter
+      // per core, about one pair per warp and round
+      const int nh = (int)huge.size();
+      const int res = resident_clusters(jacobi_kernel<T>, 16, j_hdr_of(16), rc.st);
+      const int cap = std::min(res / nh, kXSlots / nh);
+      G = std::min(cap, (huge_pairs + 16 * 8 - 1) / (16 * 8));
+      if (jacobi_forced_groups() > 1) G = std::min(cap, jacobi_forced_groups());
+      if (G < 2) {
+        for (int i : huge) add_task(i, 16);
+        huge.clear();
+      }
     }
     size_t off = sg.jlist_off;
     std::vector<JacobiLaunch> ls;
@@ -373,6 +413,12 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
       HB_TRY(cudaMemcpyAsync(lst, groups[g].data(), groups[g].size() * 4, cudaMemcpyHostToDevice, rc.st));
       ls.push_back(JacobiLaunch{si, g, (int)groups[g].size(), j_hdr_of(g), j_base, need[g], off});
       off += groups[g].size();
+    }
+    if (!huge.empty()) {
+      int32_t* lst = reinterpret_cast<int32_t*>(ws + p.jlist.off) + off;
+      HB_TRY(cudaMemcpyAsync(lst, huge.data(), huge.size() * 4, cudaMemcpyHostToDevice, rc.st));
+      ls.push_back(JacobiLaunch{si, 16, (int)huge.size(), j_hdr_of(16), j_base, 0, off, G});
+      off += huge.size();
     }
     HB_TRY(jacobi_group_launches(ls));
     if (rc.record) rc.record->insert(rc.record->end(), ls.begin(), ls.end());
@@ -386,7 +432,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     const size_t j_cap = ((size_t)sg.kcap + cj - 1) / cj * (2 * (size_t)sg.kcap + 1) * sizeof(T);
     const size_t j_dsm = std::min(j_cap, (size_t)kJacobiSmemLimit - j_hdr);
     HB_TIMED(KC_JACOBI, HB_TRY(launch_cluster(jacobi_kernel<T>, nt * cj, cj, j_hdr + j_dsm, rc.st, D, jacobi_max_sweeps(), (int)j_hdr,
-                                              (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr)));
+                                              (int)j_base, (int64_t)j_dsm, (const int32_t*)nullptr, jg1)));
     ++rc.launches;
   }
   if (!p.tape) {

@@ -51,6 +51,7 @@ struct KernelTimer {
 struct JacobiLaunch {
   int stage, cluster, count;
   size_t hdr, base, dsm, list_off;
+  int groups = 1;  // clusters per core (> 1: a cooperative launch, columns in global memory)
 };
 
 struct RunCtx {
@@ -85,4 +86,8 @@ int jacobi_forced_cluster();
 // CTAs per matrix of the QR and Q-application launches forced by
 // hbaca_debug_set_qr_cluster (0: the per-stage choice).
 int qr_forced_cluster();
+// Clusters per core of the Jacobi SVD of cores too large for one cluster's
+// shared memory, forced by hbaca_debug_set_jacobi_groups (0: the per-stage
+// choice; 1: never more than one).
+int jacobi_forced_groups();
 }  // namespace hbaca

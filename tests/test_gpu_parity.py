@@ -276,6 +276,36 @@ def test_product_of_random_exact_rank(ctx, cplx):
     assert err < 1e-12
 
 
+def test_grouped_jacobi_for_large_cores(ctx):
+    """Merge cores of 640 columns (complex) do not fit one cluster's shared
+    memory: their Jacobi SVD is swept by several 16-CTA clusters at once.  The
+    factors equal those of one cluster per core bit for bit, for automatic and
+    forced numbers of clusters, and keep the exact rank and the rounding
+    error of a product of random factors."""
+    LU, LV = inputs.lowrank(17, 1600, 1600, 320, complex_=True)
+    spec = B.lowrank(LU, LV)
+    opts = B.make_opts(1e-10, 32, 1, seed=5, rank_cap=1024, leaf_rank_cap=512)
+    outs = {}
+    prev = B.set_jacobi_groups(1)
+    try:
+        for gsel in (1, 0, 2, 3):
+            B.set_jacobi_groups(gsel)
+            r = B.compress(ctx, spec, opts)
+            torch.cuda.synchronize()
+            outs[gsel] = (r.rank, r.U.clone(), r.S.clone(), r.V.clone())
+    finally:
+        B.set_jacobi_groups(prev)
+    ref = outs[1]
+    assert ref[0] == 320
+    for gsel in (0, 2, 3):
+        got = outs[gsel]
+        assert got[0] == ref[0] and torch.equal(got[2], ref[2]) and torch.equal(got[1], ref[1]) \
+            and torch.equal(got[3], ref[3]), gsel
+    A = LU @ LV
+    err = dense_rel_error(A, ref[1].cpu().numpy(), ref[2].cpu().numpy(), ref[3].cpu().numpy())
+    assert err < 1e-12
+
+
 def _pivot_sets(tr):
     return [(tuple(t["I"]), tuple(t["J"])) for leaf in sorted(tr) for t in tr[leaf]["trace"]]
 
