@@ -255,7 +255,8 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
               reinterpret_cast<unsigned*>(ws + p.xcnt.off)};
   if (rc.xgroups && qr_forced_cluster() == 0 && cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
     const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
-                             resident_clusters(qapply_kernel<T>, 8, qa_smem, rc.st));
+                             std::min(resident_clusters(qapply_kernel<T, false>, 8, qa_smem, rc.st),
+                                      resident_clusters(qapply_kernel<T, true>, 8, qa_smem, rc.st)));
     const int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
     if (G > 1) {
       cq = 8;
@@ -455,7 +456,14 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   ++rc.launches;
   X.njobs = sg.nq;
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
-  HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
+  {
+    // the instance that keeps the reflectors in registers when a CTA's rows fit
+    const int64_t rows_cta = ((int64_t)sg.rows_max + (int64_t)X.G * cq - 1) / ((int64_t)X.G * cq);
+    if (rows_cta <= 32 * kQaRegs<T>)
+      HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T, true>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
+    else
+      HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T, false>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
+  }
   rc.launches += 5;  // pack, QR, core, pivoted QR of the core, Q application
   if (sg.kind != TASK_LEAF) {
     // element-parallel; a stage with few (large) tasks spreads each over more CTAs
