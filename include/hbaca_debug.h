@@ -91,6 +91,14 @@ int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster);
    launch shapes. */
 int32_t hbaca_debug_set_qr_cluster(int32_t cluster);
 
+/* Upper bound (1 .. 32) on the number of 8-CTA clusters that the QR and the Q
+   application of a stage with few matrices spread one matrix over, in every
+   later synchronous call in this process (fewer than 3: one 16-CTA cluster
+   per matrix); 0 restores the automatic choice.  Returns the previous
+   setting.  Partial sums are combined in cluster order, so results depend on
+   it at the rounding level; it exists to time the launch shapes. */
+int32_t hbaca_debug_set_qr_groups(int32_t groups);
+
 /* Clusters of 16 CTAs per core (1 .. 32) for the one-sided Jacobi SVD of the
    cores whose columns do not fit one cluster's shared memory, in every later
    synchronous call in this process: 1 keeps one cluster per core, 0 restores

@@ -128,6 +128,7 @@ SIGNATURES = [
     ("hbaca_debug_set_jacobi_cluster", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_qr_cluster", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_jacobi_groups", ctypes.c_int32, [ctypes.c_int32]),
+    ("hbaca_debug_set_qr_groups", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_error_workspace_size", ctypes.c_size_t, [ctypes.c_int64]),
     ("hbaca_debug_launch_times", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_void_p, ctypes.c_int32]),
@@ -363,6 +364,13 @@ def set_jacobi_groups(g):
     cores too large for one cluster (0 = automatic, 1 = one); returns the
     previous setting."""
     return int(lib().hbaca_debug_set_jacobi_groups(int(g)))
+
+
+def set_qr_groups(g):
+    """hbaca_debug_set_qr_groups: upper bound on the clusters per matrix of
+    the QR / Q application of stages with few matrices (0 = automatic);
+    returns the previous setting."""
+    return int(lib().hbaca_debug_set_qr_groups(int(g)))
 
 
 def set_qr_cluster(c):

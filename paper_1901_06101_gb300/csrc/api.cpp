@@ -84,6 +84,7 @@ std::atomic<int> g_jacobi_sweeps{kDefaultJacobiSweeps};
 std::atomic<int> g_jacobi_cluster{0};
 std::atomic<int> g_qr_cluster{0};
 std::atomic<int> g_jacobi_groups{0};
+std::atomic<int> g_qr_groups{0};
 
 }  // namespace
 
@@ -94,6 +95,7 @@ int jacobi_max_sweeps() { return g_jacobi_sweeps.load(std::memory_order_relaxed)
 int jacobi_forced_cluster() { return g_jacobi_cluster.load(std::memory_order_relaxed); }
 int qr_forced_cluster() { return g_qr_cluster.load(std::memory_order_relaxed); }
 int jacobi_forced_groups() { return g_jacobi_groups.load(std::memory_order_relaxed); }
+int qr_forced_groups() { return g_qr_groups.load(std::memory_order_relaxed); }
 }  // namespace hbaca
 
 extern "C" {
@@ -601,6 +603,11 @@ int32_t hbaca_debug_set_jacobi_cluster(int32_t cluster) {
 int32_t hbaca_debug_set_jacobi_groups(int32_t groups) {
   const int v = groups >= 1 && groups <= hbaca::kXSlots ? groups : 0;
   return g_jacobi_groups.exchange(v);
+}
+
+int32_t hbaca_debug_set_qr_groups(int32_t groups) {
+  const int v = groups >= 1 && groups <= hbaca::kXSlots ? groups : 0;
+  return g_qr_groups.exchange(v);
 }
 
 int32_t hbaca_debug_set_qr_cluster(int32_t cluster) {

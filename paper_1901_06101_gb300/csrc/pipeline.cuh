@@ -123,11 +123,15 @@ inline int pick_qr_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
 }
 
 // Clusters per matrix when a stage has too few matrices to fill the machine
-// with one 16-CTA cluster each: 8-CTA clusters, as many per matrix as the
-// SMs (and the exchange slots) allow; 1 when that is not more than 16 CTAs.
+// with one 16-CTA cluster each: 8-CTA clusters, as many per matrix as two
+// CTAs per SM, the resident clusters and the exchange slots allow; 1 when
+// that is not more than 16 CTAs.  (The column steps of such a stage are bound
+// by each CTA's own FP64 work: on the 50000-row root of the sparse-product
+// workload QR + Q application took 3394 / 1932 / 1405 / 974 ms with 4 / 8 /
+// 12 / 19 clusters.)
 inline int pick_groups(int jobs, int rows, int sms, int resident, int min_rows_per_cta) {
   int G = 1;
-  while (jobs * (G + 1) <= kXSlots && jobs * (G + 1) * 8 <= sms && jobs * (G + 1) <= resident &&
+  while (jobs * (G + 1) <= kXSlots && jobs * (G + 1) * 8 <= 2 * sms && jobs * (G + 1) <= resident &&
          rows / ((G + 1) * 8) >= min_rows_per_cta)
     ++G;
   return G * 8 > 16 ? G : 1;
@@ -257,7 +261,8 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
                              std::min(resident_clusters(qapply_kernel<T, false>, 8, qa_smem, rc.st),
                                       resident_clusters(qapply_kernel<T, true>, 8, qa_smem, rc.st)));
-    const int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
+    int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
+    if (qr_forced_groups() > 0 && G > qr_forced_groups()) G = qr_forced_groups() * 8 > 16 ? qr_forced_groups() : 1;
     if (G > 1) {
       cq = 8;
       X.G = G;

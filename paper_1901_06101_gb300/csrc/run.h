@@ -90,4 +90,8 @@ int qr_forced_cluster();
 // shared memory, forced by hbaca_debug_set_jacobi_groups (0: the per-stage
 // choice; 1: never more than one).
 int jacobi_forced_groups();
+// Largest number of 8-CTA clusters per matrix of the QR and Q application of
+// stages with few matrices, forced by hbaca_debug_set_qr_groups (0: the
+// per-stage choice).
+int qr_forced_groups();
 }  // namespace hbaca

@@ -98,7 +98,7 @@ struct TaskDims {
 
 // Cluster slots of the inter-cluster partial-sum exchange of one QR or
 // Q-application launch (matrices x clusters per matrix).
-constexpr int kXSlots = 32;
+constexpr int kXSlots = 64;
 
 struct QrJob {
   int32_t task;
