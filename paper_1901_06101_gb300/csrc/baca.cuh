@@ -529,6 +529,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// panel columns (C_k) or rows (R_k) one thread forms together
+constexpr int kPanel = 4;
+
 template <typename Gen>
 __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParams<Gen> P) {
   using T = typename Gen::scalar;
@@ -579,16 +582,37 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
     for (; it < itmax; ++it) {
       if (dJ == 0) { stop = STOP_NO_COLS; break; }
       // ---- C_k = A(:, J_k) - U V(:, J_k)   (line 3)
-      for (int e = tid; e < mr * dJ; e += blockDim.x) {
-        const int il = e % mr, j = e / mr, i = ra + il, jc = S.sJ[j];
-        T acc = Traits<T>::zero();
-        const T* up = U + i;
-        const T* vp = V + jc;
-#pragma unroll 4
-        for (int p = 0; p < r; ++p) acc = mac(acc, up[(size_t)p * m], ldcg(vp + (size_t)p * n));
-        T val = sub(gen(Lf.row0 + i, Lf.col0 + jc), acc);
-        S.work[(size_t)j * mr + il] = val;
-        Cg[(size_t)j * m + i] = val;
+      // a thread takes one row and kPanel columns of the panel, so each entry
+      // of U is loaded once per kPanel columns (the sums run over p in the
+      // same order as for one column)
+      {
+        const int ngrp = (dJ + kPanel - 1) / kPanel;
+        for (int e = tid; e < mr * ngrp; e += blockDim.x) {
+          const int il = e % mr, j0 = (e / mr) * kPanel, i = ra + il;
+          const int nj = min(kPanel, dJ - j0);
+          T acc[kPanel];
+          const T* vp[kPanel];
+#pragma unroll
+          for (int u = 0; u < kPanel; ++u) {
+            acc[u] = Traits<T>::zero();
+            vp[u] = V + S.sJ[j0 + (u < nj ? u : 0)];
+          }
+          const T* up = U + i;
+          for (int p = 0; p < r; ++p) {
+            const T uv = up[(size_t)p * m];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u)
+              if (u < nj) acc[u] = mac(acc[u], uv, ldcg(vp[u] + (size_t)p * n));
+          }
+#pragma unroll
+          for (int u = 0; u < kPanel; ++u) {
+            if (u >= nj) continue;
+            const int j = j0 + u, jc = S.sJ[j];
+            const T val = sub(gen(Lf.row0 + i, Lf.col0 + jc), acc[u]);
+            S.work[(size_t)j * mr + il] = val;
+            Cg[(size_t)j * m + i] = val;
+          }
+        }
       }
       for (int i = tid; i < mr; i += blockDim.x) S.cand[i] = !S.kept_row[i];
       __syncthreads();
@@ -603,16 +627,36 @@ __global__ void __launch_bounds__(kBacaThreads) baca_leaf_kernel(const BacaParam
         __syncthreads();
       }
       // ---- R_k = A(I_k, :) - U(I_k, :) V   (line 5)
-      for (int e = tid; e < nc * dI; e += blockDim.x) {
-        const int jl = e % nc, s = e / nc, j = ca + jl, i = S.sI[s];
-        T acc = Traits<T>::zero();
-        const T* up = U + i;
-        const T* vp = V + j;
-#pragma unroll 4
-        for (int p = 0; p < r; ++p) acc = mac(acc, ldcg(up + (size_t)p * m), vp[(size_t)p * n]);
-        T val = sub(gen(Lf.row0 + i, Lf.col0 + j), acc);
-        S.work[(size_t)s * nc + jl] = val;
-        Rg[(size_t)s * n + j] = val;
+      // a thread takes one column and kPanel rows of the panel (each entry of
+      // V loaded once per kPanel rows; the same order of the sums)
+      {
+        const int ngrp = (dI + kPanel - 1) / kPanel;
+        for (int e = tid; e < nc * ngrp; e += blockDim.x) {
+          const int jl = e % nc, s0 = (e / nc) * kPanel, j = ca + jl;
+          const int ns = min(kPanel, dI - s0);
+          T acc[kPanel];
+          const T* up[kPanel];
+#pragma unroll
+          for (int u = 0; u < kPanel; ++u) {
+            acc[u] = Traits<T>::zero();
+            up[u] = U + S.sI[s0 + (u < ns ? u : 0)];
+          }
+          const T* vp = V + j;
+          for (int p = 0; p < r; ++p) {
+            const T vv = vp[(size_t)p * n];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u)
+              if (u < ns) acc[u] = mac(acc[u], ldcg(up[u] + (size_t)p * m), vv);
+          }
+#pragma unroll
+          for (int u = 0; u < kPanel; ++u) {
+            if (u >= ns) continue;
+            const int s = s0 + u, i = S.sI[s];
+            const T val = sub(gen(Lf.row0 + i, Lf.col0 + j), acc[u]);
+            S.work[(size_t)s * nc + jl] = val;
+            Rg[(size_t)s * n + j] = val;
+          }
+        }
       }
       for (int jl = tid; jl < nc; jl += blockDim.x) {
         bool ex = S.kept_col[jl];
