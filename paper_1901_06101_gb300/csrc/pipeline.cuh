@@ -460,6 +460,14 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   }
   ++rc.launches;
   X.njobs = sg.nq;
+  // the block-diagonal side of a merge needs only the core's right (or left)
+  // vectors, not the Q application: it runs on the auxiliary stream beside it
+  // (fork after finish, join at the end of the stage)
+  const bool side = sg.kind != TASK_LEAF && rc.aux && rc.fork_ev && rc.join_ev;
+  if (side) {
+    HB_TRY(cudaEventRecord(rc.fork_ev, rc.st));
+    HB_TRY(cudaStreamWaitEvent(rc.aux, rc.fork_ev, 0));
+  }
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
   {
     // the instance that keeps the reflectors in registers when a CTA's rows fit
@@ -473,8 +481,16 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   if (sg.kind != TASK_LEAF) {
     // element-parallel; a stage with few (large) tasks spreads each over more CTAs
     const int gx = std::max(64, std::min(1024, 8 * rc.sms / std::max(nt, 1)));
-    HB_TIMED(KC_BLOCKPROD, blockprod_kernel<T><<<dim3(gx, nt), 256, 0, rc.st>>>(D); HB_TRY(cudaGetLastError()));
+    cudaStream_t s2 = side ? rc.aux : rc.st;
+    if (rc.kt) HB_TRY(rc.kt->begin(KC_BLOCKPROD, s2));
+    blockprod_kernel<T><<<dim3(gx, nt), 256, 0, s2>>>(D);
+    HB_TRY(cudaGetLastError());
+    if (rc.kt) HB_TRY(rc.kt->end(s2));
     ++rc.launches;
+    if (side) {
+      HB_TRY(cudaEventRecord(rc.join_ev, rc.aux));
+      HB_TRY(cudaStreamWaitEvent(rc.st, rc.join_ev, 0));
+    }
   }
   return cudaSuccess;
 }
