@@ -51,11 +51,6 @@ int32_t hbaca_debug_launch_times(hbaca_ctx* ctx, int32_t* cls, int32_t* stage, d
    len).  Returns the length the full text needs. */
 size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char* buf, size_t len);
 
-/* FP64 throughput probe on the current device: a DFMA loop and an FP64 MMA
-   (mma.sync m8n8k4) loop over all SMs; results in TFLOP/s.  Used by the
-   benchmark to report the unit rates beside the derived FP64 peak. */
-hbaca_status hbaca_debug_fp64_probe(double* dfma_tflops, double* dmma_tflops);
-
 /* Layout of the reverse pass for a taped forward (gen, opts, workspace) with
    nrhs right-hand sides, as JSON in buf (NUL-terminated, truncated to len):
    per leaf the byte offsets, in the backward workspace, of the BACA factor

@@ -123,7 +123,6 @@ SIGNATURES = [
                                                 ctypes.c_size_t]),
     ("hbaca_phase_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]),
-    ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("hbaca_debug_set_jacobi_sweeps", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_jacobi_cluster", ctypes.c_int32, [ctypes.c_int32]),
     ("hbaca_debug_set_qr_cluster", ctypes.c_int32, [ctypes.c_int32]),
@@ -870,7 +869,30 @@ def phase_times(ctx):
     return tuple(ms), n.value
 
 
+PROBE_PATH = os.path.join(HERE, "libhbaca_probe.so")
+PROBE_SIGNATURES = [
+    ("hbaca_debug_fp64_probe", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+]
+_PROBE = None
+
+
+def probe_lib():
+    """Load libhbaca_probe.so, the FP64 unit-rate probe the benchmark reports."""
+    global _PROBE
+    if _PROBE is None:
+        if not os.path.exists(PROBE_PATH):
+            raise RuntimeError("libhbaca_probe.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(PROBE_PATH)
+        for name, res, args in PROBE_SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _PROBE = L
+    return _PROBE
+
+
 def fp64_probe():
+    """(DFMA, DMMA) TFLOP/s measured on the current device."""
     a, b = ctypes.c_double(), ctypes.c_double()
-    check(lib().hbaca_debug_fp64_probe(ctypes.byref(a), ctypes.byref(b)))
+    check(probe_lib().hbaca_debug_fp64_probe(ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value

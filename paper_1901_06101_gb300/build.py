@@ -1,7 +1,8 @@
 """Build libhbaca.so in-tree for sm_103a (GB300).
 
 Each translation unit is compiled by its own nvcc process (in parallel),
-then the objects are linked into ``paper_1901_06101_gb300/libhbaca.so``.
+then the objects are linked into ``paper_1901_06101_gb300/libhbaca.so``; the
+FP64 unit-rate probe the benchmark reports goes to ``libhbaca_probe.so``.
 Usage: ``python -m paper_1901_06101_gb300.build`` (or ``build()``).
 """
 import os
@@ -14,7 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhbaca.so")
-SOURCES = ["hbaca_f64.cu", "hbaca_c128.cu", "plan.cpp", "api.cpp", "probe.cu", "noalloc.cu", "adjoint.cu", "errnorm.cu", "hmatrix.cpp"]
+LIB_PROBE = os.path.join(HERE, "libhbaca_probe.so")
+SOURCES = ["hbaca_f64.cu", "hbaca_c128.cu", "plan.cpp", "api.cpp", "noalloc.cu", "adjoint.cu", "errnorm.cu", "hmatrix.cpp"]
+PROBE_SOURCES = ["probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,16 +42,17 @@ def _compile(src, verbose_ptxas=False):
 
 def build(verbose_ptxas=False, quiet=False):
     os.makedirs(OBJ, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
-    objs = [o for o, _ in results]
+    allsrc = SOURCES + PROBE_SOURCES
+    with ThreadPoolExecutor(max_workers=len(allsrc)) as ex:
+        results = dict(zip(allsrc, ex.map(lambda s: _compile(s, verbose_ptxas), allsrc)))
     if verbose_ptxas and not quiet:
-        for _, log in results:
+        for _, log in results.values():
             sys.stderr.write(log)
-    cmd = [_nvcc(), "-shared", "-o", LIB] + objs + ARCH
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+    for lib_path, srcs in ((LIB, SOURCES), (LIB_PROBE, PROBE_SOURCES)):
+        cmd = [_nvcc(), "-shared", "-o", lib_path] + [results[s][0] for s in srcs] + ARCH
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     return LIB
 
 

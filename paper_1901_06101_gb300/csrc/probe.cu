@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "hbaca.h"
-#include "hbaca_debug.h"
+#include "hbaca_probe.h"
 
 namespace {
 

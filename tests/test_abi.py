@@ -13,9 +13,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include"))) if f.endswith(".h")]
 
 
-def declared_functions():
+def declared_functions(probe=False):
+    """Functions the headers declare: those of libhbaca.so, or (probe) of
+    libhbaca_probe.so (include/hbaca_probe.h)."""
     names = []
     for h in HEADERS:
+        if (os.path.basename(h) == "hbaca_probe.h") != probe:
+            continue
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(hbaca_[a-z0-9_]+)\s*\(", src, flags=re.M)
@@ -36,6 +40,18 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
     bound = {s[0] for s in B.SIGNATURES}
     assert set(names) <= bound, set(names) - bound
+
+
+def test_probe_library_exports_its_header():
+    if not os.path.exists(B.PROBE_PATH):
+        pytest.skip("libhbaca_probe.so not built")
+    names = declared_functions(probe=True)
+    assert names == ["hbaca_debug_fp64_probe"]
+    L = B.probe_lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert {s[0] for s in B.PROBE_SIGNATURES} == set(names)
+    assert not hasattr(B.lib(), "hbaca_debug_fp64_probe")  # not in the compression library
 
 
 def test_version_and_last_error(lib):
