@@ -1340,12 +1340,7 @@ __global__ void finish_kernel(const DenseParams<T> P) {
 // from the last to the first; each needs w = u^H D (cluster-wide partial sums
 // combined through DSMEM) and a rank-1 update of this CTA's rows.
 
-// rows of a CTA per lane whose reflector entries the Q application keeps in
-// registers (the kRegs instance, launched when a CTA's rows fit)
-template <typename T> constexpr int kQaRegs = 16;
-template <> constexpr int kQaRegs<cplx> = 8;
-
-template <typename T, bool kRegs>
+template <typename T>
 __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams<T> P, const QJob* jobs, const XGroup<T> X) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int xok;
@@ -1398,42 +1393,14 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
     const int i0 = max(ra, pair ? jm : j);
     const T* uj = A + (int64_t)j * lda;
     const T* ujm = A + (int64_t)(pair ? jm : j) * lda;
-    // when this CTA's rows are few (the top merges, whose columns stream from
-    // DRAM), every lane keeps the two reflectors' entries of its rows in
-    // registers and a warp takes whole columns of D: all of a column's loads
-    // are independent and in flight together (the same sums in the same order
-    // as the row loop below)
-    const int nrows = rb - i0;
-    const bool in_regs = kRegs && nrows <= 32 * kQaRegs<T>;  // block-uniform
-    T rj[kQaRegs<T>], rm[kQaRegs<T>];
-    if (in_regs) {
-#pragma unroll
-      for (int k = 0; k < kQaRegs<T>; ++k) {
-        const int i = i0 + lane + 32 * k;
-        rj[k] = i < rb ? (i < j ? zero : (i == j ? one : uj[i])) : zero;
-        rm[k] = (i < rb && pair) ? (i == jm ? one : ujm[i]) : zero;
-      }
-    }
     for (int tc = warp; tc < s; tc += nw) {
       const T* d = D + (int64_t)tc * ldd;
       T a0 = zero, a1 = zero;
-      if (in_regs) {
-#pragma unroll
-        for (int k = 0; k < kQaRegs<T>; ++k) {
-          const int i = i0 + lane + 32 * k;
-          if (32 * k < nrows && i < rb) {
-            const T x = d[i];
-            a0 = cmac(a0, rj[k], x);
-            a1 = cmac(a1, rm[k], x);
-          }
-        }
-      } else {
-        for (int i = i0 + lane; i < rb; i += 32) {
-          const T x = d[i];
-          const T vj = i < j ? zero : (i == j ? one : uj[i]);
-          a0 = cmac(a0, vj, x);
-          if (pair) a1 = cmac(a1, i == jm ? one : ujm[i], x);
-        }
+      for (int i = i0 + lane; i < rb; i += 32) {
+        const T x = d[i];
+        const T vj = i < j ? zero : (i == j ? one : uj[i]);
+        a0 = cmac(a0, vj, x);
+        if (pair) a1 = cmac(a1, i == jm ? one : ujm[i], x);
       }
       int col, comp;
       bool first;
@@ -1478,22 +1445,10 @@ __global__ void __launch_bounds__(kDenseThreads) qapply_kernel(const DenseParams
       tot[s + tc] = pair ? mul(tjm, msub(tot[s + tc], gam, w)) : zero;
     }
     __syncthreads();
-    // D(i, tc) -= u_j(i) w_tc + u_{j-1}(i) w'_tc: a warp per column with the
-    // reflectors in registers (few rows), else one thread per row, four
-    // columns per step
+    // D(i, tc) -= u_j(i) w_tc + u_{j-1}(i) w'_tc: one thread per row, four columns per step
     const T* wa = tot;
     const T* wb = tot + s;
-    if (in_regs) {
-      for (int tc = warp; tc < s; tc += nw) {
-        T* d = D + (int64_t)tc * ldd;
-        const T a = wa[tc], b = wb[tc];
-#pragma unroll
-        for (int k = 0; k < kQaRegs<T>; ++k) {
-          const int i = i0 + lane + 32 * k;
-          if (32 * k < nrows && i < rb) d[i] = msub(msub(d[i], rj[k], a), rm[k], b);
-        }
-      }
-    } else for (int i = i0 + tid; i < rb; i += blockDim.x) {
+    for (int i = i0 + tid; i < rb; i += blockDim.x) {
       const T vj = i < j ? zero : (i == j ? one : uj[i]);
       const T vm = !pair ? zero : (i == jm ? one : ujm[i]);
       int tc = 0;

@@ -127,8 +127,8 @@ inline int pick_qr_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
 // CTAs per SM, the resident clusters and the exchange slots allow; 1 when
 // that is not more than 16 CTAs.  (The column steps of such a stage are bound
 // by each CTA's own FP64 work: on the 50000-row root of the sparse-product
-// workload QR + Q application took 3394 / 1932 / 1405 / 974 ms with 4 / 8 /
-// 12 / 19 clusters.)
+// workload QR + Q application took 3394 / 1932 / 1405 / 974 / 625 ms with 4 /
+// 8 / 12 / 19 / 37 clusters.)
 inline int pick_groups(int jobs, int rows, int sms, int resident, int min_rows_per_cta) {
   int G = 1;
   while (jobs * (G + 1) <= kXSlots && jobs * (G + 1) * 8 <= 2 * sms && jobs * (G + 1) <= resident &&
@@ -259,8 +259,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
               reinterpret_cast<unsigned*>(ws + p.xcnt.off)};
   if (rc.xgroups && qr_forced_cluster() == 0 && cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
     const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
-                             std::min(resident_clusters(qapply_kernel<T, false>, 8, qa_smem, rc.st),
-                                      resident_clusters(qapply_kernel<T, true>, 8, qa_smem, rc.st)));
+                             resident_clusters(qapply_kernel<T>, 8, qa_smem, rc.st));
     int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
     if (qr_forced_groups() > 0 && G > qr_forced_groups()) G = qr_forced_groups() * 8 > 16 ? qr_forced_groups() : 1;
     if (G > 1) {
@@ -469,14 +468,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
     HB_TRY(cudaStreamWaitEvent(rc.aux, rc.fork_ev, 0));
   }
   if (coop) HB_TRY(cudaMemsetAsync(X.xcnt, 0, kXSlots * sizeof(unsigned), rc.st));
-  {
-    // the instance that keeps the reflectors in registers when a CTA's rows fit
-    const int64_t rows_cta = ((int64_t)sg.rows_max + (int64_t)X.G * cq - 1) / ((int64_t)X.G * cq);
-    if (rows_cta <= 32 * kQaRegs<T>)
-      HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T, true>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
-    else
-      HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T, false>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
-  }
+  HB_TIMED(KC_QAPPLY, HB_TRY(launch_cluster_x(qapply_kernel<T>, sg.nq * X.G * cq, cq, qa_smem, rc.st, coop, D, aj, X)));
   rc.launches += 5;  // pack, QR, core, pivoted QR of the core, Q application
   if (sg.kind != TASK_LEAF) {
     // element-parallel; a stage with few (large) tasks spreads each over more CTAs
