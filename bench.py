@@ -201,16 +201,37 @@ def leaf_accounting(traces, leaf_sizes, d, complex_):
 
 
 def task_dims(ws, plan):
-    """Per stage: (kind, device-written task sizes (ntasks x 8 ints), rows of
-    the stacked QR operand per task)."""
+    """Per stage: (kind, device-written task sizes (ntasks x 8 ints: k, kra,
+    krb, s, sweeps, nout, rotations, pad), rows of the stacked QR operand per
+    task, and rows of the second QR operand (leaf tasks; 0 for merges))."""
     import torch
     out = []
     for st in plan["stages"]:
         nt = st["ntasks"]
         d = ws[st["dims"]: st["dims"] + 32 * nt].view(torch.int32).view(nt, 8).cpu().numpy()
         rows = np.array([t["rows_a"] for t in st["tasks"]], np.int64)
-        out.append((st["kind"], d, rows))
+        rows_b = np.array([t["rows_b"] if st["kind"] == 0 else 0 for t in st["tasks"]], np.int64)
+        out.append((st["kind"], d, rows, rows_b))
     return out
+
+
+def qr_flops(m, k):
+    """Householder QR of an m x k matrix (LAPACK geqrf count): the reflector of
+    column j (m - j rows) applied to the k - j - 1 columns after it, two
+    flops per entry for the inner products and two for the update."""
+    m = np.asarray(m, np.float64)
+    k = np.minimum(np.asarray(k, np.float64), m)
+    return 2.0 * m * k ** 2 - 2.0 * k ** 3 / 3.0
+
+
+def qapply_flops(m, k, s):
+    """Q [Z; 0] for the Q of k Householder reflectors of m rows applied to s
+    columns (LAPACK ormqr count): reflector j touches m - j rows of every
+    column, two flops per entry for the inner product and two for the update."""
+    m = np.asarray(m, np.float64)
+    k = np.asarray(k, np.float64)
+    s = np.asarray(s, np.float64)
+    return 4.0 * m * k * s - 2.0 * k ** 2 * s
 
 
 def jacobi_flops_8d(dims, complex_):
@@ -219,7 +240,7 @@ def jacobi_flops_8d(dims, complex_):
     columns) and 20 (2 s)^3 per merge core (2 s = r1 + r2 stacked columns),
     four times that for complex data."""
     tot = 0.0
-    for kind, d, _ in dims:
+    for kind, d, _, _ in dims:
         ncm = d[:, 2] if kind == 0 else d[:, 0]
         nc = np.minimum(d[:, 1], ncm).astype(np.float64)
         tot += float(np.sum(20.0 * nc ** 3))
@@ -236,12 +257,31 @@ def whole_flops_8d(traces, leaf_sizes, d, dims, complex_):
     for tr, (m, n) in zip(traces, leaf_sizes):
         r = float(tr["rank_baca"])
         tot += (m + n) * 2 * r * r + 2 * d * r * (m + n) + 2 * d * r * n + 4 * (m + n) * r * r + 20 * r ** 3
-    for kind, dd, rows in dims:
+    for kind, dd, rows, _ in dims:
         if kind == 0:
             continue
         sv = dd[:, 3].astype(np.float64)
         tot += float(np.sum(12.0 * rows * sv ** 2 + 20.0 * (2 * sv) ** 3))
     return tot * (4.0 if complex_ else 1.0)
+
+
+def dense_flops(dims, complex_):
+    """(QR flops, Q-application flops) of one compression's re-compression and
+    merge stages: a leaf task factors both of its BACA factors (rows_a x k
+    and rows_b x k) and applies both Qs to its nout output columns; a merge
+    factors and applies the stacked side only (the block-diagonal side is a
+    plain product).  Four times that for complex data."""
+    qr = qa = 0.0
+    for kind, d, rows, rows_b in dims:
+        k = d[:, 0].astype(np.float64)
+        nout = d[:, 5].astype(np.float64)
+        qr += float(np.sum(qr_flops(rows, k)))
+        qa += float(np.sum(qapply_flops(rows, d[:, 1], nout)))
+        if kind == 0:
+            qr += float(np.sum(qr_flops(rows_b, k)))
+            qa += float(np.sum(qapply_flops(rows_b, d[:, 2], nout)))
+    f = 4.0 if complex_ else 1.0
+    return qr * f, qa * f
 
 
 # ------------------------------------------------------------------ clocks
@@ -576,13 +616,22 @@ def run_ours(args, rank, world):
                  "DMMA %.3f TFLOP/s" % probe)
     dominant = max(ktimes, key=lambda kk: ktimes[kk][0])
     traffic = TRAFFIC_PER_LAUNCH.get(args.workload, {})
-    work = {"baca_leaf_kernel": flops, "jacobi_kernel": jac_8d}
+    qr_fl, qa_fl = dense_flops(dims, True)
+    work = {"baca_leaf_kernel": flops, "jacobi_kernel": jac_8d, "qr_kernel": qr_fl, "qapply_kernel": qa_fl}
     roofs = {kn: roofline_of(kn, fl, ktimes, traffic.get(kn), peak_note) for kn, fl in work.items()}
+    counts = {"jacobi_kernel": "20 r^3 per leaf core, 20 (2s)^3 per merge core, x4 complex",
+              "qr_kernel": "2 m k^2 - 2 k^3 / 3 per Householder QR of m x k (geqrf count), x4 complex",
+              "qapply_kernel": ("4 m k s - 2 k^2 s per application of k reflectors of m rows to s columns "
+                                "(ormqr count), x4 complex; its event time overlaps the block products "
+                                "running beside it on the auxiliary stream"),
+              "baca_leaf_kernel": "the leaf BACA's own count from the pivot tape"}
+    for kn in roofs:
+        roofs[kn]["flop_count"] = counts[kn]
     roof = dict(roofs.get(dominant, roofs["jacobi_kernel"]), dominant_kernel=dominant)
     if roof["kernel"] == "jacobi_kernel":
         own = roofline_of("jacobi_kernel", jac_own, ktimes)
-        roof["flop_count"] = "20 r^3 per leaf core, 20 (2s)^3 per merge core, x4 complex"
         roof["frac_by_kernel_sweeps"] = own["frac"]
+    roof["frac_by_kernel"] = {kn: rr["frac"] for kn, rr in roofs.items()}
     whole = {"flops": whole_8d, "ms": ms_max, "achieved": whole_8d / (ms_max / 1e3) / 1e12,
              "frac": whole_8d / (ms_max / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "peak": FP64_PEAK_TFLOPS,
              "unit": "TFLOP/s", "flop_count": "leaf and merge work count of the measurement plan (r, s measured)"}
