@@ -211,17 +211,19 @@ def aca(gen, eps, seed=0, bid=0):
     return dict(U=U, V=V, r=U.shape[1], piv=piv, mu=mu)
 
 
-def recompress(U, V, eps, rank=None):
+def recompress(U, V, eps, rank=None, frob=False):
     """SVD re-compression of U V (Sec. 3.2, last paragraph):
     [Q_U, T_U] = QR(U), [Q_V, T_V] = QR(V^H), SVD(T_U T_V^H, eps) = X S Y^H;
-    returns (Q_U X, s, Y^H Q_V^H).  ``rank`` freezes the truncation rank."""
+    returns (Q_U X, s, Y^H Q_V^H).  ``rank`` freezes the truncation rank;
+    ``frob`` truncates by the Frobenius rule (linalg.frob_rank) with budget
+    eps."""
     m, r = U.shape
     n = V.shape[1]
     if r == 0:
         return U[:, :0], np.zeros(0), V[:0, :]
     Qu, Tu = np.linalg.qr(U)
     Qv, Tv = np.linalg.qr(V.conj().T)
-    X, s, Yh = truncated_svd(Tu @ Tv.conj().T, eps, rank)
+    X, s, Yh = truncated_svd(Tu @ Tv.conj().T, eps, rank, frob)
     return Qu @ X, s, Yh @ Qv.conj().T
 
 

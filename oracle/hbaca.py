@@ -8,6 +8,14 @@ s splits into a first child of ceil(s/2) and a second of floor(s/2) ("approximat
 equal sizes", Sec. 3.3).  Each merge is the literal SVD(., eps) of Sec. 2
 applied to the stacked factor (LAPACK gesdd), then the product with the
 other stacked factor.
+
+Optional Frobenius truncation (trunc="frob"): the accuracy the paper reports
+is the relative Frobenius error (Sec. 5.2), and a block passes through 2L + 1
+truncations (its leaf re-compression, then a horizontal and a vertical merge
+per level); each of them keeps the fewest singular triplets whose discarded
+tail is at most eps_loc = eps / sqrt(2L + 1) of that block's Frobenius norm,
+so the budgets add up to eps in quadrature.  BACA's own stopping test keeps
+eps.
 """
 import numpy as np
 
@@ -31,7 +39,7 @@ def tree_levels(n, L):
     return levels
 
 
-def horizontal_merge(U1, s1, V1, U2, s2, V2, eps, rank=None):
+def horizontal_merge(U1, s1, V1, U2, s2, V2, eps, rank=None, frob=False):
     """Eqs. columncomb, columnsvdmerge: U_bar = [U1 S1, U2 S2],
     V_bar = diag(V1, V2); [U, S, V'] = SVD(U_bar, eps); V = V' V_bar."""
     Ub = np.concatenate([U1 * s1[None, :], U2 * s2[None, :]], axis=1)
@@ -39,11 +47,11 @@ def horizontal_merge(U1, s1, V1, U2, s2, V2, eps, rank=None):
     Vb = np.zeros((r1 + r2, V1.shape[1] + V2.shape[1]), np.result_type(V1, V2))
     Vb[:r1, :V1.shape[1]] = V1
     Vb[r1:, V1.shape[1]:] = V2
-    U, s, Vp = truncated_svd(Ub, eps, rank)
+    U, s, Vp = truncated_svd(Ub, eps, rank, frob)
     return U, s, Vp @ Vb
 
 
-def vertical_merge(U1, s1, V1, U2, s2, V2, eps, rank=None):
+def vertical_merge(U1, s1, V1, U2, s2, V2, eps, rank=None, frob=False):
     """Alg. 3 lines 17-20: U_bar = diag(U1, U2), V_bar = [S1 V1; S2 V2];
     [U', S, V] = SVD(V_bar, eps); U = U_bar U'."""
     r1, r2 = U1.shape[1], U2.shape[1]
@@ -51,11 +59,17 @@ def vertical_merge(U1, s1, V1, U2, s2, V2, eps, rank=None):
     Ub[:U1.shape[0], :r1] = U1
     Ub[U1.shape[0]:, r1:] = U2
     Vb = np.concatenate([s1[:, None] * V1, s2[:, None] * V2], axis=0)
-    Up, s, V = truncated_svd(Vb, eps, rank)
+    Up, s, V = truncated_svd(Vb, eps, rank, frob)
     return Ub @ Up, s, V
 
 
-def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None, ranks=None):
+def frob_budget(eps, L):
+    """Frobenius budget of one truncation of an L-level H-BACA: the 2L + 1
+    truncations a block passes through share eps in quadrature."""
+    return eps / np.sqrt(2.0 * L + 1.0)
+
+
+def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None, ranks=None, trunc="sigma"):
     """H-BACA(A, n_b = 4^L, d, eps) of Alg. 3.  Returns a dict with U, s, V,
     rank r, the leaf BACA results (if ``keep_leaves``), the leaf ranks before
     and after re-compression, and the merge ranks per level.  ``forced``
@@ -65,7 +79,14 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None,
     ``ranks`` freezes truncation ranks: it maps ("full", 0, a, b) (leaf
     re-compression), ("half", l, a, b) and ("full", l, a, b) (merges) to a
     rank; the result's "ranks" entry lists every truncation rank taken, in the
-    same keys, so that one run's choices can be frozen in another."""
+    same keys, so that one run's choices can be frozen in another.
+    ``trunc``: "sigma" (the eps-rank of Sec. 2) or "frob" (each truncation
+    keeps the fewest triplets whose tail is at most frob_budget(eps, L) of the
+    block's Frobenius norm)."""
+    if trunc not in ("sigma", "frob"):
+        raise ValueError("trunc must be 'sigma' or 'frob'")
+    frob = trunc == "frob"
+    et = frob_budget(eps, L) if frob else eps
     taken = {}
 
     def rk(key):
@@ -86,7 +107,7 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None,
                 res["stop"] = "replayed"
             else:
                 res = baca(w, d, eps, seed=seed, bid=block_id(batch_index, a, b))
-            U, s, V = recompress(res["U"], res["V"], eps, rk(("full", 0, a, b)))
+            U, s, V = recompress(res["U"], res["V"], et, rk(("full", 0, a, b)), frob)
             taken[("full", 0, a, b)] = len(s)
             blocks[(a, b)] = (U, s, V)
             info = dict(r_baca=res["r"], r=len(s), iters=len(res["trace"]), stop=res["stop"])
@@ -101,14 +122,14 @@ def hbaca(gen, L, d, eps, seed=0, batch_index=0, keep_leaves=False, forced=None,
             for b in range(len(cols[l])):
                 U1, s1, V1 = blocks[(a, 2 * b)]
                 U2, s2, V2 = blocks[(a, 2 * b + 1)]
-                half[(a, b)] = horizontal_merge(U1, s1, V1, U2, s2, V2, eps, rk(("half", l, a, b)))
+                half[(a, b)] = horizontal_merge(U1, s1, V1, U2, s2, V2, et, rk(("half", l, a, b)), frob)
                 taken[("half", l, a, b)] = len(half[(a, b)][1])
         full = {}
         for a in range(len(rows[l])):
             for b in range(len(cols[l])):
                 U1, s1, V1 = half[(2 * a, b)]
                 U2, s2, V2 = half[(2 * a + 1, b)]
-                full[(a, b)] = vertical_merge(U1, s1, V1, U2, s2, V2, eps, rk(("full", l, a, b)))
+                full[(a, b)] = vertical_merge(U1, s1, V1, U2, s2, V2, et, rk(("full", l, a, b)), frob)
                 taken[("full", l, a, b)] = len(full[(a, b)][1])
         merge_ranks.append(dict(half={k: len(v[1]) for k, v in half.items()},
                                 full={k: len(v[1]) for k, v in full.items()}))

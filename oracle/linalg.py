@@ -11,6 +11,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 * ``strong_rrqr``: Gu and Eisenstat's swap refinement of a chosen set, one of
   the subset-selection alternatives to QRCP that Sec. 3.2 names.
 * ``eps_rank``: r = min{k : Sigma_{k+1,k+1} < eps Sigma_{1,1}} (Sec. 2).
+* ``frob_rank``: the Frobenius reading of a truncation, the smallest t whose
+  discarded tail sqrt(sum_{j>t} Sigma_jj^2) is at most eps_loc ||A||_F (the
+  paper measures accuracy as the relative Frobenius error, Sec. 5.2).
 """
 import numpy as np
 import scipy.linalg
@@ -195,11 +198,25 @@ def eps_rank(s, eps):
     return int(np.count_nonzero(s >= eps * s[0]))
 
 
-def truncated_svd(A, eps, rank=None):
+def frob_rank(s, eps_loc):
+    """Smallest t with sqrt(sum_{j >= t} s_j^2) <= eps_loc sqrt(sum_j s_j^2)
+    for a descending singular value list s (0-based: s[t:] is discarded).
+    By Eckart and Young the rank-t truncation of A then has Frobenius error
+    at most eps_loc ||A||_F and every smaller rank has more."""
+    s = np.asarray(s, dtype=np.float64)
+    total = np.sqrt(np.sum(s * s))
+    for t in range(s.size + 1):
+        if np.sqrt(np.sum(s[t:] * s[t:])) <= eps_loc * total:
+            return t
+    return s.size
+
+
+def truncated_svd(A, eps, rank=None, frob=False):
     """[U, Sigma, V, r] = SVD(A, eps) (Sec. 2): LAPACK gesdd with a gesvd
-    fallback, truncated at the eps-rank, or at ``rank`` when given (a frozen
-    truncation rank, used to differentiate the map with its discrete choices
-    held fixed).  Returns U (m x r), s (r), Vh (r x n)."""
+    fallback, truncated at the eps-rank, at frob_rank(s, eps) when ``frob``
+    (eps is then the truncation's own Frobenius budget), or at ``rank`` when
+    given (a frozen truncation rank, used to differentiate the map with its
+    discrete choices held fixed).  Returns U (m x r), s (r), Vh (r x n)."""
     A = np.asarray(A)
     m, n = A.shape
     if m == 0 or n == 0:
@@ -209,5 +226,8 @@ def truncated_svd(A, eps, rank=None):
     except np.linalg.LinAlgError:
         import scipy.linalg
         U, s, Vh = scipy.linalg.svd(A, full_matrices=False, lapack_driver="gesvd")
-    r = eps_rank(s, eps) if rank is None else min(int(rank), s.size)
+    if rank is not None:
+        r = min(int(rank), s.size)
+    else:
+        r = frob_rank(s, eps) if frob else eps_rank(s, eps)
     return U[:, :r], s[:r], Vh[:r]

@@ -119,3 +119,19 @@ def test_strong_rrqr_criterion_without_residual_term(monkeypatch):
         return np.abs(Ri @ (Q.conj().T @ M[:, rest])) ** 2
     monkeypatch.setattr(ol, "strong_rrqr_criterion", bad)
     _expect_failure(pins.test_strong_rrqr_criterion_is_the_volume_ratio_of_a_swap, 9, 5)
+
+
+def test_frob_budget_not_split_over_the_truncations(monkeypatch):
+    monkeypatch.setattr(oh, "frob_budget", lambda eps, L: eps)
+    _expect_failure(pins.test_hbaca_frob_truncations_follow_the_budget)
+
+
+def test_frob_budget_split_linearly(monkeypatch):
+    monkeypatch.setattr(oh, "frob_budget", lambda eps, L: eps / (2.0 * L + 1.0))
+    _expect_failure(pins.test_hbaca_frob_truncations_follow_the_budget)
+
+
+def test_frob_rank_off_by_one(monkeypatch):
+    orig = ol.frob_rank
+    monkeypatch.setattr(ol, "frob_rank", lambda s, e: max(orig(s, e) - 1, 0))
+    _expect_failure(pins.test_frob_truncation_is_eckart_young_minimal, 1e-3)

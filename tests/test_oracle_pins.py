@@ -236,6 +236,90 @@ def test_eps_rank_definition():
     assert ol.eps_rank([], 1e-6) == 0
 
 
+def test_frob_rank_definition():
+    """Frobenius reading of a truncation (Sec. 5.2 measures the relative
+    Frobenius error): the fewest kept values whose discarded tail is at most
+    eps_loc of the whole.  s = (1, 0.1, 0.01, 0.001): ||s|| = 1.0050378,
+    tails from t = 1: 0.1005038, 0.0100499, 0.001, 0."""
+    s = [1.0, 0.1, 0.01, 0.001]
+    assert ol.frob_rank(s, 1e-4) == 4   # 1.005e-4 < 0.001
+    assert ol.frob_rank(s, 5e-3) == 3   # 0.001 <= 5.025e-3 < 0.01005
+    assert ol.frob_rank(s, 0.02) == 2   # 0.01005 <= 0.0201 < 0.1005
+    assert ol.frob_rank(s, 0.5) == 1
+    assert ol.frob_rank(s, 1.0) == 0
+    assert ol.frob_rank([3.0, 4.0], 0.8) == 1  # tail 4 <= 0.8 * 5, equality kept
+    assert ol.frob_rank([0.0, 0.0], 1e-6) == 0
+    assert ol.frob_rank([], 1e-6) == 0
+
+
+@pytest.mark.parametrize("eps_loc", [1e-1, 1e-3, 1e-7])
+def test_frob_truncation_is_eckart_young_minimal(eps_loc):
+    """truncated_svd(frob=True) keeps t triplets with ||A - A_t||_F <= eps_loc
+    ||A||_F formed directly from A, while the best rank t - 1 approximation
+    (from an independent gesvd) misses it."""
+    rng = np.random.default_rng(11)
+    m, n = 90, 70
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q1 * np.logspace(0, -12, n)[None, :]) @ Q2.T
+    U, s, Vh = ol.truncated_svd(A, eps_loc, frob=True)
+    t = len(s)
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(A - (U * s) @ Vh) <= eps_loc * nA * (1 + 1e-12)
+    assert t >= 1
+    Ug, sg, Vg = scipy.linalg.svd(A, lapack_driver="gesvd", full_matrices=False)
+    prev = A - (Ug[:, :t - 1] * sg[:t - 1]) @ Vg[:t - 1]
+    assert np.linalg.norm(prev) > eps_loc * nA
+
+
+def _frob_rule_holds(M, t, budget, slack=1e-9):
+    """t is the fewest singular values of M (dense SVD) whose discarded tail
+    is at most budget ||M||_F (decisions within slack of the threshold
+    accept either side)."""
+    sv = np.linalg.svd(M, compute_uv=False)
+    nM = np.linalg.norm(sv)
+    tail = lambda k: np.linalg.norm(sv[k:])
+    ok_t = tail(t) <= budget * nM * (1 + slack)
+    minimal = t == 0 or tail(t - 1) > budget * nM * (1 - slack)
+    return ok_t and minimal
+
+
+def test_hbaca_frob_truncations_follow_the_budget():
+    """trunc="frob" with L = 1: each leaf re-compression and each horizontal
+    merge keeps the fewest triplets whose tail is at most eps / sqrt(3) of the
+    block's Frobenius norm (2L + 1 = 3 truncations per block), checked on the
+    dense blocks (the leaf's BACA product, the two re-compressed neighbours
+    side by side) with numpy's SVD; the final error meets eps."""
+    x, y = inputs.gaussian_pair(seed=3, m=240, n=220)
+    g = og.Gaussian(x, y, 0.8)
+    eps, L = 1e-5, 1
+    res = oh.hbaca(g, L, 8, eps, seed=0, keep_leaves=True, trunc="frob")
+    budget = eps / np.sqrt(3.0)
+    leaves = dict(res["stages"][0][2])
+    for (a, b), info in res["leaves"].items():
+        bac = info["baca"]
+        assert _frob_rule_holds(bac["U"] @ bac["V"], info["r"], budget), ("leaf", a, b)
+    half = dict(res["stages"][1][2])
+    for (a, b), (U, s, V) in half.items():
+        U1, s1, V1 = leaves[(a, 2 * b)]
+        U2, s2, V2 = leaves[(a, 2 * b + 1)]
+        M = np.concatenate([(U1 * s1) @ V1, (U2 * s2) @ V2], axis=1)
+        assert _frob_rule_holds(M, len(s), budget), ("half", a, b)
+    A = g(np.arange(g.m), np.arange(g.n))
+    err = np.linalg.norm(A - (res["U"] * res["s"]) @ res["V"]) / np.linalg.norm(A)
+    assert err <= eps
+
+
+def test_hbaca_frob_nb1_is_baca_plus_frob_recompression():
+    """With n_b = 1 the budget is eps itself (2L + 1 = 1)."""
+    g = _gauss_small()
+    h = oh.hbaca(g, 0, 8, 1e-6, seed=4, trunc="frob")
+    b = ob.baca(g, 8, 1e-6, seed=4, bid=osamp.block_id(0, 0, 0))
+    U, s, V = ob.recompress(b["U"], b["V"], 1e-6, frob=True)
+    np.testing.assert_allclose(h["s"], s, rtol=1e-12)
+    assert _frob_rule_holds(b["U"] @ b["V"], len(s), 1e-6)
+
+
 # ---------------------------------------------------------------- LRID / norms
 @pytest.mark.parametrize("cplx", [False, True])
 def test_lrid_is_interpolative_decomposition(cplx):
