@@ -132,6 +132,15 @@ typedef struct hbaca_gen {
                                   resident; waits are bounded, HBACA_TIMEOUT on expiry).
                                   This flag is for tools that serialise or re-launch
                                   kernels (profilers), which cannot keep them resident. */
+#define HBACA_FLAG_FROB 32u    /* truncate every leaf re-compression and merge by the
+                                  Frobenius rule instead of the eps-rank of Sec. 2: keep
+                                  the fewest singular triplets whose discarded tail
+                                  sqrt(sum_{j>t} sigma_j^2) is at most eps / sqrt(2L + 1)
+                                  of the block's Frobenius norm (L: the block's merge
+                                  levels; a block passes through 2L + 1 truncations, so
+                                  their budgets add up to eps in quadrature, the relative
+                                  Frobenius error of Sec. 5.2).  BACA's own stopping test
+                                  (nu < eps mu) is unchanged. */
 
 /* Options of one compression (Alg. 3 inputs n_b, d, eps). */
 typedef struct hbaca_opts {

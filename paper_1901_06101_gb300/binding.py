@@ -19,6 +19,7 @@ FLAG_PROFILE = 2
 FLAG_TAPE = 4
 FLAG_GRAPH = 8
 FLAG_SINGLE_CLUSTER = 16
+FLAG_FROB = 32
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "RANK_CAPACITY", 3: "CUDA", 4: "TIMEOUT",
           5: "NO_TAPE", 6: "NUMERICAL", 7: "WORKSPACE", 8: "NOT_CONVERGED"}
 STOP = {0: "converged", 1: "iterations", 2: "no columns", 3: "no rows", 4: "capacity", 5: "numerical"}

@@ -1142,8 +1142,29 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
     if (tid == 0) {
       const double s1 = sv[ord[0]];
       int s = 0;
-      if (s1 > 0.0 && isfinite(s1))
-        while (s < nc && s < mr && sv[ord[s]] >= P.eps * s1) ++s;
+      if (s1 > 0.0 && isfinite(s1)) {
+        const int pmax = min(nc, mr);
+        if (t.trunc > 0) {
+          // Frobenius rule: the fewest values whose discarded tail
+          // sqrt(sum_{j >= s} sigma_j^2) is at most eps / sqrt(2L + 1) of
+          // sqrt(sum_j sigma_j^2); the tail grows from the smallest value
+          const double budget = P.eps / sqrt((double)t.trunc);
+          double total = 0.0;
+          for (int j = 0; j < pmax; ++j) total = fma(sv[ord[j]], sv[ord[j]], total);
+          const double lim = budget * sqrt(total);
+          double tail = 0.0;
+          s = pmax;
+          while (s > 0) {
+            const double v = sv[ord[s - 1]];
+            const double nt = fma(v, v, tail);
+            if (!(sqrt(nt) <= lim)) break;
+            tail = nt;
+            --s;
+          }
+        } else {
+          while (s < pmax && sv[ord[s]] >= P.eps * s1) ++s;
+        }
+      }
       if (!isfinite(s1)) set_status(P.status, DS_NUMERICAL);
       const BlockRef ob = P.out_blocks[t.out];
       if (s > ob.cap) { set_status(P.status, DS_RANK_CAPACITY); s = ob.cap; }

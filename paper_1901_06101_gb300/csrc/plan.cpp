@@ -248,6 +248,7 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
   // keeps all singular triplets of its core: storage capacity = the producing
   // task's k capacity, the number stored goes to a second rank-array slot)
   p.tape = (o.flags & HBACA_FLAG_TAPE) != 0;
+  p.frob = (o.flags & HBACA_FLAG_FROB) != 0;
   std::vector<int64_t> kc_b(nblocks);
   for (int b = 0; b < nblocks; ++b) kc_b[b] = std::min<int64_t>(2 * p.cap_b[b], 2 * std::min(gens[b].m, gens[b].n));
   std::vector<BlockRef> refs;
@@ -391,6 +392,7 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
       t.rows_b = L.n;
       t.src_v_off = L.v_off;
       t.out = p.Lb[b] == 0 ? (p.tape ? p.root_tape_first + b : p.user_ref_first + b) : p.full_idx[b][0][a * nb + cc];
+      t.trunc = p.frob ? 2 * p.Lb[b] + 1 : 0;
     }
     add_stage(ts, TASK_LEAF, -1, 0);
   }
@@ -413,6 +415,7 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
             t.lda = t.rows_a;
             t.out = p.half_idx[b][l][a * ncn + cc];
             t.m1 = (int32_t)cols[b][l - 1][2 * cc].second;
+            t.trunc = p.frob ? 2 * p.Lb[b] + 1 : 0;
             th.push_back(t);
           }
       }
@@ -431,6 +434,7 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
             t.out = p.Lb[b] == l ? (p.tape ? p.root_tape_first + b : p.user_ref_first + b)
                                  : p.full_idx[b][l][a * ncn + cc];
             t.m1 = (int32_t)rows[b][l - 1][2 * a].second;
+            t.trunc = p.frob ? 2 * p.Lb[b] + 1 : 0;
             tv.push_back(t);
           }
       }

@@ -72,6 +72,7 @@ struct Plan {
   int nslots = 0;                 // length of the rank array (refs, then full-triplet counts)
   int user_ref_first = 0;         // global ref index of block 0's result
   bool tape = false;              // HBACA_FLAG_TAPE: every node keeps all its singular triplets
+  bool frob = false;              // HBACA_FLAG_FROB: Frobenius truncation rule
   int root_tape_first = -1;       // tape: global ref index of block 0's root node
   // device-written tables
   size_t leafout_off = 0, ranks_off = 0;

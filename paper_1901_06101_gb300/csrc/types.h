@@ -69,7 +69,9 @@ struct SvdTask {
   int64_t lda;
   // QR operand B (LEAF only): rows_b x k, column-major (V^H), in the QR arena
   int64_t b_off;
-  int32_t rows_b, pad0;
+  int32_t rows_b;
+  int32_t trunc;       // truncation rule: 0 the eps-rank (Sec. 2); n > 0 the Frobenius
+                       // rule with budget eps / sqrt(n), n = 2L + 1 (HBACA_FLAG_FROB)
   int64_t src_v_off;   // LEAF: offset of the leaf's V (k x rows_b, row-major) in the BACA V arena
   int64_t tau_off;     // 3 * kcap scalars: reflectors of QR(A), QR(B), QRCP of the core
   int64_t m_off;       // core M (kcap x kcap, column-major ld kcap); QRCP in place

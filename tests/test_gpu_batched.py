@@ -76,6 +76,28 @@ def test_batched_matches_oracle_per_block(ctx):
     assert len(depths) >= 2, depths
 
 
+def test_batched_frob_budget_per_block(ctx):
+    """HBACA_FLAG_FROB in a batch: every block's truncations take the budget
+    of its own depth, eps / sqrt(2L + 1); each block against the oracle
+    H-BACA with trunc="frob" at that depth."""
+    blocks = inputs.batched_blocks(seed=3, nblocks=6, lo=64, hi=700)
+    d, eps, target, seed = 8, 1e-8, 256, 0
+    specs = _specs(blocks)
+    opts = B.make_opts(eps, d, -target, seed=seed, rank_cap=256, leaf_rank_cap=256, flags=B.FLAG_FROB)
+    outs = B.compress_batched(ctx, specs, opts)
+    torch.cuda.synchronize()
+    depths = set()
+    for b, ((x, y, h), res) in enumerate(zip(blocks, outs)):
+        ogen = og.Gaussian(x, y, h)
+        L = levels_for(ogen.m, ogen.n, target)
+        depths.add(L)
+        nb = 1 << L
+        traces = {leaf: B.read_leaf_trace_batched(specs, opts, outs[0].ws, b, leaf) for leaf in range(nb * nb)}
+        full = oh.hbaca(ogen, L, d, eps, seed=seed, batch_index=b, forced=traces, trunc="frob")
+        check_result(ogen, res, eps, full)
+    assert len(depths) >= 2, depths
+
+
 def test_batched_single_block_equals_compress(ctx):
     """A batch of one is the plain call: same plan, same streams, same bits."""
     x, y = inputs.gaussian_pair(seed=4, m=777, n=650)

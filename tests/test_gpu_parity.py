@@ -311,6 +311,41 @@ def _pivot_sets(tr):
 
 
 @pytest.mark.parametrize("cplx", [False, True])
+def test_frob_truncation_against_oracle(ctx, cplx):
+    """HBACA_FLAG_FROB (each of the 2L + 1 truncations a block passes through
+    keeps the fewest triplets whose tail is at most eps / sqrt(2L + 1) of its
+    Frobenius norm): the final factors against the frozen-pivot oracle H-BACA
+    run with trunc="frob" (rank within 2, relative error within 1e-10,
+    singular values to 1e-9 sigma_1) and an error within 1.5 eps.  On the
+    Gaussian matrix, whose spectrum decays smoothly, the rule keeps more than
+    the eps-rank of the same call without the flag and brings the relative
+    Frobenius error (Sec. 5.2) below that run's; the Helmholtz pair of
+    spheres has a sharp drop after its 66th value, where both rules agree."""
+    if cplx:
+        x, y = inputs.sphere_pair(seed=2, m=1200, n=1100)
+        spec, og_ = B.helmholtz(x, y, 4 * np.pi), og.Helmholtz(x, y, 4 * np.pi)
+        eps, d = 1e-4, 16
+    else:
+        x, y = inputs.gaussian_pair(seed=0, m=2000, n=2000)
+        spec, og_ = B.gaussian(x, y, 1.0), og.Gaussian(x, y, 1.0)
+        eps, d = 1e-6, 8
+    L = 2
+    opts = B.make_opts(eps, d, L, seed=0, rank_cap=256, leaf_rank_cap=256, flags=B.FLAG_FROB)
+    res = B.compress(ctx, spec, opts)
+    plain = B.compress(ctx, spec, B.make_opts(eps, d, L, seed=0, rank_cap=256, leaf_rank_cap=256))
+    torch.cuda.synchronize()
+    traces = {leaf: B.read_leaf_trace(spec, opts, res.ws, leaf) for leaf in range(16)}
+    full = oh.hbaca(og_, L, d, eps, seed=0, forced=traces, trunc="frob")
+    err = check_result(og_, res, eps, full)
+    A = og_(np.arange(og_.m), np.arange(og_.n))
+    err_plain = dense_rel_error(A, plain.U.cpu().numpy(), plain.S.cpu().numpy(), plain.V.cpu().numpy())
+    assert res.rank >= plain.rank, (res.rank, plain.rank)
+    assert err <= 1.5 * eps, err
+    if not cplx:  # a smooth spectrum: the eps-rank run misses eps, the Frobenius rule keeps more
+        assert res.rank > plain.rank and err < err_plain, (res.rank, plain.rank, err, err_plain)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
 def test_strong_rrqr_pivots(ctx, cplx):
     """BACA with strong-RRQR pivot sets (f = 1.1): every GPU set passes the
     oracle's frozen replay with the strong criterion (no swap above f^2 left,
