@@ -666,7 +666,18 @@ def bench_cfg1(args, dev, flush, stream):
     gms, gres = _timed_calls(lambda: B.compress(ctx, spec, gopts, ws=gws, out=gout), max(3, min(args.steps, 10)),
                              max(3, args.warmup), flush, stream)
     assert gres.rank == r["rank"]
+    # the Frobenius truncation rule (HBACA_FLAG_FROB): budget eps / sqrt(2L + 1)
+    # per truncation instead of the eps-rank
+    fopts = mk_opts(1e-6, 8, 2, seed=0, rank_cap=128, leaf_rank_cap=256, flags=B.FLAG_FROB)
+    fws = torch.empty(B.workspace_size(spec.gen, fopts), dtype=torch.uint8, device=dev)
+    fout = (torch.empty((128, 2000), dtype=torch.float64, device=dev), torch.empty(128, dtype=torch.float64, device=dev),
+            torch.empty((128, 2000), dtype=torch.float64, device=dev))
+    fms, fres = _timed_calls(lambda: B.compress(ctx, spec, fopts, ws=fws, out=fout), max(3, min(args.steps, 10)),
+                             max(3, args.warmup), flush, stream)
+    ferr = B.rel_error(ctx, spec, fres)
+    torch.cuda.synchronize(dev)
     return {"workload": "gaussian_f64_2000_d8_L2_eps1e-6", "ms": r["ms"], "ms_graph_replay": gms,
+            "frob_truncation": {"ms": fms, "rank": fres.rank, "rel_error": ferr},
             "entries_per_s": r["entries"] / (r["ms"] / 1e3),
             "rank": r["rank"], "rel_error": err,
             "roofline_whole": {"achieved": whole, "frac": whole / FP64_PEAK_TFLOPS, "flops": r["whole_flops"],
