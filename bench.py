@@ -71,7 +71,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA 
 # DRAM bytes (read + write) per launch of the current kernels on the default
 # workload, averaged over one compression's launches (ncu dram__bytes_read.sum
 # + dram__bytes_write.sum); None where no capture of the current kernel exists
-TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 15.52e6, "qr_kernel": 33.67e9, "qapply_kernel": 16.92e9}}
+TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 15.52e6, "qr_kernel": 33.67e9, "qapply_kernel": 16.92e9,
+                                         "baca_leaf_kernel": 11.56e9}}
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json beside this
+    file), or None when the file is absent."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 EXTRA_FLAGS = 0  # option flags added to every call (--single-cluster)
@@ -502,6 +513,13 @@ def roofline_of(kname, flops, ktimes, traffic=None, note=None):
          "ms_per_launch": kms / max(kl, 1), "launches": kl}
     if note:
         r["peak_note"] = note
+    hbm = measured_hbm_gbs()
+    if traffic and hbm:
+        # the same launches against the memory roofline: DRAM bytes per launch
+        # (ncu) over the event-timed launch time, of the measured copy bandwidth
+        gbs = traffic / (r["ms_per_launch"] / 1e3) / 1e9
+        r["dram"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
     return r
 
 
