@@ -124,11 +124,15 @@ inline int pick_qr_cluster(int jobs, int rows, int sms, int min_rows_per_cta) {
 
 // Clusters per matrix when a stage has too few matrices to fill the machine
 // with one 16-CTA cluster each: 8-CTA clusters, as many per matrix as two
-// CTAs per SM, the resident clusters and the exchange slots allow; 1 when
-// that is not more than 16 CTAs.  (The column steps of such a stage are bound
-// by each CTA's own FP64 work: on the 50000-row root of the sparse-product
-// workload QR + Q application took 3394 / 1932 / 1405 / 974 / 625 ms with 4 /
-// 8 / 12 / 19 / 37 clusters.)
+// CTAs per SM, the resident clusters and the exchange slots allow, with at
+// least min_rows_per_cta rows per CTA; 1 when that is not more than 16 CTAs.
+// (The column steps of such a stage are bound by each CTA's own FP64 work:
+// on the 50000-row root of the sparse-product workload QR + Q application
+// took 3394 / 1932 / 1405 / 974 / 625 ms with 4 / 8 / 12 / 19 / 37 clusters.
+// Each step also waits for every cluster of its matrix, which costs more
+// than the rows it saves below about 128 rows per CTA: the 10000- and
+// 20000-row top stages of the 20000^2 workload, 132 columns, took 14.9 and
+// 15.7 ms with 18 and 37 clusters, 14.35 and 14.95 with 9 and 18.)
 inline int pick_groups(int jobs, int rows, int sms, int resident, int min_rows_per_cta) {
   int G = 1;
   while (jobs * (G + 1) <= kXSlots && jobs * (G + 1) * 8 <= 2 * sms && jobs * (G + 1) <= resident &&
@@ -260,7 +264,7 @@ cudaError_t run_stage(Plan& p, int si, const Stage& sg, RunCtx& rc, std::string&
   if (rc.xgroups && qr_forced_cluster() == 0 && cq == 16 && sg.nqr == sg.nq && sg.nqr * 16 < rc.sms) {
     const int res = std::min(resident_clusters(qr_kernel<T>, 8, qr_smem, rc.st),
                              resident_clusters(qapply_kernel<T>, 8, qa_smem, rc.st));
-    int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 64);
+    int G = pick_groups(sg.nqr, sg.rows_max, rc.sms, res, 128);
     if (qr_forced_groups() > 0 && G > qr_forced_groups()) G = qr_forced_groups() * 8 > 16 ? qr_forced_groups() : 1;
     if (G > 1) {
       cq = 8;
