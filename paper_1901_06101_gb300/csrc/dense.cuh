@@ -1147,15 +1147,22 @@ __global__ void __launch_bounds__(kDenseThreads, 3) jacobi_kernel(const DensePar
         if (t.trunc > 0) {
           // Frobenius rule: the fewest values whose discarded tail
           // sqrt(sum_{j >= s} sigma_j^2) is at most eps / sqrt(2L + 1) of
-          // sqrt(sum_j sigma_j^2); the tail grows from the smallest value
+          // sqrt(sum_j sigma_j^2); the tail grows from the smallest value.
+          // The values are scaled by the power of two below sigma_1 (exact,
+          // so every comparison is the unscaled one; the squares cannot
+          // overflow)
           const double budget = P.eps / sqrt((double)t.trunc);
+          const double r2 = pow2_inverse(pow2_below(s1));
           double total = 0.0;
-          for (int j = 0; j < pmax; ++j) total = fma(sv[ord[j]], sv[ord[j]], total);
+          for (int j = 0; j < pmax; ++j) {
+            const double v = sv[ord[j]] * r2;
+            total = fma(v, v, total);
+          }
           const double lim = budget * sqrt(total);
           double tail = 0.0;
           s = pmax;
           while (s > 0) {
-            const double v = sv[ord[s - 1]];
+            const double v = sv[ord[s - 1]] * r2;
             const double nt = fma(v, v, tail);
             if (!(sqrt(nt) <= lim)) break;
             tail = nt;
