@@ -71,7 +71,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA 
 # DRAM bytes (read + write) per launch of the current kernels on the default
 # workload, averaged over one compression's launches (ncu dram__bytes_read.sum
 # + dram__bytes_write.sum); None where no capture of the current kernel exists
-TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 15.51e6, "qr_kernel": 33.67e9, "qapply_kernel": 16.92e9,
+TRAFFIC_PER_LAUNCH = {"helmholtz20000": {"jacobi_kernel": 15.67e6, "qr_kernel": 33.67e9, "qapply_kernel": 16.92e9,
                                          "baca_leaf_kernel": 11.56e9}}
 
 
