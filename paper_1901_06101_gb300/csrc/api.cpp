@@ -680,7 +680,8 @@ size_t hbaca_debug_plan_json(const hbaca_gen* gen, const hbaca_opts* opts, char*
            ", \"tau_off\": " + std::to_string(t.tau_off) + ", \"m_off\": " + std::to_string(t.m_off) +
            ", \"y_off\": " + std::to_string(t.y_off) + ", \"ord_off\": " + std::to_string(t.ord_off) +
            ", \"kcap\": " + std::to_string(t.kcap) + ", \"in1\": " + std::to_string(t.in1) +
-           ", \"in2\": " + std::to_string(t.in2) + ", \"out\": " + std::to_string(t.out) + "}";
+           ", \"in2\": " + std::to_string(t.in2) + ", \"out\": " + std::to_string(t.out) +
+           ", \"trunc\": " + std::to_string(t.trunc) + "}";
       if (ti + 1 < st.tasks_h->size()) j += ", ";
     }
     j += "]}";

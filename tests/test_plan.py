@@ -60,3 +60,20 @@ def test_baca_cluster_follows_the_rounds_rule(m, L, expect):
 
 def test_explicit_cluster_size_is_kept():
     assert _plan(20000, 20000, 4, cluster=2)["baca_cluster"] == 2
+
+
+@pytest.mark.parametrize("L", [0, 2, 4])
+def test_frobenius_budget_per_task(L):
+    """HBACA_FLAG_FROB: every leaf re-compression and merge task carries the
+    divisor 2L + 1 of its Frobenius budget eps / sqrt(2L + 1); without the
+    flag every task keeps the eps-rank (0)."""
+    m = 20000 if L else 1200
+    plain = _plan(m, m, L)
+    frob = _plan(m, m, L, flags=B.FLAG_FROB)
+    for j, want in ((plain, 0), (frob, 2 * L + 1)):
+        tasks = [t for st in j["stages"] for t in st["tasks"]]
+        # 4^L leaves; per level l, 2 * 4^(L-l) horizontal and 4^(L-l) vertical merges
+        assert len(tasks) == 4 ** L + sum(3 * 4 ** (L - l) for l in range(1, L + 1))
+        assert all(t["trunc"] == want for t in tasks)
+    nstages = 1 + 2 * L
+    assert len(frob["stages"]) == nstages
