@@ -3,6 +3,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 
@@ -47,11 +48,17 @@ bool check_gen(const hbaca_gen& g, std::string& err) {
       break;
     case HBACA_GEN_GAUSSIAN:
       if (g.dtype != HBACA_F64) { err = "GAUSSIAN is float64"; return false; }
-      if (!g.x || !g.y || g.dim < 1 || g.dim > 64 || !(g.h > 0.0)) { err = "GAUSSIAN needs x, y, 1 <= dim <= 64, h > 0"; return false; }
+      if (!g.x || !g.y || g.dim < 1 || g.dim > 64 || !(g.h > 0.0 && std::isfinite(g.h))) {
+        err = "GAUSSIAN needs x, y, 1 <= dim <= 64 and a finite h > 0";
+        return false;
+      }
       break;
     case HBACA_GEN_HELMHOLTZ:
       if (g.dtype != HBACA_C128) { err = "HELMHOLTZ is complex128"; return false; }
-      if (!g.x || !g.y || g.dim < 1 || g.dim > 64) { err = "HELMHOLTZ needs x, y, 1 <= dim <= 64"; return false; }
+      if (!g.x || !g.y || g.dim < 1 || g.dim > 64 || !std::isfinite(g.k)) {
+        err = "HELMHOLTZ needs x, y, 1 <= dim <= 64 and a finite k";
+        return false;
+      }
       break;
     case HBACA_GEN_SPARSE_PRODUCT:
       if (g.dtype != HBACA_F64) { err = "SPARSE_PRODUCT is float64"; return false; }
@@ -66,15 +73,15 @@ bool check_gen(const hbaca_gen& g, std::string& err) {
       break;
     case HBACA_GEN_POLYNOMIAL:
       if (g.dtype != HBACA_F64) { err = "POLYNOMIAL is float64"; return false; }
-      if (!g.x || !g.y || g.dim < 1 || g.dim > 1024 || !(g.h == g.h)) {
+      if (!g.x || !g.y || g.dim < 1 || g.dim > 1024 || !std::isfinite(g.h)) {
         err = "POLYNOMIAL needs x, y, 1 <= dim <= 1024 and a finite h";
         return false;
       }
       break;
     case HBACA_GEN_HANKEL2D:
       if (g.dtype != HBACA_C128) { err = "HANKEL2D is complex128"; return false; }
-      if (!g.x || !g.y || g.dim < 1 || g.dim > 64 || !(g.k > 0.0)) {
-        err = "HANKEL2D needs x, y, 1 <= dim <= 64, k > 0";
+      if (!g.x || !g.y || g.dim < 1 || g.dim > 64 || !(g.k > 0.0 && std::isfinite(g.k))) {
+        err = "HANKEL2D needs x, y, 1 <= dim <= 64 and a finite k > 0";
         return false;
       }
       break;
@@ -128,6 +135,11 @@ bool make_plan(const hbaca_gen* gens, int nblocks, const hbaca_opts& o, int sms,
   }
   if (!(o.eps > 0.0 && o.eps < 1.0)) { err = "eps must be in (0, 1)"; return false; }
   if (o.d < 1 || o.d > 32) { err = "d must be in [1, 32]"; return false; }
+  if (o.flags & ~(HBACA_FLAG_ASYNC | HBACA_FLAG_PROFILE | HBACA_FLAG_TAPE | HBACA_FLAG_GRAPH | HBACA_FLAG_SINGLE_CLUSTER |
+                  HBACA_FLAG_FROB)) {
+    err = "unknown option flags";
+    return false;
+  }
   if (!(o.srrqr_f == 0.0 || (o.srrqr_f > 1.0 && o.srrqr_f < 1e150))) {
     err = "srrqr_f must be 0 or a finite value > 1"; return false;
   }

@@ -77,3 +77,42 @@ def test_frobenius_budget_per_task(L):
         assert all(t["trunc"] == want for t in tasks)
     nstages = 1 + 2 * L
     assert len(frob["stages"]) == nstages
+
+
+def _size_error(kind, dtype, flags=0, eps=1e-4, d=16, L=2, **fields):
+    g = B.Gen(kind=kind, dtype=dtype, m=2000, n=1800, x=4096, y=8192, dim=3, **fields)
+    opts = B.make_opts(eps, d, L, seed=1, rank_cap=128, leaf_rank_cap=128, flags=flags)
+    try:
+        B.workspace_size(g, opts)
+    except B.HbacaError as e:
+        return str(e)
+    return None
+
+
+@pytest.mark.parametrize("case", [
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=float("nan")),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=float("inf")),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=0.0),
+    dict(kind=B.GEN_HELMHOLTZ, dtype=B.C128, k=float("nan")),
+    dict(kind=B.GEN_HELMHOLTZ, dtype=B.C128, k=float("inf")),
+    dict(kind=B.GEN_POLYNOMIAL, dtype=B.F64, h=float("inf")),
+    dict(kind=B.GEN_HANKEL2D, dtype=B.C128, k=float("inf")),
+    dict(kind=B.GEN_HANKEL2D, dtype=B.C128, k=-1.0),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.C128, h=1.0),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=1.0, eps=float("nan")),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=1.0, eps=1.0),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=1.0, d=33),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=1.0, L=11),
+    dict(kind=B.GEN_GAUSSIAN, dtype=B.F64, h=1.0, flags=64),
+])
+def test_invalid_parameters_are_refused_when_planning(case):
+    """Faults injected on the host: a NaN or infinite generator parameter, a
+    wrong dtype, tolerance, block size or depth, or an unknown option flag is
+    refused (HBACA_INVALID_ARG with a message) before any launch."""
+    msg = _size_error(**case)
+    assert msg, case
+
+
+def test_valid_parameters_plan():
+    assert _size_error(B.GEN_GAUSSIAN, B.F64, h=0.7) is None
+    assert _size_error(B.GEN_HELMHOLTZ, B.C128, k=4 * np.pi, flags=B.FLAG_FROB | B.FLAG_TAPE) is None
