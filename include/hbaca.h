@@ -79,8 +79,8 @@ typedef struct hbaca_gen {
   const double* y;     /* n x dim */
   int32_t dim;         /* 1 .. 64 */
   int32_t pad0;
-  double h;            /* Gaussian width (> 0); POLYNOMIAL: the shift h */
-  double k;            /* Helmholtz / HANKEL2D wavenumber (HANKEL2D: > 0) */
+  double h;            /* Gaussian width (finite, > 0); POLYNOMIAL: the shift h (finite) */
+  double k;            /* Helmholtz / HANKEL2D wavenumber (finite; HANKEL2D: > 0) */
   /* DENSE */
   const void* a;       /* m x n column-major, scalar = dtype */
   int64_t lda;
@@ -154,7 +154,7 @@ typedef struct hbaca_opts {
                              merged block), <= 1024; 0 = min(m, n, 1024) */
   int64_t leaf_rank_cap;  /* capacity of a leaf's BACA factors before
                              re-compression, <= 1024; 0 = min(m_leaf, n_leaf, 1024) */
-  uint32_t flags;         /* HBACA_FLAG_* */
+  uint32_t flags;         /* HBACA_FLAG_* (any other bit: HBACA_INVALID_ARG) */
   int32_t cluster;        /* CTAs per leaf (1, 2, 4, 8, 16); 0 = choose automatically */
   double srrqr_f;         /* 0: the greedy QRCP pivots of Alg. 2.  f > 1: each greedy
                              pivot set I_k / J_{k+1} whose smallest pivot residual is
