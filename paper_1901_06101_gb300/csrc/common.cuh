@@ -86,8 +86,6 @@ template <typename T> __device__ __forceinline__ T from_re(double r);
 template <> __device__ __forceinline__ double from_re<double>(double r) { return r; }
 template <> __device__ __forceinline__ cplx from_re<cplx>(double r) { return mk(r, 0.0); }
 
-__device__ __forceinline__ bool finite_(double a) { return isfinite(a); }
-
 // Loads of data written by other CTAs of the cluster earlier in the same
 // kernel go through L2 (ld.global.cg), never a possibly stale L1 line.
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
