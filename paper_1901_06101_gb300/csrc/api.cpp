@@ -28,8 +28,8 @@ struct hbaca_ctx {
   hbaca::Plan gplan;
   cudaStream_t cap_stream;  // captures run on this stream (the legacy default stream cannot be captured)
   // concurrent Jacobi launch groups of one stage (created on first use)
-  cudaStream_t aux_stream;
-  cudaEvent_t fork_ev, join_ev;
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace {
@@ -115,12 +115,19 @@ hbaca_status hbaca_create(hbaca_ctx** ctx) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (major * 10 + minor != 103)
     return fail(HBACA_CUDA, "libhbaca is built for sm_103a (GB300); device is sm_" + std::to_string(major * 10 + minor));
-  *ctx = new (std::nothrow) hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0, {}, nullptr, {}, {}, nullptr};
-  if (!*ctx) return fail(HBACA_INVALID_ARG, "out of host memory");
+  hbaca_ctx* c = new (std::nothrow)
+      hbaca_ctx{dev, sms, {nullptr, nullptr, nullptr, nullptr}, false, 0, {}, nullptr, {}, {}, nullptr, nullptr, nullptr,
+                nullptr};
+  if (!c) return fail(HBACA_INVALID_ARG, "out of host memory");
   for (int i = 0; i < 4; ++i) {
-    e = cudaEventCreate(&(*ctx)->ev[i]);
-    if (e != cudaSuccess) return fail(HBACA_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(c->ev[j]);
+      delete c;
+      return fail(HBACA_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
   }
+  *ctx = c;
   tls_err.clear();
   return HBACA_OK;
 }
