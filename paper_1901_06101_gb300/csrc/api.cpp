@@ -161,6 +161,7 @@ size_t hbaca_workspace_size_batched(int32_t nblocks, const hbaca_gen* gens, cons
 static hbaca_status compress_blocks(hbaca_ctx* ctx, int32_t nblocks, const hbaca_gen* gens, const hbaca_opts* opts,
                                     hbaca_result* outs, void* workspace, void* stream) {
   if (!ctx || !gens || !opts || !outs || nblocks < 1) return fail(HBACA_INVALID_ARG, "NULL ctx, gens, opts or results");
+  const hbaca::NvtxRange range(nblocks > 1 ? "hbaca_compress_batched" : "hbaca_compress");
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return fail(HBACA_WORKSPACE, "workspace must be a non-NULL, 256-byte aligned device pointer");
   for (int b = 0; b < nblocks; ++b) {

@@ -143,6 +143,7 @@ inline int pick_groups(int jobs, int rows, int sms, int resident, int min_rows_p
 
 template <typename Gen>
 cudaError_t run_baca(Plan& p, const Gen& gen, RunCtx& rc, std::string& err) {
+  const NvtxRange range("hbaca leaf BACA (Alg. 2)");
   using T = typename Gen::scalar;
   char* ws = rc.ws;
   BacaParams<Gen> P;
@@ -499,6 +500,10 @@ cudaError_t run_stages(Plan& p, RunCtx& rc, std::string& err) {
   if (rc.ev[1]) HB_TRY(cudaEventRecord(rc.ev[1], rc.st));  // leaf BACA done
   for (size_t i = 0; i < p.stages.size(); ++i) {
     const Stage& sg = p.stages[i];
+    const NvtxRange range(std::string("hbaca stage ") + std::to_string(i) +
+                          (sg.kind == TASK_LEAF ? " leaf re-compression" : sg.kind == TASK_HORIZ ? " horizontal merge"
+                                                                                                 : " vertical merge") +
+                          " (" + std::to_string(sg.ntasks) + " tasks)");
     if (rc.ev[2] && sg.kind != TASK_LEAF && (i == 0 || p.stages[i - 1].kind == TASK_LEAF))
       HB_TRY(cudaEventRecord(rc.ev[2], rc.st));  // leaf re-compression done
     cudaError_t e = run_stage<T>(p, (int)i, sg, rc, err);

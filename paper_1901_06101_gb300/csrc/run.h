@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <utility>
@@ -10,6 +11,17 @@
 #include "plan.h"
 
 namespace hbaca {
+
+// A named range on the host timeline (NVTX) around a call or a phase, for
+// timeline and profiling tools (ncu --nvtx); it costs nothing measurable when
+// no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  explicit NvtxRange(const std::string& name) { nvtxRangePushA(name.c_str()); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Kernel classes timed under HBACA_FLAG_PROFILE (hbaca_kernel_times).
 enum KernelClass {
